@@ -1,0 +1,152 @@
+"""Pins of the oracle's samplers (Algs. 1-3) against a pure-Python twin.
+
+The twin builds every draw from numpy's Philox (an independent
+implementation of the generator), Python integers for randi, and a Python
+set for nonzero membership, following the sampling conventions: nonzero
+draws first, then zeros; stratified zeros are the first q accepted
+candidates in candidate order.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from test_oracle_rng import numpy_philox_block
+
+
+def twin_index(dims, seed, stream, tag, j, problem=0):
+    return [(numpy_philox_block([j, stream, tag, k // 4], [seed, problem])[k % 4] * n) >> 64
+            for k, n in enumerate(dims)]
+
+
+def twin_key(dims, ix):
+    key = 0
+    for n, i in zip(dims, ix):
+        key = key * n + i
+    return key
+
+
+def twin_sample(dims, dense, coo, vals, kind, p, q, seed, stream, rho=1.1):
+    omega = math.prod(dims)
+    out = []  # (idx, x, w, cls)
+    if kind == oracle.UNIFORM:
+        for j in range(q):
+            ix = twin_index(dims, seed, stream, oracle.TAG_UNIFORM, j)
+            out.append((ix, dense[tuple(ix)], omega / q, oracle.CLS_UNIFORM))
+        return out
+    eta = len(coo)
+    for j in range(p):
+        w0 = numpy_philox_block([j, stream, oracle.TAG_NONZERO, 0], [seed, 0])[0]
+        xi = (w0 * eta) >> 64
+        out.append((list(coo[xi]), 1.0 if vals is None else vals[xi], eta / p,
+                    oracle.CLS_STRAT_NZ if kind == oracle.STRATIFIED else oracle.CLS_SEMI_NZ))
+    if kind == oracle.SEMI_STRATIFIED:
+        for j in range(q):
+            ix = twin_index(dims, seed, stream, oracle.TAG_SEMI_ZERO, j)
+            out.append((ix, 0.0, omega / q, oracle.CLS_SEMI_ZERO))
+        return out
+    nzset = {twin_key(dims, c) for c in coo}
+    zeta = omega - eta
+    c = 0
+    while len(out) < p + q:
+        ix = twin_index(dims, seed, stream, oracle.TAG_ZERO_CANDIDATE, c)
+        c += 1
+        if twin_key(dims, ix) in nzset:
+            continue
+        out.append((ix, 0.0, zeta / q, oracle.CLS_STRAT_ZERO))
+    return out
+
+
+def compare(S, twin):
+    assert S.n == len(twin)
+    for e, (ix, x, w, cls) in enumerate(twin):
+        assert S.idx[e].tolist() == [int(v) for v in ix]
+        assert S.x[e] == x
+        assert S.w[e] == pytest.approx(w, rel=1e-15)
+        assert S.cls[e] == cls
+
+
+def sparse_problem(dims, density, seed, binary=False):
+    rng = np.random.default_rng(seed)
+    X = (rng.random(dims) < density) * (1.0 if binary else rng.integers(1, 5, dims))
+    coo = np.argwhere(X != 0)
+    vals = None if binary else X[tuple(coo.T)]
+    return X, coo, vals
+
+
+def test_uniform_matches_twin():
+    dims = (5, 6, 7)
+    X = np.random.default_rng(0).standard_normal(dims)
+    S = oracle.sample(oracle.Tensor(dims, dense=X), oracle.UNIFORM, 0, 200, 17, 3)
+    compare(S, twin_sample(dims, X, None, None, oracle.UNIFORM, 0, 200, 17, 3))
+
+
+@pytest.mark.parametrize("binary", [False, True])
+def test_stratified_matches_twin(binary):
+    dims = (6, 5, 4, 3)
+    X, coo, vals = sparse_problem(dims, 0.3, 1, binary)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    S = oracle.sample(T, oracle.STRATIFIED, 50, 80, 23, 9)
+    compare(S, twin_sample(dims, X, coo, vals, oracle.STRATIFIED, 50, 80, 23, 9))
+    # accepted zeros are zeros; nonzero draws are nonzeros
+    for e in range(S.n):
+        is_nz = X[tuple(S.idx[e])] != 0
+        assert is_nz == (S.cls[e] == oracle.CLS_STRAT_NZ)
+
+
+@pytest.mark.parametrize("binary", [False, True])
+def test_semi_stratified_matches_twin(binary):
+    dims = (6, 5, 4, 3, 2)
+    X, coo, vals = sparse_problem(dims, 0.2, 2, binary)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    S = oracle.sample(T, oracle.SEMI_STRATIFIED, 40, 60, 29, 4)
+    compare(S, twin_sample(dims, X, coo, vals, oracle.SEMI_STRATIFIED, 40, 60, 29, 4))
+
+
+def test_stratified_candidates_counted():
+    dims = (8, 8, 8)
+    X, coo, vals = sparse_problem(dims, 0.5, 3)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    S = oracle.sample(T, oracle.STRATIFIED, 10, 100, 5, 0)
+    nzset = {twin_key(dims, c) for c in coo}
+    rejected = sum(twin_key(dims, twin_index(dims, 5, 0, oracle.TAG_ZERO_CANDIDATE, c)) in nzset
+                   for c in range(S.candidates_used))
+    assert S.candidates_used - rejected == 100
+    # the last candidate examined was accepted
+    last = twin_index(dims, 5, 0, oracle.TAG_ZERO_CANDIDATE, S.candidates_used - 1)
+    assert twin_key(dims, last) not in nzset
+
+
+def test_stratified_shortfall_is_reported():
+    """With a single zero entry and rho tiny, 64 batches cannot supply q zeros."""
+    dims = (4, 4, 4)
+    coo = np.array([c for c in np.ndindex(*dims) if c != (1, 2, 3)])
+    T = oracle.Tensor(dims, coo=coo, vals=np.ones(len(coo)))
+    with pytest.raises(RuntimeError, match="short"):
+        oracle.sample(T, oracle.STRATIFIED, 1, 50, 1, 0, rho=0.01)
+
+
+def test_nonzero_draw_counts_are_binomial():
+    dims = (10, 10, 10)
+    X, coo, vals = sparse_problem(dims, 0.05, 4)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    p = 20000
+    S = oracle.sample(T, oracle.SEMI_STRATIFIED, p, 0, 8, 0)
+    keys = [twin_key(dims, ix) for ix in S.idx[:p].tolist()]
+    eta = len(coo)
+    counts = np.array([keys.count(twin_key(dims, c)) for c in coo])
+    sd = math.sqrt(p * (1 / eta) * (1 - 1 / eta))
+    assert np.all(np.abs(counts - p / eta) < 5 * sd)
+
+
+def test_sorted_keys_membership():
+    dims = (7, 9, 11)
+    X, coo, vals = sparse_problem(dims, 0.1, 5)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    keys = T.sorted_keys()
+    assert np.all(np.diff(keys.astype(np.float64)) > 0)
+    flat = X.reshape(-1)
+    lib = oracle._load()
+    for key in range(flat.size):
+        assert bool(lib.orc_is_nonzero(T.nnz, oracle._p(keys), key)) == (flat[key] != 0)
