@@ -1,0 +1,350 @@
+/*
+ * gcp.h -- C ABI of libgcp_gb300.so, the GB300 (sm_103a) sampled-gradient
+ * path of generalized CP decomposition fitted by Adam (GCP-SGD / GCP-Adam,
+ * Kolda & Hong, "Stochastic Gradients for Large-Scale Tensor Decomposition",
+ * arXiv:1906.01687).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Pointers named "host" are host memory.
+ *  - Indices are 0-based.  Dense tensors are row-major (last mode fastest).
+ *    A linear key is the row-major linear index of a multi-index.
+ *  - Arguments are validated on the host before anything is launched; a bad
+ *    argument returns GCP_ERR_INVALID_ARG and launches nothing.
+ *  - Work is enqueued on the given stream and returns without waiting
+ *    (stream-ordered, asynchronous), except where a function says otherwise.
+ *    Errors found by a kernel (a stratified shortfall, a non-finite value)
+ *    are recorded in a sticky device status word read by
+ *    gcp_get_device_status().
+ *  - Random draws come from Philox4x64-10 (Salmon, Moraes, Dror and Shaw,
+ *    SC'11) with key (seed, problem) and counter (j, stream, tag, k / 4);
+ *    mode k of draw j takes word k % 4 of that block and becomes
+ *    randi(n_k) = floor(word * n_k / 2^64).  Tags: 0 uniform draw, 1 nonzero
+ *    draw (word 0 gives xi = randi(nnz)), 2 stratified zero candidate,
+ *    3 semi-stratified "zero".  The sample set is therefore a pure function
+ *    of (seed, problem, stream) and the tensor.
+ */
+#ifndef GCP_GB300_H
+#define GCP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gcp_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+#define GCP_MAX_MODES 8
+/* Philox stream word of a fixed loss-estimate sample set (Section 5.1: one
+   set serves every epoch and every run). */
+#define GCP_STREAM_EST 0xFFFFFFFFFFFFFFFFull
+
+typedef enum gcp_status {
+    GCP_OK = 0,
+    GCP_ERR_INVALID_ARG = 1,      /* rejected on the host, nothing launched */
+    GCP_ERR_CUDA = 2,             /* a CUDA runtime call failed */
+    GCP_ERR_NO_MEMORY = 3,        /* a library-owned allocation failed */
+    GCP_ERR_SAMPLE_SHORTFALL = 4, /* stratified zeros: fewer than q accepted */
+    GCP_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+    GCP_ERR_NONFINITE = 6,        /* a non-finite loss estimate was seen */
+    GCP_ERR_UNSUPPORTED = 7       /* valid but not supported (e.g. prod(dims) >= 2^64 for stratified) */
+} gcp_status;
+
+/* Elementwise losses f(x, m) and g = df/dm.  Gaussian is Section 1's
+   (x - m)^2; Bernoulli-logit log(1 + e^m) - x m and Poisson-log e^m - x m are
+   the log-link losses of the GCP paper this one builds on (HoKoDu20). */
+typedef enum gcp_loss {
+    GCP_LOSS_GAUSSIAN = 0,
+    GCP_LOSS_BERNOULLI_LOGIT = 1,
+    GCP_LOSS_POISSON_LOG = 2
+} gcp_loss;
+
+/* Samplers: Alg. 1 (uniform, Section 4.1), Alg. 2 (stratified, Section 4.2),
+   Alg. 3 (semi-stratified, Section 4.3). */
+typedef enum gcp_sampler {
+    GCP_SAMPLER_UNIFORM = 0,
+    GCP_SAMPLER_STRATIFIED = 1,
+    GCP_SAMPLER_SEMI_STRATIFIED = 2
+} gcp_sampler;
+
+/* Class of a drawn entry; it selects the form of y_i and of the F-hat term:
+   semi-stratified nonzeros use w [g(x,m) - g(0,m)] and w [f(x,m) - f(0,m)],
+   every other class w g(x,m) and w f(x,m) (x = 0 for zeros). */
+typedef enum gcp_class {
+    GCP_CLS_UNIFORM = 0,    /* Alg. 1, w = omega / s            */
+    GCP_CLS_STRAT_NZ = 1,   /* Alg. 2 nonzero, w = eta / p      */
+    GCP_CLS_STRAT_ZERO = 2, /* Alg. 2 zero, w = zeta / q        */
+    GCP_CLS_SEMI_NZ = 3,    /* Alg. 3 nonzero, w = eta / p      */
+    GCP_CLS_SEMI_ZERO = 4   /* Alg. 3 "zero", w = omega / q     */
+} gcp_class;
+
+/* The data tensor X (Section 3.2).
+   dense  (sparse = 0): vals = prod(dims) FP32 values, row-major, device.
+   sparse (sparse = 1): coordinate format; idx[k][e] = i_k of nonzero e
+                        (int32, device), vals = nnz FP32 values or NULL for
+                        an all-ones (binary) tensor.  Positions must be
+                        unique for the stratified sampler's rejection test. */
+typedef struct gcp_tensor {
+    int32_t d;                        /* modes, 1..8 */
+    int32_t sparse;
+    int64_t dims[GCP_MAX_MODES];      /* n_k, each in [1, 2^31) */
+    int64_t nnz;                      /* sparse only */
+    const float *vals;
+    const int32_t *idx[GCP_MAX_MODES];
+} gcp_tensor;
+
+/* Factor matrices A_k of the CP model (Eq. (1.1)).  Mode k is an n_k x ld
+   row-major FP32 matrix A[k] (device); ld is a multiple of 4 with
+   ld >= rank and columns rank..ld-1 hold zeros.  With bf16 = 1 the gradient
+   and the loss estimate gather rows from the BF16 copies A_bf16[k]
+   (raw bfloat16 bits, same n_k x ld layout), while A stays the FP32 master
+   that gcp_adam_step updates and re-rounds into A_bf16 whenever A_bf16[k]
+   is non-NULL. */
+typedef struct gcp_factors {
+    int32_t rank;
+    int32_t ld;
+    int32_t bf16;
+    int32_t reserved;
+    float *A[GCP_MAX_MODES];
+    uint16_t *A_bf16[GCP_MAX_MODES];
+} gcp_factors;
+
+/* What to draw (Sections 4.1-4.3).  uniform: s = q draws (p ignored);
+   stratified / semi-stratified: p nonzero draws then q zero draws.
+   oversample is Section 4.2's rho (<= 0 selects 1.1): stratified zeros are
+   examined in batches of ceil(rho q omega / zeta) candidates and the first q
+   accepted in candidate order are kept; after 64 batches the draw stops
+   with GCP_ERR_SAMPLE_SHORTFALL in the device status. */
+typedef struct gcp_sampling {
+    int32_t kind;     /* gcp_sampler */
+    int32_t reserved;
+    int64_t p;
+    int64_t q;
+    uint64_t seed;
+    uint64_t problem; /* second key word: separates independent runs */
+    uint64_t stream;  /* counter word: the iteration, or GCP_STREAM_EST */
+    double oversample;
+} gcp_sampling;
+
+/* An explicit list of drawn entries, struct of arrays, device memory owned
+   by the caller: idx[k][e] (int32), x[e], w[e] (FP32), cls[e] (gcp_class). */
+typedef struct gcp_samples {
+    int64_t n;
+    int32_t *idx[GCP_MAX_MODES];
+    float *x;
+    float *w;
+    int8_t *cls;
+} gcp_samples;
+
+/* Adam hyper-parameters (Alg. 4; defaults of Section 5.1: alpha 0.01,
+   beta1 0.9, beta2 0.999, eps 1e-8).  eps_inside_sqrt = 1 divides by
+   sqrt(Ch + eps) as Alg. 4 prints it, 0 by sqrt(Ch) + eps.  lower is the
+   projection bound l (-INFINITY for none). */
+typedef struct gcp_adam_params {
+    float beta1;
+    float beta2;
+    float eps;
+    float lower;
+    int32_t eps_inside_sqrt;
+    int32_t reserved;
+} gcp_adam_params;
+
+/* Epoch control of Alg. 4: tau iterations per epoch, learning-rate decay nu
+   after a failed epoch, stop after more than kappa failed epochs. */
+typedef struct gcp_epoch_params {
+    int64_t tau;
+    float nu;
+    int32_t kappa;
+} gcp_epoch_params;
+
+/* Optimizer state, resident in DEVICE memory (64 bytes, 8-byte aligned,
+   caller-owned), so that whole epochs can be replayed from a CUDA graph
+   without host involvement.  Fields are read and written by kernels. */
+typedef struct gcp_adam_state {
+    double F;        /* current loss estimate F-hat */
+    double F_old;    /* F-hat at the start of the epoch */
+    int64_t t;       /* Adam steps taken; step t+1's bias correction uses power t+1 */
+    int64_t iter;    /* iterations ever run: the Philox stream word of the draws (never wound back) */
+    float alpha;     /* current learning rate */
+    int32_t bad;     /* failed epochs so far (c in Alg. 4) */
+    int32_t done;    /* 1 once more than kappa epochs failed: Adam steps become no-ops */
+    int32_t status;  /* sticky gcp_status of the optimizer kernels */
+    uint32_t ticket; /* internal completion counter; 0 between launches */
+    uint32_t reserved[3];
+} gcp_adam_state;
+
+typedef struct gcp_handle gcp_handle; /* opaque: a prepared tensor */
+
+/* ------------------------------------------------------------------------ */
+/* Handles                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Prepares X for sampling (Section 3.2 storage; Section 4.2 lookup).
+   Copies the descriptor (the caller keeps X's device arrays alive and
+   unchanged for the handle's lifetime) and, for a sparse X, builds in
+   library-owned device memory a packed nonzero record per entry (indices and
+   value in one 16- or 32-byte record, so that a nonzero draw reads one
+   aligned segment).  The nonzero-key hash table of the stratified sampler is
+   built on first stratified use.  Allocates with cudaMalloc and waits for
+   the stream; call it before any stream capture.
+   Errors: GCP_ERR_INVALID_ARG (d outside 1..8, a dimension outside
+   [1, 2^31), nnz < 1 for sparse, NULL arrays), GCP_ERR_NO_MEMORY,
+   GCP_ERR_CUDA. */
+gcp_status gcp_create(gcp_handle **out, const gcp_tensor *X, gcp_stream_t stream);
+
+/* Frees the handle's device memory (synchronises the device first). */
+gcp_status gcp_destroy(gcp_handle *h);
+
+/* Reads and clears the handle's sticky device status word (a gcp_status).
+   Synchronises the device.  host_out: host. */
+gcp_status gcp_get_device_status(gcp_handle *h, int32_t *host_out);
+
+/* Number of entries a sampling spec draws: q for uniform, p + q otherwise.
+   Returns -1 for an invalid spec. */
+int64_t gcp_sample_count(const gcp_sampling *S);
+
+/* ------------------------------------------------------------------------ */
+/* Sampling: Algs. 1-3                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Materialises the drawn entries of Alg. 1 (uniform over a dense X),
+   Alg. 2 (stratified: p nonzeros with xi = randi(nnz), then q zeros by
+   rejection against the nonzero keys) or Alg. 3 (semi-stratified: p
+   nonzeros, then q indices from all of Omega without rejection) into out,
+   nonzero draws first.  Each entry gets its value x (0 for zeros), its
+   weight w (omega/s, eta/p, zeta/q or omega/q, computed in FP64 on the host
+   and rounded once) and its class.  out->n must equal gcp_sample_count(S).
+   stratified needs a sparse X with prod(dims) < 2^64 (else
+   GCP_ERR_UNSUPPORTED); uniform needs a dense X.  May allocate library
+   scratch on the first stratified call (cudaMalloc): make that first call
+   before any stream capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
+   the device status; the unfilled zero slots then hold weight 0. */
+gcp_status gcp_sample(gcp_handle *h, const gcp_sampling *S, const gcp_samples *out,
+                      gcp_stream_t stream);
+
+/* Performs every library-owned allocation that gcp_sample and gcp_grad would
+   make for this spec (the stratified sampler's nonzero-key hash, candidate
+   scratch and zero list), so that later calls with the same or a smaller
+   spec allocate nothing and can be captured in a CUDA graph.  Waits for the
+   stream.  Errors: as gcp_sample. */
+gcp_status gcp_reserve(gcp_handle *h, const gcp_sampling *S, gcp_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Sampled gradient: Eq. (4.3) via Algs. 1-3                               */
+/* ------------------------------------------------------------------------ */
+
+/* Accumulates the stochastic gradient G~_k = Y~_(k) Z_k (Eq. (4.3)) into
+   G[k] (device, FP32, n_k x F->ld, row-major; the caller zeroes G before a
+   fresh gradient -- gcp_adam_step leaves it zeroed).  For every drawn entry
+   i: m_i = sum_j prod_k A_k(i_k, j) (Eq. (1.1)); y_i = w g(x_i, m_i), or
+   w [g(x_i, m_i) - g(0, m_i)] for a semi-stratified nonzero; and for every
+   k, G_k(i_k, :) += y_i * prod_{l != k} A_l(i_l, :).
+   Exactly one of S and list is non-NULL:
+     S    -- draws generated inside the kernel from the spec (fused
+             sampling, nothing materialised except stratified zeros, which
+             go through library scratch);
+     list -- a materialised list (gcp_sample output or the caller's own).
+   stream_dev (device, nullable): if non-NULL the Philox stream word is read
+   from *stream_dev on the device at run time instead of S->stream (used by
+   graph-replayed epochs with &state->iter).
+   Errors: GCP_ERR_INVALID_ARG; kernel-side shortfall as in gcp_sample. */
+gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
+                    const gcp_sampling *S, const gcp_samples *list,
+                    const int64_t *stream_dev, float *const G[GCP_MAX_MODES],
+                    gcp_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Loss estimate: Eqs. (5.1)-(5.2)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* F-hat = sum over the fixed list of w f(x, m) (w [f(x,m) - f(0,m)] for
+   semi-stratified nonzeros), each term in FP32, summed in FP64 in a fixed
+   order (deterministic for a given list), written to *out_dev (device,
+   one double).  Uses library scratch for the per-block partial sums. */
+gcp_status gcp_loss_est(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
+                        const gcp_samples *list, double *out_dev, gcp_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Adam with projection and the epoch logic of Alg. 4                       */
+/* ------------------------------------------------------------------------ */
+
+/* Sets *state (device) to the start of a run: F = F_old = 0, t = iter = 0,
+   alpha, bad = done = status = ticket = 0. */
+gcp_status gcp_state_init(gcp_adam_state *state, float alpha, gcp_stream_t stream);
+
+/* One Adam step for every mode (Alg. 4, inner loop): with t = state->t,
+   B = b1 B + (1-b1) G; C = b2 C + (1-b2) G^2; Bh = B / (1 - b1^(t+1));
+   Ch = C / (1 - b2^(t+1)); A = max(A - alpha Bh / sqrt(Ch + eps), lower)
+   (or sqrt(Ch) + eps); then G = 0, the BF16 copy (where non-NULL) is
+   re-rounded from A, and state->t, state->iter advance by one.  alpha is
+   read from state.  B, C, G: device FP32 with A's layout.  Does nothing
+   but zero G once state->done is set.  dims: host, d entries. */
+gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
+                         float *const G[GCP_MAX_MODES], float *const B[GCP_MAX_MODES],
+                         float *const C[GCP_MAX_MODES], const gcp_adam_params *prm,
+                         gcp_adam_state *state, gcp_stream_t stream);
+
+/* Saves the epoch-start copy of {A, B, C} into {SA, SB, SC} (same layouts)
+   and sets F_old = F (the "save copies" step that opens each epoch of
+   Alg. 4).  Call once after the first loss estimate. */
+gcp_status gcp_epoch_begin(const gcp_factors *F, int32_t d, const int64_t *dims,
+                           float *const B[GCP_MAX_MODES], float *const C[GCP_MAX_MODES],
+                           float *const SA[GCP_MAX_MODES], float *const SB[GCP_MAX_MODES],
+                           float *const SC[GCP_MAX_MODES], gcp_adam_state *state,
+                           gcp_stream_t stream);
+
+/* Closes an epoch (Alg. 4, after EstObj): if state->F > state->F_old or F
+   is not finite, restores {A, B, C} (and the BF16 copy) from {SA, SB, SC},
+   sets F = F_old, t -= tau, alpha *= nu, bad += 1, done = (bad > kappa);
+   otherwise accepts, copying {A, B, C} into {SA, SB, SC} and setting
+   F_old = F for the next epoch.  An equal estimate is accepted.  All on the
+   device; graph-capturable. */
+gcp_status gcp_epoch_end(const gcp_factors *F, int32_t d, const int64_t *dims,
+                         float *const B[GCP_MAX_MODES], float *const C[GCP_MAX_MODES],
+                         float *const SA[GCP_MAX_MODES], float *const SB[GCP_MAX_MODES],
+                         float *const SC[GCP_MAX_MODES], const gcp_epoch_params *ep,
+                         gcp_adam_state *state, gcp_stream_t stream);
+
+/* Rounds A[k] into A_bf16[k] (round to nearest even) for every mode. */
+gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *dims,
+                               gcp_stream_t stream);
+
+/* Launch shape of gcp_grad for one handle (0 / -1 fields mean "choose
+   automatically").  lanes x chunks float4 column chunks cover a row:
+   lanes in {1,2,4,8,16,32} lanes per draw, chunks in {1,2,3,4} per lane
+   (only compiled pairs are accepted); block threads (multiple of 32, <= 256);
+   grid_blocks CTAs (0 = enough for one resident wave); smem_bytes the
+   shared-memory budget for per-CTA accumulation of small G_k (-1 = default,
+   0 = off); smem_min_hits the least expected draws per row per CTA for a
+   mode to accumulate in shared memory (a tenth of a unit: 10 = 1.0).
+   A tuning choice changes the summation order only, never the draws. */
+typedef struct gcp_tuning {
+    int32_t lanes;
+    int32_t chunks;
+    int32_t block;
+    int32_t grid_blocks;
+    int32_t smem_bytes;
+    int32_t smem_min_hits;
+} gcp_tuning;
+
+/* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch
+   shape.  Errors: GCP_ERR_INVALID_ARG for a shape that is not compiled. */
+gcp_status gcp_set_tuning(gcp_handle *h, const gcp_tuning *t);
+
+/* Reports the launch shape gcp_grad would use for these factors and draw
+   count (after automatic choices).  out: host. */
+gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, gcp_tuning *out);
+
+/* A static string naming a status code. */
+const char *gcp_status_string(gcp_status s);
+
+/* Library version string. */
+const char *gcp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCP_GB300_H */

@@ -85,6 +85,10 @@ def _load():
     lib.orc_grad_from_samples.restype = i32
     lib.orc_loss_from_samples.argtypes = [i32, vp, i32, vp, i32, i64, vp, vp, vp, vp]
     lib.orc_loss_from_samples.restype = f64
+    lib.orc_loss_abs_from_samples.argtypes = [i32, vp, i32, vp, i32, i64, vp, vp, vp, vp]
+    lib.orc_loss_abs_from_samples.restype = f64
+    lib.orc_grad_abs_from_samples.argtypes = [i32, vp, i32, vp, i32, i64, vp, vp, vp, vp, vp]
+    lib.orc_grad_abs_from_samples.restype = i32
     lib.orc_full_grad.argtypes = [i32, vp, i32, vp, i32, vp, vp, vp, P(f64)]
     lib.orc_full_grad.restype = i32
     lib.orc_adam_step.argtypes = [i64, vp, vp, vp, vp, f64, f64, f64, f64, f64, i64, i32]
@@ -284,6 +288,30 @@ def loss_estimate(dims, factors, loss: int, S: Samples) -> float:
     A = concat_factors(factors)
     return float(lib.orc_loss_from_samples(len(dims), _p(dims), rank, _p(A), loss, S.n,
                                            _p(S.idx), _p(S.x), _p(S.w), _p(S.cls)))
+
+
+def loss_abs(dims, factors, loss: int, S: Samples) -> float:
+    """Sum of |term| of F-hat over S: the error scale of any summation order."""
+    lib = _load()
+    dims = _i64(dims)
+    rank = factors[0].shape[1]
+    A = concat_factors(factors)
+    return float(lib.orc_loss_abs_from_samples(len(dims), _p(dims), rank, _p(A), loss, S.n,
+                                               _p(S.idx), _p(S.x), _p(S.w), _p(S.cls)))
+
+
+def grad_abs(dims, factors, loss: int, S: Samples):
+    """Per-entry sum of |contribution| to the sampled gradient over S."""
+    lib = _load()
+    dims = _i64(dims)
+    rank = factors[0].shape[1]
+    A = concat_factors(factors)
+    G = np.zeros_like(A)
+    st = lib.orc_grad_abs_from_samples(len(dims), _p(dims), rank, _p(A), loss, S.n,
+                                       _p(S.idx), _p(S.x), _p(S.w), _p(S.cls), _p(G))
+    if st != OK:
+        raise ValueError("oracle grad_abs: invalid arguments")
+    return split_factors(G, dims, rank)
 
 
 def full_grad(dims, factors, loss: int, X_dense, weights=None):

@@ -384,6 +384,47 @@ double orc_loss_from_samples(int d, const int64_t *dims, int rank, const double 
     return F;
 }
 
+/* Sum of |term| over the same list: the scale that bounds the rounding     */
+/* error of any summation order of F-hat's terms (used for tolerances).     */
+double orc_loss_abs_from_samples(int d, const int64_t *dims, int rank, const double *A, int loss,
+                                 int64_t n, const int64_t *idx, const double *x, const double *w,
+                                 const int8_t *cls)
+{
+    double S = 0.0;
+    for (int64_t e = 0; e < n; ++e) {
+        double m = orc_model_value(d, dims, rank, A, idx + e * d);
+        S += fabs(orc_entry_f(loss, cls[e], x[e], m, w[e]));
+    }
+    return S;
+}
+
+/* Per-entry sum of |contribution| to the sampled gradient: for every drawn  */
+/* entry, Gabs_k(i_k,:) += |y * prod_{l != k} A_l(i_l,:)|.  The scale that  */
+/* bounds the rounding error of any summation order of G's terms.           */
+int orc_grad_abs_from_samples(int d, const int64_t *dims, int rank, const double *A, int loss,
+                              int64_t n, const int64_t *idx, const double *x, const double *w,
+                              const int8_t *cls, double *Gabs)
+{
+    if (d < 1 || d > ORC_MAX_D || rank < 1) return ORC_ERR_ARG;
+    int64_t off[ORC_MAX_D];
+    mode_offsets(d, dims, rank, off);
+    int64_t total = off[d - 1] + dims[d - 1] * rank;
+    memset(Gabs, 0, (size_t)total * sizeof(double));
+    for (int64_t e = 0; e < n; ++e) {
+        const int64_t *ix = idx + e * d;
+        double m = orc_model_value(d, dims, rank, A, ix);
+        double y = orc_entry_y(loss, cls[e], x[e], m, w[e]);
+        for (int k = 0; k < d; ++k)
+            for (int j = 0; j < rank; ++j) {
+                double prod = 1.0;
+                for (int l = 0; l < d; ++l)
+                    if (l != k) prod *= A[off[l] + ix[l] * rank + j];
+                Gabs[off[k] + ix[k] * rank + j] += fabs(y * prod);
+            }
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Full (non-stochastic) gradient and objective over all of Omega of a     */
 /* dense tensor: G_k = Y_(k) Z_k with y_i = v_i g(x_i, m_i) (Eqs. (4.1),    */

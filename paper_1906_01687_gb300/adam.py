@@ -1,0 +1,124 @@
+"""GCP-Adam (Alg. 4) driven through the C ABI, with device-resident state.
+
+One epoch is: tau x (fused sampled gradient, Adam step with projection),
+then the fixed-sample loss estimate and the accept-or-revert decision, all
+enqueued on one stream.  The Philox stream word of each iteration's draws is
+read by the gradient kernel from the device state (``iter``), so an epoch's
+launches are identical every time and can be captured once in a CUDA graph
+and replayed; the host reads the 64-byte state only to decide when to stop.
+
+Readings of Alg. 4 (shared with the oracle's driver): the bias correction of
+step t uses t + 1; an equal estimate is accepted; a non-finite one fails; the
+draws' stream word counts every iteration ever run and is never wound back.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional, Sequence
+
+import torch
+
+from . import gcp
+
+
+class GcpAdam:
+    def __init__(self, X: gcp.DataTensor, A0: Sequence, loss: int, sampler: int, p: int, q: int,
+                 est_p: int, est_q: int, seed: int, est_seed: int, alpha: float = 0.01, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8, tau: int = 1000, kappa: int = 1, nu: float = 0.1,
+                 lower: float = -math.inf, bf16: bool = False, problem: int = 0, oversample: float = 1.1,
+                 handle: Optional[gcp.Handle] = None, eps_inside_sqrt: bool = True, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = handle if handle is not None else gcp.Handle(X, stream=self.stream)
+        self.loss = loss
+        self.tau, self.kappa, self.nu = int(tau), int(kappa), float(nu)
+        self.adam = dict(beta1=beta1, beta2=beta2, eps=eps, lower=lower, eps_inside_sqrt=eps_inside_sqrt)
+        device = self.stream.device if hasattr(self.stream, "device") else "cuda"
+        with torch.cuda.stream(self.stream):
+            self.F = gcp.Factors(A0, bf16=bf16, device=device)
+            self.G, self.B, self.C = self.F.like(), self.F.like(), self.F.like()
+            self.SA, self.SB, self.SC = self.F.like(), self.F.like(), self.F.like()
+            self.state = gcp.new_state(device)
+        self.spec = gcp.Sampling(sampler, p, q, seed, 0, problem, oversample)
+        est_spec = gcp.Sampling(sampler, est_p, est_q, est_seed, gcp.STREAM_EST, problem, oversample)
+        gcp.gcp_reserve(self.h, self.spec, stream=self.stream)
+        gcp.gcp_reserve(self.h, est_spec, stream=self.stream)
+        self.est = gcp.gcp_sample(self.h, est_spec, stream=self.stream)
+        gcp.gcp_state_init(self.state, alpha, stream=self.stream)
+        gcp.gcp_loss_est(self.h, self.F, loss, self.est, self.state[0:1], stream=self.stream)
+        gcp.gcp_epoch_begin(self.F, self.B, self.C, self.SA, self.SB, self.SC, self.state, stream=self.stream)
+        self.graph = None
+        self.history = []
+
+    # -- one epoch of launches --------------------------------------------
+    def iteration(self):
+        """One sampled gradient + Adam step (draws from the device iteration counter)."""
+        gcp.gcp_grad(self.h, self.F, self.loss, self.G, S=self.spec, stream_dev=self.state[3:4], stream=self.stream)
+        gcp.gcp_adam_step(self.F, self.G, self.B, self.C, self.state, stream=self.stream, **self.adam)
+
+    def end_epoch(self):
+        gcp.gcp_loss_est(self.h, self.F, self.loss, self.est, self.state[0:1], stream=self.stream)
+        gcp.gcp_epoch_end(self.F, self.B, self.C, self.SA, self.SB, self.SC, self.state, self.tau, self.nu,
+                          self.kappa, stream=self.stream)
+
+    def enqueue_epoch(self):
+        for _ in range(self.tau):
+            self.iteration()
+        self.end_epoch()
+
+    def _warm(self):
+        """Runs every kernel of an epoch once on throwaway copies, so that no
+        kernel is first loaded inside a graph capture."""
+        F = gcp.Factors([a[:, : self.F.rank] for a in self.F.A], bf16=self.F.bf16, device=self.F.A[0].device)
+        G, B, C, SA, SB, SC = (F.like() for _ in range(6))
+        st = gcp.new_state(self.F.A[0].device)
+        gcp.gcp_state_init(st, 0.0, stream=self.stream)
+        gcp.gcp_grad(self.h, F, self.loss, G, S=self.spec, stream_dev=st[3:4], stream=self.stream)
+        gcp.gcp_adam_step(F, G, B, C, st, stream=self.stream, **self.adam)
+        gcp.gcp_loss_est(self.h, F, self.loss, self.est, st[0:1], stream=self.stream)
+        gcp.gcp_epoch_end(F, B, C, SA, SB, SC, st, self.tau, self.nu, self.kappa, stream=self.stream)
+        self.stream.synchronize()
+
+    def capture(self):
+        """Captures one epoch's launches in a CUDA graph (replayed by run_epoch)."""
+        self._warm()
+        self.stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=self.stream.device)
+        with torch.cuda.graph(g, stream=cap):
+            saved, self.stream = self.stream, torch.cuda.current_stream()
+            try:
+                self.enqueue_epoch()
+            finally:
+                self.stream = saved
+        self.graph = g
+        return g
+
+    def run_epoch(self):
+        if self.graph is not None:
+            with torch.cuda.stream(self.stream):
+                self.graph.replay()
+        else:
+            self.enqueue_epoch()
+
+    def status(self) -> dict:
+        self.stream.synchronize()
+        return gcp.read_state(self.state)
+
+    def fit(self, max_epochs: int = 1000, use_graph: bool = True, log=None) -> dict:
+        if use_graph and self.graph is None:
+            self.capture()
+        st = self.status()
+        self.history.append(st["F"])
+        for epoch in range(max_epochs):
+            self.run_epoch()
+            st = self.status()
+            self.history.append(st["F"])
+            if log is not None:
+                log(dict(epoch=epoch + 1, **st))
+            if st["done"]:
+                break
+        return st
+
+    def factors(self):
+        self.stream.synchronize()
+        return self.F.numpy()

@@ -1,0 +1,206 @@
+// Adam with projection and the epoch logic of Alg. 4, with the optimizer
+// state (F-hat, F-hat_old, t, iteration, alpha, failed epochs) kept in device
+// memory so that whole epochs can be replayed from a CUDA graph.
+//
+// Scalars that every block reads at its start are changed only by the last
+// block to finish (a completion ticket), after all blocks have read them.
+#include <cuda_bf16.h>
+
+#include "gcp_device.cuh"
+#include "gcp_kernels.cuh"
+
+namespace gcpk {
+
+__device__ __forceinline__ int mode_of(const ModeTable& mt, int64_t i4)
+{
+    int k = 0;
+#pragma unroll
+    for (int l = 1; l < GCP_MAX_MODES; ++l)
+        if (l < mt.d && i4 >= mt.off4[l]) k = l;
+    return k;
+}
+
+__device__ __forceinline__ void store_bf16x4(uint16_t* dst, float4 v)
+{
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y);
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(v.z), b3 = __float2bfloat16_rn(v.w);
+    uint2 packed;
+    packed.x = static_cast<uint32_t>(__bfloat16_as_ushort(b0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b1)) << 16);
+    packed.y = static_cast<uint32_t>(__bfloat16_as_ushort(b2)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b3)) << 16);
+    *reinterpret_cast<uint2*>(dst) = packed;
+}
+
+// Completion ticket: returns true in exactly one thread of the last block.
+__device__ __forceinline__ bool last_block_done(unsigned int* ticket)
+{
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return is_last && threadIdx.x == 0;
+}
+
+__device__ __forceinline__ float adam_one(float& a, float& b, float& c, float g, float beta1, float beta2,
+                                          float c1, float c2, float eps, float alpha, float lower, bool inside)
+{
+    b = beta1 * b + (1.0f - beta1) * g;
+    c = beta2 * c + (1.0f - beta2) * (g * g);
+    const float bh = b / c1;
+    const float ch = c / c2;
+    const float den = inside ? sqrtf(ch + eps) : sqrtf(ch) + eps;
+    a = fmaxf(a - alpha * (bh / den), lower);
+    return a;
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
+{
+    __shared__ float s_alpha, s_c1, s_c2;
+    __shared__ int s_done;
+    if (threadIdx.x == 0) {
+        const double t1 = static_cast<double>(a.st->t + 1);
+        s_c1 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta1), t1));
+        s_c2 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta2), t1));
+        s_alpha = a.st->alpha;
+        s_done = a.st->done;
+    }
+    __syncthreads();
+    const ModeTable& mt = a.mt;
+    const int64_t total4 = mt.off4[mt.d];
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const bool inside = a.eps_inside_sqrt != 0;
+    for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
+        const int k = mode_of(mt, i4);
+        const int64_t loc = i4 - mt.off4[k];
+        const int col = static_cast<int>((loc * 4) % mt.ld);
+        float4* g4 = reinterpret_cast<float4*>(mt.G[k]) + loc;
+        if (!s_done && col < mt.rank) {
+            const float4 g = *g4;
+            float4* a4p = reinterpret_cast<float4*>(mt.A[k]) + loc;
+            float4* b4p = reinterpret_cast<float4*>(mt.B[k]) + loc;
+            float4* c4p = reinterpret_cast<float4*>(mt.C[k]) + loc;
+            float4 A4 = *a4p, B4 = *b4p, C4 = *c4p;
+            const int live = mt.rank - col;  // columns of this chunk below rank
+            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
+            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
+            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
+            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
+            *a4p = A4;
+            *b4p = B4;
+            *c4p = C4;
+            if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + loc * 4, A4);
+        }
+        *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (last_block_done(&a.st->ticket)) {
+        if (!a.st->done) a.st->t += 1;
+        a.st->iter += 1;
+        a.st->ticket = 0u;
+        __threadfence();
+    }
+}
+
+cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s)
+{
+    adam_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// epoch_begin (snapshot) and epoch_end (accept or revert)
+__global__ void __launch_bounds__(256) epoch_kernel(const EpochArgs a)
+{
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        const double F = a.st->F, Fo = a.st->F_old;
+        s_fail = a.begin ? 0 : !(F <= Fo);  // an increase or a non-finite estimate fails
+    }
+    __syncthreads();
+    const ModeTable& mt = a.mt;
+    const int64_t total4 = mt.off4[mt.d];
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
+        const int k = mode_of(mt, i4);
+        const int64_t loc = i4 - mt.off4[k];
+        float4* A4 = reinterpret_cast<float4*>(mt.A[k]) + loc;
+        float4* B4 = reinterpret_cast<float4*>(mt.B[k]) + loc;
+        float4* C4 = reinterpret_cast<float4*>(mt.C[k]) + loc;
+        float4* SA4 = reinterpret_cast<float4*>(mt.SA[k]) + loc;
+        float4* SB4 = reinterpret_cast<float4*>(mt.SB[k]) + loc;
+        float4* SC4 = reinterpret_cast<float4*>(mt.SC[k]) + loc;
+        if (s_fail) {
+            const float4 sa = *SA4;
+            *A4 = sa;
+            *B4 = *SB4;
+            *C4 = *SC4;
+            if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + loc * 4, sa);
+        } else {
+            *SA4 = *A4;
+            *SB4 = *B4;
+            *SC4 = *C4;
+        }
+    }
+    if (last_block_done(&a.st->ticket)) {
+        gcp_adam_state* st = a.st;
+        if (a.begin) {
+            st->F_old = st->F;
+        } else if (s_fail) {
+            if (!isfinite(st->F)) atomicCAS(&st->status, 0, static_cast<int32_t>(GCP_ERR_NONFINITE));
+            st->F = st->F_old;
+            st->t -= a.tau;
+            st->alpha *= a.nu;
+            st->bad += 1;
+            st->done = st->bad > a.kappa ? 1 : 0;
+        } else {
+            st->F_old = st->F;
+        }
+        st->ticket = 0u;
+        __threadfence();
+    }
+}
+
+cudaError_t launch_epoch(const EpochArgs& a, int grid, cudaStream_t s)
+{
+    epoch_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void state_init_kernel(gcp_adam_state* st, float alpha)
+{
+    st->F = 0.0;
+    st->F_old = 0.0;
+    st->t = 0;
+    st->iter = 0;
+    st->alpha = alpha;
+    st->bad = 0;
+    st->done = 0;
+    st->status = 0;
+    st->ticket = 0u;
+    st->reserved[0] = st->reserved[1] = st->reserved[2] = 0u;
+}
+
+cudaError_t launch_state_init(gcp_adam_state* st, float alpha, cudaStream_t s)
+{
+    state_init_kernel<<<1, 1, 0, s>>>(st, alpha);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) to_bf16_kernel(const ModeTable mt)
+{
+    const int64_t total4 = mt.off4[mt.d];
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
+        const int k = mode_of(mt, i4);
+        const int64_t loc = i4 - mt.off4[k];
+        if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + loc * 4, reinterpret_cast<const float4*>(mt.A[k])[loc]);
+    }
+}
+
+cudaError_t launch_to_bf16(const ModeTable& mt, int grid, cudaStream_t s)
+{
+    to_bf16_kernel<<<grid, 256, 0, s>>>(mt);
+    return cudaGetLastError();
+}
+
+}  // namespace gcpk

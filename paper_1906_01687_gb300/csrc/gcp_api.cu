@@ -1,0 +1,767 @@
+// The C ABI of include/gcp.h: argument validation, library-owned memory,
+// launch-shape choice and kernel dispatch.  No arithmetic of the method
+// happens here except the FP64 sampling weights, computed once per call.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/gcp.h"
+#include "gcp_kernels.cuh"
+
+using namespace gcpk;
+
+static_assert(sizeof(gcp_tensor) == 152, "gcp_tensor layout");
+static_assert(sizeof(gcp_factors) == 144, "gcp_factors layout");
+static_assert(sizeof(gcp_sampling) == 56, "gcp_sampling layout");
+static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
+static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
+static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
+static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
+static_assert(sizeof(gcp_tuning) == 24, "gcp_tuning layout");
+
+struct gcp_handle {
+    gcp_tensor X{};
+    uint64_t strides[GCP_MAX_MODES]{};
+    bool omega_fits_u64 = false;
+    double omega = 0.0;
+    int rec_int4 = 0;
+    int4* recs = nullptr;
+    int32_t* d_status = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    // nonzero-key hash (stratified)
+    unsigned long long* table = nullptr;
+    uint64_t table_mask = 0;
+    // stratified zero list and its pass scratch
+    int64_t zq_cap = 0;
+    int32_t* zidx_base = nullptr;
+    int64_t* zcount = nullptr;
+    int64_t ztiles_cap = 0;
+    uint32_t* mask_words = nullptr;
+    int32_t* tile_counts = nullptr;
+    int64_t* tile_offsets = nullptr;
+    // loss-estimate partial sums
+    double* partials = nullptr;
+    unsigned int* ticket = nullptr;
+    int partials_cap = 0;
+    gcp_tuning tune{0, 0, 0, 0, -1, -1};
+};
+
+namespace {
+
+constexpr int kLossMaxBlocks = 2048;
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+gcp_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return GCP_OK;
+    if (e == cudaErrorMemoryAllocation) return GCP_ERR_NO_MEMORY;
+    return GCP_ERR_CUDA;
+}
+
+#define GCP_CUDA_TRY(expr)                                 \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_status(e_);     \
+    } while (0)
+
+// prod(dims) exactly, or flag overflow of 64 bits
+bool omega_u64(const gcp_tensor& X, uint64_t* out)
+{
+    unsigned __int128 w = 1;
+    for (int k = 0; k < X.d; ++k) {
+        w *= static_cast<unsigned __int128>(X.dims[k]);
+        if (w >> 64) return false;
+    }
+    *out = static_cast<uint64_t>(w);
+    return true;
+}
+
+gcp_status check_factors(const gcp_handle* h, const gcp_factors* F)
+{
+    if (!F) return GCP_ERR_INVALID_ARG;
+    if (F->rank < 1 || F->rank > 256 || F->ld < F->rank || F->ld % 4 != 0) return GCP_ERR_INVALID_ARG;
+    for (int k = 0; k < h->X.d; ++k) {
+        if (!F->A[k] || !aligned(F->A[k], 16)) return GCP_ERR_INVALID_ARG;
+        if (F->bf16 && (!F->A_bf16[k] || !aligned(F->A_bf16[k], 8))) return GCP_ERR_INVALID_ARG;
+    }
+    return GCP_OK;
+}
+
+gcp_status check_list(const gcp_handle* h, const gcp_samples* L)
+{
+    if (!L || L->n < 0) return GCP_ERR_INVALID_ARG;
+    if (L->n == 0) return GCP_OK;
+    for (int k = 0; k < h->X.d; ++k)
+        if (!L->idx[k]) return GCP_ERR_INVALID_ARG;
+    if (!L->x || !L->w || !L->cls) return GCP_ERR_INVALID_ARG;
+    return GCP_OK;
+}
+
+gcp_status check_spec(const gcp_handle* h, const gcp_sampling* S)
+{
+    if (!S || S->p < 0 || S->q < 0) return GCP_ERR_INVALID_ARG;
+    if (S->p > (int64_t(1) << 40) || S->q > (int64_t(1) << 40)) return GCP_ERR_INVALID_ARG;
+    switch (S->kind) {
+    case GCP_SAMPLER_UNIFORM:
+        if (h->X.sparse) return GCP_ERR_UNSUPPORTED;  // uniform sampling of a sparse tensor needs a value lookup
+        return GCP_OK;
+    case GCP_SAMPLER_STRATIFIED:
+        if (!h->X.sparse) return GCP_ERR_INVALID_ARG;
+        if (!h->omega_fits_u64) return GCP_ERR_UNSUPPORTED;
+        if (S->q > 0 && h->omega - static_cast<double>(h->X.nnz) <= 0.0) return GCP_ERR_INVALID_ARG;
+        return GCP_OK;
+    case GCP_SAMPLER_SEMI_STRATIFIED:
+        if (!h->X.sparse) return GCP_ERR_INVALID_ARG;
+        return GCP_OK;
+    default:
+        return GCP_ERR_INVALID_ARG;
+    }
+}
+
+// Draw descriptor shared by every kernel that generates or reads draws.
+DrawArgs make_draw_args(const gcp_handle* h, const gcp_sampling* S, const gcp_samples* L,
+                        const int64_t* stream_dev)
+{
+    DrawArgs a{};
+    a.d = h->X.d;
+    for (int k = 0; k < h->X.d; ++k) {
+        a.dims[k] = static_cast<uint32_t>(h->X.dims[k]);
+        a.strides[k] = h->strides[k];
+    }
+    a.X = h->X.sparse ? nullptr : h->X.vals;
+    a.nz_rec = h->recs;
+    a.rec_int4 = h->rec_int4;
+    a.nnz = h->X.nnz;
+    a.stream_dev = stream_dev;
+    if (L) {
+        a.src = kSrcList;
+        a.n_total = L->n;
+        for (int k = 0; k < h->X.d; ++k) a.lidx[k] = L->idx[k];
+        a.lx = L->x;
+        a.lw = L->w;
+        a.lcls = L->cls;
+        return a;
+    }
+    a.seed = S->seed;
+    a.problem = S->problem;
+    a.stream = S->stream;
+    const double omega = h->omega, eta = static_cast<double>(h->X.nnz);
+    if (S->kind == GCP_SAMPLER_UNIFORM) {
+        a.src = kSrcUniformDense;
+        a.p = 0;
+        a.n_total = S->q;
+        a.w_first = S->q > 0 ? static_cast<float>(omega / static_cast<double>(S->q)) : 0.0f;
+        return a;
+    }
+    a.src = kSrcSparse;
+    a.semi = S->kind == GCP_SAMPLER_SEMI_STRATIFIED;
+    a.p = S->p;
+    a.n_total = S->p + S->q;
+    a.w_first = S->p > 0 ? static_cast<float>(eta / static_cast<double>(S->p)) : 0.0f;
+    if (S->q > 0)
+        a.w_second = static_cast<float>((a.semi ? omega : omega - eta) / static_cast<double>(S->q));
+    return a;
+}
+
+template <typename T>
+gcp_status grow(T** ptr, int64_t* cap, int64_t need)
+{
+    if (*cap >= need) return GCP_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(ptr), static_cast<size_t>(need) * sizeof(T)));
+    *cap = need;
+    return GCP_OK;
+}
+
+gcp_status ensure_hash(gcp_handle* h, cudaStream_t s)
+{
+    if (h->table) return GCP_OK;
+    uint64_t cap = 1024;
+    while (cap < 2 * static_cast<uint64_t>(h->X.nnz)) cap <<= 1;
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->table), cap * sizeof(unsigned long long)));
+    h->table_mask = cap - 1;
+    GCP_CUDA_TRY(cudaMemsetAsync(h->table, 0xFF, cap * sizeof(unsigned long long), s));
+    GCP_CUDA_TRY(launch_hash_build(h->recs, h->rec_int4, h->X.d, h->strides, h->X.nnz, h->table, h->table_mask,
+                                   h->d_status, s));
+    return GCP_OK;
+}
+
+gcp_status ensure_zero_list(gcp_handle* h, int64_t q)
+{
+    if (q <= h->zq_cap) return GCP_OK;
+    cudaFree(h->zidx_base);
+    h->zidx_base = nullptr;
+    h->zq_cap = 0;
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->zidx_base), static_cast<size_t>(q) * h->X.d * sizeof(int32_t)));
+    h->zq_cap = q;
+    return GCP_OK;
+}
+
+gcp_status ensure_zero_scratch(gcp_handle* h, int64_t tiles)
+{
+    if (tiles <= h->ztiles_cap) return GCP_OK;
+    cudaFree(h->mask_words);
+    cudaFree(h->tile_counts);
+    cudaFree(h->tile_offsets);
+    h->mask_words = nullptr;
+    h->tile_counts = nullptr;
+    h->tile_offsets = nullptr;
+    h->ztiles_cap = 0;
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->mask_words), static_cast<size_t>(tiles) * 32 * sizeof(uint32_t)));
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->tile_counts), static_cast<size_t>(tiles) * sizeof(int32_t)));
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->tile_offsets), static_cast<size_t>(tiles) * sizeof(int64_t)));
+    h->ztiles_cap = tiles;
+    return GCP_OK;
+}
+
+// Candidate batch of Section 4.2: ceil(rho * q * omega / zeta).
+int64_t zero_batch(const gcp_handle* h, const gcp_sampling* S)
+{
+    const double rho = S->oversample > 0.0 ? S->oversample : 1.1;
+    const double zeta = h->omega - static_cast<double>(h->X.nnz);
+    return static_cast<int64_t>(std::ceil(rho * static_cast<double>(S->q) * h->omega / zeta));
+}
+
+// Runs the ordered rejection pass; the accepted zeros go to the given destination.
+gcp_status run_zero_pass(gcp_handle* h, const gcp_sampling* S, const int64_t* stream_dev,
+                         int32_t* const out_idx[GCP_MAX_MODES], float* out_x, float* out_w, int8_t* out_cls,
+                         float w_zero, cudaStream_t s)
+{
+    gcp_status st = ensure_hash(h, s);
+    if (st != GCP_OK) return st;
+    const int64_t batch = zero_batch(h, S);
+    const int64_t tiles = (batch + 1023) / 1024;
+    st = ensure_zero_scratch(h, tiles);
+    if (st != GCP_OK) return st;
+    ZeroArgs z{};
+    z.d = h->X.d;
+    for (int k = 0; k < h->X.d; ++k) {
+        z.dims[k] = static_cast<uint32_t>(h->X.dims[k]);
+        z.strides[k] = h->strides[k];
+        z.out_idx[k] = out_idx[k];
+    }
+    z.seed = S->seed;
+    z.problem = S->problem;
+    z.stream = S->stream;
+    z.stream_dev = stream_dev;
+    z.q = S->q;
+    z.first_tiles = tiles;
+    z.cap = 64 * batch;
+    z.table = h->table;
+    z.table_mask = h->table_mask;
+    z.mask_words = h->mask_words;
+    z.tile_counts = h->tile_counts;
+    z.tile_offsets = h->tile_offsets;
+    z.count_out = h->zcount;
+    z.status = h->d_status;
+    z.out_x = out_x;
+    z.out_w = out_w;
+    z.out_cls = out_cls;
+    z.w_zero = w_zero;
+    GCP_CUDA_TRY(launch_zero_sampling(z, s));
+    return GCP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+struct Shape {
+    int D = 3, L = 1, NC = 1, block = 256, grid = 1;
+    size_t smem = 0;
+    uint32_t mask = 0;
+    uint32_t off[GCP_MAX_MODES] = {};
+};
+
+int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct OccKey {
+    int D, L, NC, bf16, block;
+    size_t smem;
+    int device;
+};
+struct OccEntry {
+    OccKey key;
+    int bps;
+};
+std::mutex g_occ_mutex;
+OccEntry g_occ[256];
+int g_occ_n = 0;
+
+int occupancy(int D, int L, int NC, bool bf16, int block, size_t smem, int device)
+{
+    std::lock_guard<std::mutex> lock(g_occ_mutex);
+    for (int i = 0; i < g_occ_n; ++i) {
+        const OccKey& k = g_occ[i].key;
+        if (k.D == D && k.L == L && k.NC == NC && k.bf16 == int(bf16) && k.block == block && k.smem == smem &&
+            k.device == device)
+            return g_occ[i].bps;
+    }
+    int bps = 0;
+    if (grad_occupancy(D, L, NC, bf16, block, smem, &bps) != cudaSuccess || bps < 1) bps = 1;
+    if (g_occ_n < 256) g_occ[g_occ_n++] = OccEntry{OccKey{D, L, NC, int(bf16), block, smem, device}, bps};
+    return bps;
+}
+
+gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_total, Shape* sh)
+{
+    const int d = h->X.d;
+    sh->D = d == 3 ? 3 : (d == 4 ? 4 : 8);
+    const int chunks = (F->rank + 3) / 4;
+    const gcp_tuning& t = h->tune;
+    if (t.lanes > 0) {
+        sh->L = t.lanes;
+        sh->NC = t.chunks > 0 ? t.chunks : 1;
+        if (!grad_has_config(sh->D, sh->L, sh->NC) || sh->L * sh->NC < chunks) return GCP_ERR_INVALID_ARG;
+    } else if (chunks <= 4) {
+        sh->L = 1;
+        sh->NC = chunks;
+    } else if (chunks <= 32) {
+        sh->L = next_pow2(chunks);
+        sh->NC = 1;
+    } else {
+        sh->L = 32;
+        sh->NC = 2;
+    }
+    sh->block = t.block > 0 ? t.block : 256;
+    if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
+    const int64_t warps = (n_total + 31) / 32;
+    const int64_t blocks_needed = std::max<int64_t>(1, (warps + sh->block / 32 - 1) / (sh->block / 32));
+
+    // shared-memory accumulation of small, often-hit G_k
+    const int64_t budget = t.smem_bytes >= 0 ? t.smem_bytes : 32 * 1024;
+    const double min_hits = t.smem_min_hits >= 0 ? t.smem_min_hits / 10.0 : 2.0;
+    const int64_t grid0 = std::min<int64_t>(blocks_needed, static_cast<int64_t>(h->num_sms) * 4);
+    const double draws_per_cta = static_cast<double>(n_total) / static_cast<double>(std::max<int64_t>(grid0, 1));
+    int64_t used = 0;
+    sh->mask = 0;
+    for (int k = 0; k < d; ++k) {
+        const int64_t bytes = h->X.dims[k] * F->ld * 4;
+        if (used + bytes <= budget && draws_per_cta / static_cast<double>(h->X.dims[k]) >= min_hits) {
+            sh->mask |= 1u << k;
+            sh->off[k] = static_cast<uint32_t>(used / 4);
+            used += bytes;
+        }
+    }
+    sh->smem = static_cast<size_t>(used);
+    const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->block, sh->smem, h->device);
+    const int64_t resident = static_cast<int64_t>(h->num_sms) * bps;
+    sh->grid = static_cast<int>(t.grid_blocks > 0 ? t.grid_blocks : std::min<int64_t>(blocks_needed, resident));
+    return GCP_OK;
+}
+
+ModeTable mode_table(const gcp_factors* F, int32_t d, const int64_t* dims)
+{
+    ModeTable mt{};
+    mt.d = d;
+    mt.ld = F->ld;
+    mt.rank = F->rank;
+    mt.off4[0] = 0;
+    for (int k = 0; k < d; ++k) {
+        mt.off4[k + 1] = mt.off4[k] + dims[k] * F->ld / 4;
+        mt.A[k] = F->A[k];
+        mt.Abf[k] = F->A_bf16[k];
+    }
+    return mt;
+}
+
+gcp_status check_modes(const gcp_factors* F, int32_t d, const int64_t* dims)
+{
+    if (!F || !dims || d < 1 || d > GCP_MAX_MODES) return GCP_ERR_INVALID_ARG;
+    if (F->rank < 1 || F->rank > 256 || F->ld < F->rank || F->ld % 4 != 0) return GCP_ERR_INVALID_ARG;
+    for (int k = 0; k < d; ++k) {
+        if (dims[k] < 1 || dims[k] >= (int64_t(1) << 31)) return GCP_ERR_INVALID_ARG;
+        if (!F->A[k] || !aligned(F->A[k], 16)) return GCP_ERR_INVALID_ARG;
+        if (F->A_bf16[k] && !aligned(F->A_bf16[k], 8)) return GCP_ERR_INVALID_ARG;
+    }
+    return GCP_OK;
+}
+
+bool modes_ok(float* const P[GCP_MAX_MODES], int32_t d)
+{
+    if (!P) return false;
+    for (int k = 0; k < d; ++k)
+        if (!P[k] || !aligned(P[k], 16)) return false;
+    return true;
+}
+
+int elementwise_grid(const ModeTable& mt)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t total4 = mt.off4[mt.d];
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total4 + 255) / 256, int64_t(sms) * 8)));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gcp_version(void) { return "gcp_gb300 0.1 (sm_103a)"; }
+
+const char* gcp_status_string(gcp_status s)
+{
+    switch (s) {
+    case GCP_OK: return "ok";
+    case GCP_ERR_INVALID_ARG: return "invalid argument";
+    case GCP_ERR_CUDA: return "CUDA error";
+    case GCP_ERR_NO_MEMORY: return "out of device memory";
+    case GCP_ERR_SAMPLE_SHORTFALL: return "stratified sampling found fewer zeros than requested";
+    case GCP_ERR_TIMEOUT: return "device wait timed out";
+    case GCP_ERR_NONFINITE: return "non-finite loss estimate";
+    case GCP_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+int64_t gcp_sample_count(const gcp_sampling* S)
+{
+    if (!S || S->p < 0 || S->q < 0) return -1;
+    if (S->kind == GCP_SAMPLER_UNIFORM) return S->q;
+    if (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_SEMI_STRATIFIED) return S->p + S->q;
+    return -1;
+}
+
+gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream)
+{
+    if (!out || !X) return GCP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (X->d < 1 || X->d > GCP_MAX_MODES) return GCP_ERR_INVALID_ARG;
+    for (int k = 0; k < X->d; ++k)
+        if (X->dims[k] < 1 || X->dims[k] >= (int64_t(1) << 31)) return GCP_ERR_INVALID_ARG;
+    if (X->sparse) {
+        if (X->nnz < 1) return GCP_ERR_INVALID_ARG;
+        for (int k = 0; k < X->d; ++k)
+            if (!X->idx[k]) return GCP_ERR_INVALID_ARG;
+    } else if (!X->vals) {
+        return GCP_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    gcp_handle* h = new (std::nothrow) gcp_handle();
+    if (!h) return GCP_ERR_NO_MEMORY;
+    h->X = *X;
+    for (int k = X->d; k < GCP_MAX_MODES; ++k) {
+        h->X.dims[k] = 0;
+        h->X.idx[k] = nullptr;
+    }
+    if (!X->sparse) h->X.nnz = 0;
+    uint64_t om = 0;
+    h->omega_fits_u64 = omega_u64(h->X, &om);
+    h->omega = 1.0;
+    for (int k = 0; k < X->d; ++k) h->omega *= static_cast<double>(X->dims[k]);
+    if (!X->sparse && !h->omega_fits_u64) {
+        delete h;
+        return GCP_ERR_INVALID_ARG;
+    }
+    // row-major strides (wrap modulo 2^64 only when the tensor has >= 2^64 entries,
+    // in which case no linear key is ever formed)
+    uint64_t stride = 1;
+    for (int k = X->d - 1; k >= 0; --k) {
+        h->strides[k] = stride;
+        stride *= static_cast<uint64_t>(X->dims[k]);
+    }
+    auto fail = [&](gcp_status st) {
+        gcp_destroy(h);
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->num_sms < 1) h->num_sms = 1;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), sizeof(int32_t))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->zcount), sizeof(int64_t))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->partials), kLossMaxBlocks * sizeof(double))) != cudaSuccess)
+        return fail(cuda_status(e));
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->ticket), sizeof(unsigned int))) != cudaSuccess) return fail(cuda_status(e));
+    h->partials_cap = kLossMaxBlocks;
+    if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s)) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMemsetAsync(h->zcount, 0, sizeof(int64_t), s)) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(cuda_status(e));
+    if (X->sparse) {
+        h->rec_int4 = (X->d + 1 + 3) / 4;
+        const size_t bytes = static_cast<size_t>(X->nnz) * h->rec_int4 * sizeof(int4);
+        if ((e = cudaMalloc(reinterpret_cast<void**>(&h->recs), bytes)) != cudaSuccess) return fail(cuda_status(e));
+        if ((e = launch_pack_records(h->X, h->recs, h->rec_int4, s)) != cudaSuccess) return fail(cuda_status(e));
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_status(e));
+    h->last_stream = s;
+    *out = h;
+    return GCP_OK;
+}
+
+gcp_status gcp_destroy(gcp_handle* h)
+{
+    if (!h) return GCP_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(h->recs);
+    cudaFree(h->d_status);
+    cudaFree(h->table);
+    cudaFree(h->zidx_base);
+    cudaFree(h->zcount);
+    cudaFree(h->mask_words);
+    cudaFree(h->tile_counts);
+    cudaFree(h->tile_offsets);
+    cudaFree(h->partials);
+    cudaFree(h->ticket);
+    delete h;
+    return GCP_OK;
+}
+
+gcp_status gcp_get_device_status(gcp_handle* h, int32_t* host_out)
+{
+    if (!h || !host_out) return GCP_ERR_INVALID_ARG;
+    GCP_CUDA_TRY(cudaDeviceSynchronize());
+    int32_t v = 0;
+    GCP_CUDA_TRY(cudaMemcpy(&v, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GCP_CUDA_TRY(cudaMemset(h->d_status, 0, sizeof(int32_t)));
+    *host_out = v;
+    return GCP_OK;
+}
+
+gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
+{
+    if (!h) return GCP_ERR_INVALID_ARG;
+    if (!t) {
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1};
+        return GCP_OK;
+    }
+    if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1)) return GCP_ERR_INVALID_ARG;
+    if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
+    if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024) return GCP_ERR_INVALID_ARG;
+    h->tune = *t;
+    return GCP_OK;
+}
+
+gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, gcp_tuning* out)
+{
+    if (!h || !out || n_draws < 0) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_factors(h, F);
+    if (st != GCP_OK) return st;
+    Shape sh;
+    st = choose_shape(h, F, n_draws, &sh);
+    if (st != GCP_OK) return st;
+    out->lanes = sh.L;
+    out->chunks = sh.NC;
+    out->block = sh.block;
+    out->grid_blocks = sh.grid;
+    out->smem_bytes = static_cast<int32_t>(sh.smem);
+    out->smem_min_hits = static_cast<int32_t>(sh.mask);  // reports the shared-memory mode mask
+    return GCP_OK;
+}
+
+gcp_status gcp_sample(gcp_handle* h, const gcp_sampling* S, const gcp_samples* out, gcp_stream_t stream)
+{
+    if (!h) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_spec(h, S);
+    if (st != GCP_OK) return st;
+    st = check_list(h, out);
+    if (st != GCP_OK) return st;
+    if (out->n != gcp_sample_count(S)) return GCP_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    if (out->n == 0) return GCP_OK;
+    DrawArgs dr = make_draw_args(h, S, nullptr, nullptr);
+    if (S->kind != GCP_SAMPLER_STRATIFIED) {
+        GCP_CUDA_TRY(launch_materialise(dr, out->idx, out->x, out->w, out->cls, 0, dr.n_total, h->d_status, s));
+        return GCP_OK;
+    }
+    GCP_CUDA_TRY(launch_materialise(dr, out->idx, out->x, out->w, out->cls, 0, S->p, h->d_status, s));
+    if (S->q == 0) return GCP_OK;
+    int32_t* zdst[GCP_MAX_MODES] = {};
+    for (int k = 0; k < h->X.d; ++k) zdst[k] = out->idx[k] + S->p;
+    return run_zero_pass(h, S, nullptr, zdst, out->x + S->p, out->w + S->p, out->cls + S->p, dr.w_second, s);
+}
+
+gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream)
+{
+    if (!h) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_spec(h, S);
+    if (st != GCP_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    if (S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
+        if ((st = ensure_hash(h, s)) != GCP_OK) return st;
+        if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 1023) / 1024)) != GCP_OK) return st;
+        if ((st = ensure_zero_list(h, S->q)) != GCP_OK) return st;
+    }
+    GCP_CUDA_TRY(cudaStreamSynchronize(s));
+    return GCP_OK;
+}
+
+gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
+                    const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
+                    gcp_stream_t stream)
+{
+    if (!h || (S == nullptr) == (list == nullptr)) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_factors(h, F);
+    if (st != GCP_OK) return st;
+    if (!modes_ok(G, h->X.d)) return GCP_ERR_INVALID_ARG;
+    st = S ? check_spec(h, S) : check_list(h, list);
+    if (st != GCP_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    GradArgs a{};
+    a.dr = make_draw_args(h, S, list, stream_dev);
+    if (a.dr.n_total == 0) return GCP_OK;
+    if (S && S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
+        st = ensure_zero_list(h, S->q);
+        if (st != GCP_OK) return st;
+        int32_t* zdst[GCP_MAX_MODES] = {};
+        for (int k = 0; k < h->X.d; ++k) zdst[k] = h->zidx_base + static_cast<size_t>(k) * h->zq_cap;
+        st = run_zero_pass(h, S, stream_dev, zdst, nullptr, nullptr, nullptr, 0.0f, s);
+        if (st != GCP_OK) return st;
+        for (int k = 0; k < h->X.d; ++k) a.dr.zidx[k] = zdst[k];
+        a.dr.zcount = h->zcount;
+    }
+    Shape sh;
+    st = choose_shape(h, F, a.dr.n_total, &sh);
+    if (st != GCP_OK) return st;
+    a.ld = F->ld;
+    a.rank = F->rank;
+    a.loss = loss;
+    a.smem_floats = static_cast<int32_t>(sh.smem / 4);
+    a.smem_mask = sh.mask;
+    for (int k = 0; k < h->X.d; ++k) {
+        a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);
+        a.G[k] = G[k];
+        a.smem_off[k] = sh.off[k];
+    }
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.grid, sh.block, sh.smem, s));
+    return GCP_OK;
+}
+
+gcp_status gcp_loss_est(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_samples* list,
+                        double* out_dev, gcp_stream_t stream)
+{
+    if (!h || !out_dev || !aligned(out_dev, 8)) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_factors(h, F);
+    if (st != GCP_OK) return st;
+    st = check_list(h, list);
+    if (st != GCP_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    LossArgs a{};
+    a.dr = make_draw_args(h, nullptr, list, nullptr);
+    a.ld = F->ld;
+    a.rank = F->rank;
+    a.loss = loss;
+    for (int k = 0; k < h->X.d; ++k)
+        a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);
+    a.partials = h->partials;
+    a.ticket = h->ticket;
+    a.out = out_dev;
+    const int64_t want = std::max<int64_t>(1, (list->n + 255) / 256);
+    const int grid = static_cast<int>(std::min<int64_t>(want, std::min<int64_t>(h->partials_cap, int64_t(h->num_sms) * 4)));
+    GCP_CUDA_TRY(launch_loss(a, F->bf16 != 0, grid, 256, s));
+    return GCP_OK;
+}
+
+gcp_status gcp_state_init(gcp_adam_state* state, float alpha, gcp_stream_t stream)
+{
+    if (!state || !aligned(state, 8)) return GCP_ERR_INVALID_ARG;
+    GCP_CUDA_TRY(launch_state_init(state, alpha, reinterpret_cast<cudaStream_t>(stream)));
+    return GCP_OK;
+}
+
+gcp_status gcp_adam_step(const gcp_factors* F, int32_t d, const int64_t* dims, float* const G[GCP_MAX_MODES],
+                         float* const B[GCP_MAX_MODES], float* const C[GCP_MAX_MODES], const gcp_adam_params* prm,
+                         gcp_adam_state* state, gcp_stream_t stream)
+{
+    gcp_status st = check_modes(F, d, dims);
+    if (st != GCP_OK) return st;
+    if (!prm || !state || !aligned(state, 8) || !modes_ok(G, d) || !modes_ok(B, d) || !modes_ok(C, d))
+        return GCP_ERR_INVALID_ARG;
+    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
+        return GCP_ERR_INVALID_ARG;
+    AdamArgs a{};
+    a.mt = mode_table(F, d, dims);
+    for (int k = 0; k < d; ++k) {
+        a.mt.G[k] = G[k];
+        a.mt.B[k] = B[k];
+        a.mt.C[k] = C[k];
+    }
+    a.beta1 = prm->beta1;
+    a.beta2 = prm->beta2;
+    a.eps = prm->eps;
+    a.lower = prm->lower;
+    a.eps_inside_sqrt = prm->eps_inside_sqrt;
+    a.st = state;
+    GCP_CUDA_TRY(launch_adam(a, elementwise_grid(a.mt), reinterpret_cast<cudaStream_t>(stream)));
+    return GCP_OK;
+}
+
+static gcp_status epoch_common(const gcp_factors* F, int32_t d, const int64_t* dims, float* const B[GCP_MAX_MODES],
+                               float* const C[GCP_MAX_MODES], float* const SA[GCP_MAX_MODES],
+                               float* const SB[GCP_MAX_MODES], float* const SC[GCP_MAX_MODES],
+                               const gcp_epoch_params* ep, int begin, gcp_adam_state* state, gcp_stream_t stream)
+{
+    gcp_status st = check_modes(F, d, dims);
+    if (st != GCP_OK) return st;
+    if (!state || !aligned(state, 8) || !modes_ok(B, d) || !modes_ok(C, d) || !modes_ok(SA, d) || !modes_ok(SB, d) ||
+        !modes_ok(SC, d))
+        return GCP_ERR_INVALID_ARG;
+    if (!begin && (!ep || ep->tau < 0 || ep->kappa < 0)) return GCP_ERR_INVALID_ARG;
+    EpochArgs a{};
+    a.mt = mode_table(F, d, dims);
+    for (int k = 0; k < d; ++k) {
+        a.mt.B[k] = B[k];
+        a.mt.C[k] = C[k];
+        a.mt.SA[k] = SA[k];
+        a.mt.SB[k] = SB[k];
+        a.mt.SC[k] = SC[k];
+    }
+    if (ep) {
+        a.tau = ep->tau;
+        a.nu = ep->nu;
+        a.kappa = ep->kappa;
+    }
+    a.begin = begin;
+    a.st = state;
+    GCP_CUDA_TRY(launch_epoch(a, elementwise_grid(a.mt), reinterpret_cast<cudaStream_t>(stream)));
+    return GCP_OK;
+}
+
+gcp_status gcp_epoch_begin(const gcp_factors* F, int32_t d, const int64_t* dims, float* const B[GCP_MAX_MODES],
+                           float* const C[GCP_MAX_MODES], float* const SA[GCP_MAX_MODES],
+                           float* const SB[GCP_MAX_MODES], float* const SC[GCP_MAX_MODES], gcp_adam_state* state,
+                           gcp_stream_t stream)
+{
+    return epoch_common(F, d, dims, B, C, SA, SB, SC, nullptr, 1, state, stream);
+}
+
+gcp_status gcp_epoch_end(const gcp_factors* F, int32_t d, const int64_t* dims, float* const B[GCP_MAX_MODES],
+                         float* const C[GCP_MAX_MODES], float* const SA[GCP_MAX_MODES], float* const SB[GCP_MAX_MODES],
+                         float* const SC[GCP_MAX_MODES], const gcp_epoch_params* ep, gcp_adam_state* state,
+                         gcp_stream_t stream)
+{
+    return epoch_common(F, d, dims, B, C, SA, SB, SC, ep, 0, state, stream);
+}
+
+gcp_status gcp_factors_to_bf16(const gcp_factors* F, int32_t d, const int64_t* dims, gcp_stream_t stream)
+{
+    gcp_status st = check_modes(F, d, dims);
+    if (st != GCP_OK) return st;
+    for (int k = 0; k < d; ++k)
+        if (!F->A_bf16[k]) return GCP_ERR_INVALID_ARG;
+    ModeTable mt = mode_table(F, d, dims);
+    GCP_CUDA_TRY(launch_to_bf16(mt, elementwise_grid(mt), reinterpret_cast<cudaStream_t>(stream)));
+    return GCP_OK;
+}
+
+}  // extern "C"

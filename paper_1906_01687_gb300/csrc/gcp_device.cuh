@@ -1,0 +1,148 @@
+// Device helpers of the sampled-gradient kernels: Philox4x64-10 draws,
+// randi, the elementwise losses, BF16 row loads and the status word.
+//
+// Written for sm_103a.  Shares nothing with any other implementation of the
+// same conventions; the conventions themselves are stated in include/gcp.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/gcp.h"
+
+namespace gcpk {
+
+constexpr int kMaxModes = GCP_MAX_MODES;
+
+// Philox tags (the third counter word)
+constexpr uint64_t kTagUniform = 0, kTagNonzero = 1, kTagZeroCandidate = 2, kTagSemiZero = 3;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplies, key bumped by
+// the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct U64x4 {
+    uint64_t w[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                uint64_t k0, uint64_t k1)
+{
+    constexpr uint64_t kMul0 = 0xD2E7470EE14C6C93ull;
+    constexpr uint64_t kMul1 = 0xCA5A826395121157ull;
+    constexpr uint64_t kWeyl0 = 0x9E3779B97F4A7C15ull;
+    constexpr uint64_t kWeyl1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi0 = __umul64hi(kMul0, c0), lo0 = kMul0 * c0;
+        const uint64_t hi1 = __umul64hi(kMul1, c2), lo1 = kMul1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0;
+        const uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += kWeyl0;
+        k1 += kWeyl1;
+    }
+    return U64x4{{c0, c1, c2, c3}};
+}
+
+// randi(n), 0-based: the high word of word * n.
+__device__ __forceinline__ uint32_t randi32(uint64_t word, uint64_t n)
+{
+    return static_cast<uint32_t>(__umul64hi(word, n));
+}
+__device__ __forceinline__ uint64_t randi64(uint64_t word, uint64_t n) { return __umul64hi(word, n); }
+
+// The D mode indices of draw j in one sampling stream.
+template <int D>
+__device__ __forceinline__ void draw_index(const uint32_t* __restrict__ dims, uint64_t seed, uint64_t problem,
+                                           uint64_t stream, uint64_t tag, uint64_t j, int d_rt,
+                                           uint32_t (&ix)[D])
+{
+    if constexpr (D <= 4) {
+        const U64x4 b = philox4x64_10(j, stream, tag, 0, seed, problem);
+#pragma unroll
+        for (int k = 0; k < D; ++k) ix[k] = randi32(b.w[k], dims[k]);
+    } else {
+        U64x4 b = philox4x64_10(j, stream, tag, 0, seed, problem);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k == 4 && d_rt > 4) b = philox4x64_10(j, stream, tag, 1, seed, problem);
+            ix[k] = k < d_rt ? randi32(b.w[k & 3], dims[k]) : 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Losses: f(x,m) and g(x,m) = df/dm, FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float loss_g(int loss, float x, float m)
+{
+    if (loss == GCP_LOSS_GAUSSIAN) return 2.0f * (m - x);
+    if (loss == GCP_LOSS_BERNOULLI_LOGIT) return 1.0f / (1.0f + expf(-m)) - x;
+    return expf(m) - x;  // Poisson-log
+}
+
+__device__ __forceinline__ float loss_f(int loss, float x, float m)
+{
+    if (loss == GCP_LOSS_GAUSSIAN) {
+        const float r = x - m;
+        return r * r;
+    }
+    if (loss == GCP_LOSS_BERNOULLI_LOGIT) return fmaxf(m, 0.0f) + log1pf(expf(-fabsf(m))) - x * m;
+    return expf(m) - x * m;
+}
+
+// y of a drawn entry: the semi-stratified nonzero subtracts the x = 0 term.
+__device__ __forceinline__ float entry_y(int loss, int cls, float x, float m, float w)
+{
+    float g = loss_g(loss, x, m);
+    if (cls == GCP_CLS_SEMI_NZ) g -= loss_g(loss, 0.0f, m);
+    return w * g;
+}
+
+__device__ __forceinline__ float entry_f(int loss, int cls, float x, float m, float w)
+{
+    float f = loss_f(loss, x, m);
+    if (cls == GCP_CLS_SEMI_NZ) f -= loss_f(loss, 0.0f, m);
+    return w * f;
+}
+
+// ---------------------------------------------------------------------------
+// Row loads: 4 consecutive factor entries as float4 from FP32 (16 B) or
+// BF16 (8 B) storage.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 load4(const float* __restrict__ p)
+{
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* __restrict__ p)
+{
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+    float4 out;
+    out.x = __uint_as_float(raw.x << 16);
+    out.y = __uint_as_float(raw.x & 0xFFFF0000u);
+    out.z = __uint_as_float(raw.y << 16);
+    out.w = __uint_as_float(raw.y & 0xFFFF0000u);
+    return out;
+}
+
+__device__ __forceinline__ float4 mul4(float4 a, float4 b)
+{
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+__device__ __forceinline__ float sum4(float4 a) { return (a.x + a.y) + (a.z + a.w); }
+
+// Sticky status word: keep the first error.
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace gcpk

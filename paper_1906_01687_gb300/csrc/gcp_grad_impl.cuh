@@ -1,0 +1,146 @@
+// The fused sampled-gradient kernel: draw -> gather rows -> m_i -> y_i ->
+// scatter y_i * (Hadamard product of the other modes' rows) into every G_k
+// (Eq. (4.3) computed as in Algs. 1-3, with the model entry and the MTTKRP
+// sharing the gathered rows).
+//
+// Work layout.  A warp takes 32 consecutive draws at a time.  First every
+// lane computes one draw's descriptor (Philox, the nonzero record or the
+// dense value gather): the random DRAM reads of 32 draws are in flight at
+// once.  Then the warp splits into groups of L lanes; a group walks its L
+// draws, each lane holding NC float4 column chunks of every mode's row (so
+// L * NC * 4 >= rank).  m_i is reduced across the group with shuffles; the
+// row updates go either to shared-memory accumulators (modes whose whole G_k
+// fits and is hit often: flushed once per CTA) or straight to global memory
+// with 16-byte vector atomics (red.global.add.v4.f32).
+#pragma once
+
+#include <type_traits>
+
+#include "gcp_draw.cuh"
+
+namespace gcpk {
+
+template <int D, int L, int NC, bool BF16>
+__global__ void __launch_bounds__(256) grad_kernel(const GradArgs a)
+{
+    using T = std::conditional_t<BF16, __nv_bfloat16, float>;
+    extern __shared__ float4 smem4[];
+    float* sG = reinterpret_cast<float*>(smem4);
+    for (int i = threadIdx.x; i < a.smem_floats; i += blockDim.x) sG[i] = 0.0f;
+    __syncthreads();
+
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    const uint64_t stream = read_stream(a.dr);
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const int64_t warp_global = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int d = D <= 4 ? D : a.dr.d;
+    const int ld = a.ld, rank = a.rank;
+
+    // warp-uniform loop over batches of 32 draws
+    for (int64_t wb = warp_global * 32; wb < a.dr.n_total; wb += nwarps * 32) {
+        Draw<D> my;
+        make_draw<D>(a.dr, wb + lane, stream, my);
+#pragma unroll 1
+        for (int b = 0; b < L; ++b) {
+            const int src = gbase + b;
+            uint32_t ix[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) ix[k] = __shfl_sync(kFull, my.ix[k], src);
+            const float x = __shfl_sync(kFull, my.x, src);
+            const float w = __shfl_sync(kFull, my.w, src);
+            const int cls = __shfl_sync(kFull, my.cls, src);
+            const bool valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
+
+            // gather this lane's chunks of the d rows
+            float4 r[D][NC];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T* row = static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int col = (gl * NC + c) * 4;
+                    if (k >= d) {
+                        r[k][c] = make_float4(1.f, 1.f, 1.f, 1.f);
+                    } else if (valid && col < rank) {
+                        r[k][c] = load4(row + col);
+                    } else {
+                        r[k][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+            // m_i = sum_j prod_k A_k(i_k, j)
+            float part = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float4 prod = r[0][c];
+#pragma unroll
+                for (int k = 1; k < D; ++k) prod = mul4(prod, r[k][c]);
+                part += sum4(prod);
+            }
+#pragma unroll
+            for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+            if (!valid) continue;  // no shuffles below this point
+            const float y = entry_y(a.loss, cls, x, part, w);
+
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int col = (gl * NC + c) * 4;
+                if (col >= rank) continue;
+                // leave-one-out products prod_{l != k} A_l(i_l, cols), via prefix and suffix products
+                float4 pre[D], suf[D];
+                pre[0] = make_float4(y, y, y, y);
+#pragma unroll
+                for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], r[k - 1][c]);
+                suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+                for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], r[k + 1][c]);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if (k >= d) continue;
+                    const float4 upd = mul4(pre[k], suf[k]);
+                    if ((a.smem_mask >> k) & 1u) {
+                        float* s = sG + a.smem_off[k] + static_cast<size_t>(ix[k]) * ld + col;
+                        atomicAdd(s + 0, upd.x);
+                        atomicAdd(s + 1, upd.y);
+                        atomicAdd(s + 2, upd.z);
+                        atomicAdd(s + 3, upd.w);
+                    } else {
+                        atomicAdd(reinterpret_cast<float4*>(a.G[k] + static_cast<size_t>(ix[k]) * ld + col), upd);
+                    }
+                }
+            }
+        }
+    }
+
+    if (a.smem_mask == 0) return;
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < d; ++k) {
+        if (!((a.smem_mask >> k) & 1u)) continue;
+        const int n4 = static_cast<int>(a.dr.dims[k]) * ld / 4;
+        const float4* s = reinterpret_cast<const float4*>(sG + a.smem_off[k]);
+        float4* g = reinterpret_cast<float4*>(a.G[k]);
+        for (int e = threadIdx.x; e < n4; e += blockDim.x) {
+            const float4 v = s[e];
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(g + e, v);
+        }
+    }
+}
+
+#define GCP_GRAD_CONFIGS(X) \
+    X(1, 1) X(1, 2) X(1, 3) X(1, 4) X(2, 2) X(4, 1) X(4, 2) X(8, 1) X(8, 2) X(16, 1) X(32, 1) X(32, 2)
+
+template <int D, bool BF16>
+const void* grad_kernel_ptr(int L, int NC)
+{
+#define GCP_CASE(LL, CC) \
+    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16>);
+    GCP_GRAD_CONFIGS(GCP_CASE)
+#undef GCP_CASE
+    return nullptr;
+}
+
+}  // namespace gcpk

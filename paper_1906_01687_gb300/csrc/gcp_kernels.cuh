@@ -1,0 +1,134 @@
+// Kernel argument blocks and the host-side launchers shared by the C ABI
+// (gcp_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gcp.h"
+
+namespace gcpk {
+
+// Where the drawn entries of a gradient come from.
+enum Source : int32_t {
+    kSrcUniformDense = 0,  // Alg. 1 over a dense tensor, generated in-kernel
+    kSrcSparse = 1,        // Algs. 2/3: nonzeros generated in-kernel, zeros generated (semi) or listed (stratified)
+    kSrcList = 2           // a materialised list
+};
+
+struct DrawArgs {
+    int32_t d;
+    int32_t src;
+    int32_t semi;         // kSrcSparse: 1 = semi-stratified, 0 = stratified
+    int32_t rec_int4;     // int4 words per packed nonzero record
+    uint32_t dims[GCP_MAX_MODES];
+    uint64_t strides[GCP_MAX_MODES];  // row-major strides of the linear index
+    int64_t p;            // nonzero draws: j in [0, p)
+    int64_t n_total;      // all draws
+    uint64_t seed, problem, stream;
+    const int64_t* stream_dev;
+    float w_first;        // uniform: omega/s; sparse: eta/p
+    float w_second;       // stratified: zeta/q; semi: omega/q
+    const float* X;       // dense values
+    const int4* nz_rec;   // packed nonzero records
+    int64_t nnz;
+    const int32_t* zidx[GCP_MAX_MODES];  // stratified zero list (scratch)
+    const int64_t* zcount;                // accepted zeros in the list
+    const int32_t* lidx[GCP_MAX_MODES];  // kSrcList
+    const float* lx;
+    const float* lw;
+    const int8_t* lcls;
+};
+
+struct GradArgs {
+    DrawArgs dr;
+    int32_t ld, rank, loss, smem_floats;
+    const void* A[GCP_MAX_MODES];  // float or bf16 rows
+    float* G[GCP_MAX_MODES];
+    uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
+    uint32_t smem_off[GCP_MAX_MODES];
+};
+
+struct LossArgs {
+    DrawArgs dr;  // always kSrcList
+    int32_t ld, rank, loss, pad;
+    const void* A[GCP_MAX_MODES];
+    double* partials;     // one per block
+    unsigned int* ticket; // zero between launches
+    double* out;
+};
+
+struct ModeTable {
+    int32_t d, ld, rank, pad;
+    int64_t off4[GCP_MAX_MODES + 1];  // prefix of n_k * ld / 4
+    float* A[GCP_MAX_MODES];
+    float* B[GCP_MAX_MODES];
+    float* C[GCP_MAX_MODES];
+    float* G[GCP_MAX_MODES];
+    uint16_t* Abf[GCP_MAX_MODES];
+    float* SA[GCP_MAX_MODES];
+    float* SB[GCP_MAX_MODES];
+    float* SC[GCP_MAX_MODES];
+};
+
+struct AdamArgs {
+    ModeTable mt;
+    float beta1, beta2, eps, lower;
+    int32_t eps_inside_sqrt;
+    gcp_adam_state* st;
+};
+
+struct EpochArgs {
+    ModeTable mt;
+    int64_t tau;
+    float nu;
+    int32_t kappa;
+    int32_t begin;  // 1: epoch_begin (snapshot only), 0: epoch_end
+    gcp_adam_state* st;
+};
+
+// Stratified zero sampling (Alg. 2 with the oversampling of Section 4.2).
+struct ZeroArgs {
+    int32_t d;
+    int32_t pad;
+    uint32_t dims[GCP_MAX_MODES];
+    uint64_t strides[GCP_MAX_MODES];
+    uint64_t seed, problem, stream;
+    const int64_t* stream_dev;
+    int64_t q;
+    int64_t first_tiles;      // tiles of 1024 candidates examined in parallel
+    int64_t cap;              // candidates allowed in total (64 batches)
+    const unsigned long long* table;  // nonzero key hash (open addressing)
+    uint64_t table_mask;
+    uint32_t* mask_words;     // accept bits of the parallel pass
+    int32_t* tile_counts;
+    int64_t* tile_offsets;
+    int64_t* count_out;       // accepted zeros kept (<= q)
+    int32_t* status;
+    // destination list (zero draw e goes to slot e)
+    int32_t* out_idx[GCP_MAX_MODES];
+    float* out_x;
+    float* out_w;
+    int8_t* out_cls;
+    float w_zero;
+};
+
+// Launchers (defined in the kernel translation units).
+cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int grid, int block, size_t smem,
+                        cudaStream_t s);
+cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int block, size_t smem, int* blocks_per_sm);
+bool grad_has_config(int D, int L, int NC);
+
+cudaError_t launch_loss(const LossArgs& a, bool bf16, int grid, int block, cudaStream_t s);
+cudaError_t launch_materialise(const DrawArgs& a, int32_t* const idx[GCP_MAX_MODES], float* x, float* w,
+                               int8_t* cls, int64_t first, int64_t count, int32_t* status, cudaStream_t s);
+cudaError_t launch_zero_sampling(const ZeroArgs& a, cudaStream_t s);
+cudaError_t launch_hash_build(const int4* recs, int rec_int4, int d, const uint64_t* strides, int64_t nnz,
+                              unsigned long long* table, uint64_t mask, int32_t* status, cudaStream_t s);
+cudaError_t launch_pack_records(const gcp_tensor& X, int4* recs, int rec_int4, cudaStream_t s);
+cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_epoch(const EpochArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_state_init(gcp_adam_state* st, float alpha, cudaStream_t s);
+cudaError_t launch_to_bf16(const ModeTable& mt, int grid, cudaStream_t s);
+
+}  // namespace gcpk

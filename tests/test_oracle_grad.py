@@ -248,3 +248,27 @@ def test_stratified_variance_below_uniform():
     v_strat = var(oracle.STRATIFIED, Ts, 20, 20)
     v_semi = var(oracle.SEMI_STRATIFIED, Ts, 20, 20)
     assert v_strat < v_uni and v_semi < v_uni, (v_uni, v_strat, v_semi)
+
+
+def test_abs_scales_bound_the_sums():
+    """grad_abs and loss_abs (tolerance scales) dominate |G| and |F-hat| and
+    equal them when every term is nonnegative."""
+    dims = (3, 4, 5)
+    X, A = problem(dims, 2, oracle.GAUSSIAN, 40)
+    S = random_sample_list(dims, X, 60, 41)
+    G = oracle.grad(dims, A, oracle.GAUSSIAN, S)
+    Gabs = oracle.grad_abs(dims, A, oracle.GAUSSIAN, S)
+    for g, ga in zip(G, Gabs):
+        assert np.all(np.abs(g) <= ga + 1e-12)
+    assert oracle.loss_abs(dims, A, oracle.GAUSSIAN, S) >= abs(oracle.loss_estimate(dims, A, oracle.GAUSSIAN, S))
+    Splain = Samples(S.idx, S.x, S.w, np.full(S.n, oracle.CLS_UNIFORM))
+    assert oracle.loss_abs(dims, A, oracle.GAUSSIAN, Splain) == pytest.approx(
+        oracle.loss_estimate(dims, A, oracle.GAUSSIAN, Splain), rel=1e-12)  # Gaussian terms are >= 0
+    Apos = [np.abs(a) for a in A]
+    Spos = Samples(S.idx, S.x, S.w, np.full(S.n, oracle.CLS_UNIFORM))
+    Xbig = X + 100.0
+    Spos.x = Xbig[tuple(S.idx.T)]
+    G = oracle.grad(dims, Apos, oracle.GAUSSIAN, Spos)  # m < x everywhere: every term is negative
+    Gabs = oracle.grad_abs(dims, Apos, oracle.GAUSSIAN, Spos)
+    for g, ga in zip(G, Gabs):
+        np.testing.assert_allclose(-g, ga, rtol=1e-12)
