@@ -212,7 +212,7 @@ def ours_arm(args):
     seed = 1687 + rank
     with torch.cuda.stream(stream):
         run = GcpAdam(XT, A0, gcp.LOSS_GAUSSIAN, gcp.SAMPLER_UNIFORM, 0, S_DRAWS, 0, EST_DRAWS, seed=seed,
-                      est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream)
+                      est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream, autotune=not args.no_autotune)
         run.capture()
     for _ in range(args.warmup):
         run.run_epoch()
@@ -287,9 +287,10 @@ def ours_arm(args):
                        "sampler": "uniform", "samples_per_iter": S_DRAWS, "tau": TAU, "est_samples": EST_DRAWS,
                        "step": "one GCP-Adam epoch (tau iterations + loss estimate + accept/revert), CUDA graph",
                        "l2": "inputs larger than L2 (X = 400 MB, gathered at random)",
-                       "parallelism": f"replicas{world}", "grad_launch": launch},
+                       "parallelism": f"replicas{world}", "grad_launch": launch,
+                       "autotuned": run.tuned},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (2 * TAU + 2),
+            "gpu_launches": args.steps * ((3 if any(r > 1 for r in launch["replicas"]) else 2) * TAU + 2),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "gcp_grad (fused sampled gradient)",
                          "bytes_per_draw": BYTES_PER_DRAW, "draws_per_launch": S_DRAWS,
@@ -315,6 +316,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -249,6 +249,11 @@ gcp_status gcp_reserve(gcp_handle *h, const gcp_sampling *S, gcp_stream_t stream
    stream_dev (device, nullable): if non-NULL the Philox stream word is read
    from *stream_dev on the device at run time instead of S->stream (used by
    graph-replayed epochs with &state->iter).
+   Modes whose rows are hit often accumulate first in library-owned replica
+   slabs that a second kernel folds into G (and re-zeroes); the slabs are
+   allocated on the first call that needs them (cudaMalloc: make that call
+   before any stream capture) and are shared by every call on this handle,
+   so calls on one handle must not overlap on the GPU.
    Errors: GCP_ERR_INVALID_ARG; kernel-side shortfall as in gcp_sample. */
 gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
                     const gcp_sampling *S, const gcp_samples *list,
@@ -315,10 +320,15 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    automatically").  lanes x chunks float4 column chunks cover a row:
    lanes in {1,2,4,8,16,32} lanes per draw, chunks in {1,2,3,4} per lane
    (only compiled pairs are accepted); block threads (multiple of 32, <= 256);
-   grid_blocks CTAs (0 = enough for one resident wave); smem_bytes the
-   shared-memory budget for per-CTA accumulation of small G_k (-1 = default,
-   0 = off); smem_min_hits the least expected draws per row per CTA for a
-   mode to accumulate in shared memory (a tenth of a unit: 10 = 1.0).
+   grid_blocks CTAs (0 = one resident wave, capped by the draws).
+   Accumulation of the row updates, per mode:
+     smem_bytes    shared-memory budget for per-CTA accumulation of small
+                   G_k, flushed once per CTA (-1 or 0 = off);
+     smem_min_hits least expected draws per row per CTA for that (x10);
+     max_replicas  most replica slabs a mode's updates are spread over to
+                   keep same-address contention low (-1 = 32; 0 or 1 = off);
+     replica_target expected updates per 16-byte address per launch above
+                   which a mode is replicated (0 = 64).
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -327,7 +337,20 @@ typedef struct gcp_tuning {
     int32_t grid_blocks;
     int32_t smem_bytes;
     int32_t smem_min_hits;
+    int32_t max_replicas;
+    int32_t replica_target;
 } gcp_tuning;
+
+/* The launch shape gcp_grad chose (gcp_get_launch). */
+typedef struct gcp_launch_info {
+    int32_t lanes;
+    int32_t chunks;
+    int32_t block;
+    int32_t grid_blocks;
+    int32_t smem_bytes;
+    uint32_t smem_mode_mask;
+    int32_t replicas[GCP_MAX_MODES];
+} gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch
    shape.  Errors: GCP_ERR_INVALID_ARG for a shape that is not compiled. */
@@ -335,7 +358,7 @@ gcp_status gcp_set_tuning(gcp_handle *h, const gcp_tuning *t);
 
 /* Reports the launch shape gcp_grad would use for these factors and draw
    count (after automatic choices).  out: host. */
-gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, gcp_tuning *out);
+gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, gcp_launch_info *out);
 
 /* A static string naming a status code. */
 const char *gcp_status_string(gcp_status s);

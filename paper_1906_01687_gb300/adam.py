@@ -26,8 +26,10 @@ class GcpAdam:
                  est_p: int, est_q: int, seed: int, est_seed: int, alpha: float = 0.01, beta1: float = 0.9,
                  beta2: float = 0.999, eps: float = 1e-8, tau: int = 1000, kappa: int = 1, nu: float = 0.1,
                  lower: float = -math.inf, bf16: bool = False, problem: int = 0, oversample: float = 1.1,
-                 handle: Optional[gcp.Handle] = None, eps_inside_sqrt: bool = True, stream=None):
+                 handle: Optional[gcp.Handle] = None, eps_inside_sqrt: bool = True, stream=None,
+                 autotune: bool = False):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.stream.wait_stream(torch.cuda.current_stream())  # X and A0 may come from the current stream
         self.h = handle if handle is not None else gcp.Handle(X, stream=self.stream)
         self.loss = loss
         self.tau, self.kappa, self.nu = int(tau), int(kappa), float(nu)
@@ -48,6 +50,10 @@ class GcpAdam:
         gcp.gcp_epoch_begin(self.F, self.B, self.C, self.SA, self.SB, self.SC, self.state, stream=self.stream)
         self.graph = None
         self.history = []
+        self.tuned = None
+        if autotune:
+            from .autotune import autotune as _autotune
+            self.tuned = _autotune(self.h, self.F, loss, self.spec, stream=self.stream)
 
     # -- one epoch of launches --------------------------------------------
     def iteration(self):
@@ -68,9 +74,10 @@ class GcpAdam:
     def _warm(self):
         """Runs every kernel of an epoch once on throwaway copies, so that no
         kernel is first loaded inside a graph capture."""
-        F = gcp.Factors([a[:, : self.F.rank] for a in self.F.A], bf16=self.F.bf16, device=self.F.A[0].device)
-        G, B, C, SA, SB, SC = (F.like() for _ in range(6))
-        st = gcp.new_state(self.F.A[0].device)
+        with torch.cuda.stream(self.stream):
+            F = gcp.Factors([a[:, : self.F.rank] for a in self.F.A], bf16=self.F.bf16, device=self.F.A[0].device)
+            G, B, C, SA, SB, SC = (F.like() for _ in range(6))
+            st = gcp.new_state(self.F.A[0].device)
         gcp.gcp_state_init(st, 0.0, stream=self.stream)
         gcp.gcp_grad(self.h, F, self.loss, G, S=self.spec, stream_dev=st[3:4], stream=self.stream)
         gcp.gcp_adam_step(F, G, B, C, st, stream=self.stream, **self.adam)

@@ -1,0 +1,80 @@
+"""Autotuner of the fused sampled-gradient launch shape.
+
+For one handle, factor layout and sampling spec, times ``gcp_grad`` for a set
+of candidate shapes -- lanes per draw x float4 chunks per lane (rows per
+warp), threads per block, replica slabs per mode (the pre-reduction width of
+the L2 accumulation) and optional shared-memory accumulation -- with CUDA
+events around back-to-back launches, and keeps the fastest through
+``gcp_set_tuning``.  A shape changes only the summation order of the
+gradient, never the draws.
+"""
+from __future__ import annotations
+
+import statistics
+from typing import Iterable, Optional
+
+import torch
+
+from . import gcp
+
+COMPILED = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (16, 1), (32, 1), (32, 2)]
+
+
+def candidate_shapes(rank: int) -> list:
+    """(lanes, chunks) pairs that cover ceil(rank / 4) chunks without more than
+    doubling the lanes' work."""
+    chunks = (rank + 3) // 4
+    out = []
+    for L, NC in COMPILED:
+        cover = L * NC
+        if cover >= chunks and (cover < 2 * chunks or cover <= 4):
+            out.append((L, NC))
+    return out
+
+
+def candidates(rank: int) -> list:
+    out = []
+    for L, NC in candidate_shapes(rank):
+        for block in (128, 256):
+            for reps, target in ((0, 0), (-1, 0), (8, 128), (32, 16)):
+                out.append(dict(lanes=L, chunks=NC, block=block, max_replicas=reps, replica_target=target))
+        out.append(dict(lanes=L, chunks=NC, block=256, max_replicas=0, smem_bytes=48 * 1024, smem_min_hits=10))
+    return out
+
+
+def time_grad(h, F, loss, spec, launches=20, stream=None) -> float:
+    """Median device time (s) of one gcp_grad call for the current tuning."""
+    stream = stream or torch.cuda.current_stream()
+    G = F.like()
+    with torch.cuda.stream(stream):
+        gcp.gcp_grad(h, F, loss, G, S=spec, stream=stream)  # allocate any workspace outside the timing
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(launches)]
+        torch.cuda._sleep(50_000_000)
+        for i, (a, b) in enumerate(evs):
+            s = gcp.Sampling(spec.kind, spec.p, spec.q, spec.seed, (1 << 62) + i, spec.problem, spec.oversample)
+            a.record(stream)
+            gcp.gcp_grad(h, F, loss, G, S=s, stream=stream)
+            b.record(stream)
+    stream.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
+
+
+def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launches=20, stream=None,
+             log=None) -> dict:
+    """Times every candidate, sets the fastest on the handle, returns it with its time."""
+    best, best_t = None, float("inf")
+    results = []
+    for cfg in configs if configs is not None else candidates(F.rank):
+        try:
+            gcp.gcp_set_tuning(h, **cfg)
+        except gcp.GcpError:
+            continue
+        t = time_grad(h, F, loss, spec, launches, stream)
+        results.append((t, cfg))
+        if log:
+            log(dict(seconds=t, **cfg))
+        if t < best_t:
+            best, best_t = cfg, t
+    gcp.gcp_set_tuning(h, **best)
+    return dict(best=best, seconds=best_t, tried=len(results))

@@ -60,9 +60,11 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
     __shared__ float s_alpha, s_c1, s_c2;
     __shared__ int s_done;
     if (threadIdx.x == 0) {
-        const double t1 = static_cast<double>(a.st->t + 1);
-        s_c1 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta1), t1));
-        s_c2 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta2), t1));
+        // 1 - beta^n = -expm1(n log1p(beta - 1)): accurate to a few FP32 ulps even
+        // for beta near 1 and small n, where 1 - powf(beta, n) would cancel
+        const float n = static_cast<float>(a.st->t + 1);
+        s_c1 = -expm1f(n * log1pf(a.beta1 - 1.0f));
+        s_c2 = -expm1f(n * log1pf(a.beta2 - 1.0f));
         s_alpha = a.st->alpha;
         s_done = a.st->done;
     }

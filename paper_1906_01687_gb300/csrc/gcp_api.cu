@@ -20,7 +20,8 @@ static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
 static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
-static_assert(sizeof(gcp_tuning) == 24, "gcp_tuning layout");
+static_assert(sizeof(gcp_tuning) == 32, "gcp_tuning layout");
+static_assert(sizeof(gcp_launch_info) == 56, "gcp_launch_info layout");
 
 struct gcp_handle {
     gcp_tensor X{};
@@ -48,7 +49,10 @@ struct gcp_handle {
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
     int partials_cap = 0;
-    gcp_tuning tune{0, 0, 0, 0, -1, -1};
+    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0};
+    // replica slabs of the gradient accumulation (kept zero between calls)
+    float* rep_ws = nullptr;
+    int64_t rep_ws_cap = 0;  // floats
 };
 
 namespace {
@@ -279,6 +283,8 @@ struct Shape {
     size_t smem = 0;
     uint32_t mask = 0;
     uint32_t off[GCP_MAX_MODES] = {};
+    uint32_t reps[GCP_MAX_MODES] = {};
+    int64_t rep_floats = 0;  // replica workspace the shape needs
 };
 
 int next_pow2(int v)
@@ -341,8 +347,9 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     const int64_t warps = (n_total + 31) / 32;
     const int64_t blocks_needed = std::max<int64_t>(1, (warps + sh->block / 32 - 1) / (sh->block / 32));
 
-    // shared-memory accumulation of small, often-hit G_k
-    const int64_t budget = t.smem_bytes >= 0 ? t.smem_bytes : 32 * 1024;
+    // shared-memory accumulation of small, often-hit G_k (off unless tuned on:
+    // shared-memory float atomics are slower than L2 vector reductions here)
+    const int64_t budget = t.smem_bytes > 0 ? t.smem_bytes : 0;
     const double min_hits = t.smem_min_hits >= 0 ? t.smem_min_hits / 10.0 : 2.0;
     const int64_t grid0 = std::min<int64_t>(blocks_needed, static_cast<int64_t>(h->num_sms) * 4);
     const double draws_per_cta = static_cast<double>(n_total) / static_cast<double>(std::max<int64_t>(grid0, 1));
@@ -360,6 +367,21 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->block, sh->smem, h->device);
     const int64_t resident = static_cast<int64_t>(h->num_sms) * bps;
     sh->grid = static_cast<int>(t.grid_blocks > 0 ? t.grid_blocks : std::min<int64_t>(blocks_needed, resident));
+
+    // replica slabs for modes whose rows each receive many updates per launch
+    const int64_t max_reps = t.max_replicas >= 0 ? t.max_replicas : 32;
+    const double target = t.replica_target > 0 ? t.replica_target : 64.0;
+    sh->rep_floats = 0;
+    for (int k = 0; k < d; ++k) {
+        int64_t r = 1;
+        if (!((sh->mask >> k) & 1u)) {
+            const double hits = static_cast<double>(n_total) / static_cast<double>(h->X.dims[k]);
+            r = static_cast<int64_t>(std::ceil(hits / target));
+            r = std::max<int64_t>(1, std::min<int64_t>({r, max_reps, static_cast<int64_t>(sh->grid)}));
+        }
+        sh->reps[k] = static_cast<uint32_t>(r);
+        if (r > 1) sh->rep_floats += r * h->X.dims[k] * F->ld;
+    }
     return GCP_OK;
 }
 
@@ -517,6 +539,7 @@ gcp_status gcp_destroy(gcp_handle* h)
     cudaFree(h->tile_offsets);
     cudaFree(h->partials);
     cudaFree(h->ticket);
+    cudaFree(h->rep_ws);
     delete h;
     return GCP_OK;
 }
@@ -536,17 +559,18 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     if (!t) {
-        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1};
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0};
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1)) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
-    if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024) return GCP_ERR_INVALID_ARG;
+    if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0)
+        return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
 }
 
-gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, gcp_tuning* out)
+gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, gcp_launch_info* out)
 {
     if (!h || !out || n_draws < 0) return GCP_ERR_INVALID_ARG;
     gcp_status st = check_factors(h, F);
@@ -554,12 +578,14 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     Shape sh;
     st = choose_shape(h, F, n_draws, &sh);
     if (st != GCP_OK) return st;
+    *out = gcp_launch_info{};
     out->lanes = sh.L;
     out->chunks = sh.NC;
     out->block = sh.block;
     out->grid_blocks = sh.grid;
     out->smem_bytes = static_cast<int32_t>(sh.smem);
-    out->smem_min_hits = static_cast<int32_t>(sh.mask);  // reports the shared-memory mode mask
+    out->smem_mode_mask = sh.mask;
+    for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
 
@@ -631,17 +657,48 @@ gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gc
     Shape sh;
     st = choose_shape(h, F, a.dr.n_total, &sh);
     if (st != GCP_OK) return st;
+    if (sh.rep_floats > h->rep_ws_cap) {
+        cudaFree(h->rep_ws);
+        h->rep_ws = nullptr;
+        h->rep_ws_cap = 0;
+        GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->rep_ws), static_cast<size_t>(sh.rep_floats) * sizeof(float)));
+        GCP_CUDA_TRY(cudaMemsetAsync(h->rep_ws, 0, static_cast<size_t>(sh.rep_floats) * sizeof(float), s));
+        h->rep_ws_cap = sh.rep_floats;
+    }
     a.ld = F->ld;
     a.rank = F->rank;
     a.loss = loss;
     a.smem_floats = static_cast<int32_t>(sh.smem / 4);
     a.smem_mask = sh.mask;
+    FoldArgs fold{};
+    int64_t ws_off = 0;
+    for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
     for (int k = 0; k < h->X.d; ++k) {
         a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);
-        a.G[k] = G[k];
         a.smem_off[k] = sh.off[k];
+        a.reps[k] = sh.reps[k];
+        const int64_t slab = h->X.dims[k] * F->ld;
+        if (sh.reps[k] > 1) {
+            a.G[k] = h->rep_ws + ws_off;
+            a.rep_stride[k] = static_cast<uint64_t>(slab);
+            const int m = fold.nmodes++;
+            fold.R[m] = h->rep_ws + ws_off;
+            fold.G[m] = G[k];
+            fold.reps[m] = sh.reps[k];
+            fold.rep_stride4[m] = static_cast<uint64_t>(slab / 4);
+            fold.off4[m + 1] = fold.off4[m] + slab / 4;
+            ws_off += slab * sh.reps[k];
+        } else {
+            a.G[k] = G[k];
+            a.rep_stride[k] = 0;
+        }
     }
     GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.grid, sh.block, sh.smem, s));
+    if (fold.nmodes > 0) {
+        const int64_t total4 = fold.off4[fold.nmodes];
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total4 + 255) / 256, int64_t(h->num_sms) * 8)));
+        GCP_CUDA_TRY(launch_fold(fold, grid, s));
+    }
     return GCP_OK;
 }
 

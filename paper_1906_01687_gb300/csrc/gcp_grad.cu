@@ -43,4 +43,35 @@ cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int 
     return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
 }
 
+__global__ void __launch_bounds__(256) fold_kernel(const FoldArgs a)
+{
+    const int64_t total4 = a.off4[a.nmodes];
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
+        int m = 0;
+#pragma unroll
+        for (int l = 1; l < GCP_MAX_MODES; ++l)
+            if (l < a.nmodes && i4 >= a.off4[l]) m = l;
+        const int64_t loc = i4 - a.off4[m];
+        float4* g = reinterpret_cast<float4*>(a.G[m]) + loc;
+        float4* r = reinterpret_cast<float4*>(a.R[m]) + loc;
+        float4 acc = *g;
+        for (uint32_t k = 0; k < a.reps[m]; ++k) {
+            const float4 v = r[k * a.rep_stride4[m]];
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+            r[k * a.rep_stride4[m]] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        *g = acc;
+    }
+}
+
+cudaError_t launch_fold(const FoldArgs& a, int grid, cudaStream_t s)
+{
+    fold_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace gcpk

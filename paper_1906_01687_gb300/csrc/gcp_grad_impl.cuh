@@ -11,7 +11,10 @@
 // L * NC * 4 >= rank).  m_i is reduced across the group with shuffles; the
 // row updates go either to shared-memory accumulators (modes whose whole G_k
 // fits and is hit often: flushed once per CTA) or straight to global memory
-// with 16-byte vector atomics (red.global.add.v4.f32).
+// with 16-byte vector atomics (red.global.add.v4.f32).  A mode whose rows
+// are hit many times per launch adds into one of several replica slabs
+// (CTA b into replica b % reps), which keeps same-address contention at L2
+// low; a fold kernel then sums the replicas into G_k.
 #pragma once
 
 #include <type_traits>
@@ -21,7 +24,7 @@
 namespace gcpk {
 
 template <int D, int L, int NC, bool BF16>
-__global__ void __launch_bounds__(256) grad_kernel(const GradArgs a)
+__global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradArgs a)
 {
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
@@ -54,30 +57,29 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs a)
             const int cls = __shfl_sync(kFull, my.cls, src);
             const bool valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
 
-            // gather this lane's chunks of the d rows
-            float4 r[D][NC];
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const T* row = static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int col = (gl * NC + c) * 4;
-                    if (k >= d) {
-                        r[k][c] = make_float4(1.f, 1.f, 1.f, 1.f);
-                    } else if (valid && col < rank) {
-                        r[k][c] = load4(row + col);
-                    } else {
-                        r[k][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-            }
-            // m_i = sum_j prod_k A_k(i_k, j)
+            // m_i = sum_j prod_k A_k(i_k, j) over this lane's chunks of the d rows.
+            // With one chunk per lane the rows stay in registers for the scatter;
+            // with several they are re-read there (L1 hits) to keep registers low.
+            constexpr bool kKeep = NC == 1;
+            float4 r[D][kKeep ? 1 : 1];
             float part = 0.0f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                float4 prod = r[0][c];
+                const int col = (gl * NC + c) * 4;
+                float4 prod = make_float4(1.f, 1.f, 1.f, 1.f);
 #pragma unroll
-                for (int k = 1; k < D; ++k) prod = mul4(prod, r[k][c]);
+                for (int k = 0; k < D; ++k) {
+                    float4 v;
+                    if (k >= d) {
+                        v = make_float4(1.f, 1.f, 1.f, 1.f);
+                    } else if (valid && col < rank) {
+                        v = load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col);
+                    } else {
+                        v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    if (kKeep) r[k][0] = v;
+                    prod = mul4(prod, v);
+                }
                 part += sum4(prod);
             }
 #pragma unroll
@@ -89,14 +91,21 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs a)
             for (int c = 0; c < NC; ++c) {
                 const int col = (gl * NC + c) * 4;
                 if (col >= rank) continue;
+                float4 rc[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if (kKeep) rc[k] = r[k][0];
+                    else rc[k] = k < d ? load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col)
+                                       : make_float4(1.f, 1.f, 1.f, 1.f);
+                }
                 // leave-one-out products prod_{l != k} A_l(i_l, cols), via prefix and suffix products
                 float4 pre[D], suf[D];
                 pre[0] = make_float4(y, y, y, y);
 #pragma unroll
-                for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], r[k - 1][c]);
+                for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
                 suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
 #pragma unroll
-                for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], r[k + 1][c]);
+                for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     if (k >= d) continue;
@@ -108,7 +117,8 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs a)
                         atomicAdd(s + 2, upd.z);
                         atomicAdd(s + 3, upd.w);
                     } else {
-                        atomicAdd(reinterpret_cast<float4*>(a.G[k] + static_cast<size_t>(ix[k]) * ld + col), upd);
+                        float* gk = a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k];
+                        atomicAdd(reinterpret_cast<float4*>(gk + static_cast<size_t>(ix[k]) * ld + col), upd);
                     }
                 }
             }
@@ -122,7 +132,7 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs a)
         if (!((a.smem_mask >> k) & 1u)) continue;
         const int n4 = static_cast<int>(a.dr.dims[k]) * ld / 4;
         const float4* s = reinterpret_cast<const float4*>(sG + a.smem_off[k]);
-        float4* g = reinterpret_cast<float4*>(a.G[k]);
+        float4* g = reinterpret_cast<float4*>(a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k]);
         for (int e = threadIdx.x; e < n4; e += blockDim.x) {
             const float4 v = s[e];
             if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(g + e, v);

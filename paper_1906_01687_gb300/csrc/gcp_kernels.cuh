@@ -44,9 +44,22 @@ struct GradArgs {
     DrawArgs dr;
     int32_t ld, rank, loss, smem_floats;
     const void* A[GCP_MAX_MODES];  // float or bf16 rows
-    float* G[GCP_MAX_MODES];
+    float* G[GCP_MAX_MODES];       // destination of mode k: the caller's G_k or a replica slab
+    uint32_t reps[GCP_MAX_MODES];  // replicas of mode k's destination (CTA b adds into replica b % reps)
+    uint64_t rep_stride[GCP_MAX_MODES];  // floats between replicas
     uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
     uint32_t smem_off[GCP_MAX_MODES];
+};
+
+// Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).
+struct FoldArgs {
+    int32_t nmodes;
+    int32_t pad;
+    int64_t off4[GCP_MAX_MODES + 1];  // prefix of the folded modes' float4 counts
+    uint32_t reps[GCP_MAX_MODES];
+    uint64_t rep_stride4[GCP_MAX_MODES];
+    float* R[GCP_MAX_MODES];
+    float* G[GCP_MAX_MODES];
 };
 
 struct LossArgs {
@@ -119,6 +132,7 @@ cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int 
 cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int block, size_t smem, int* blocks_per_sm);
 bool grad_has_config(int D, int L, int NC);
 
+cudaError_t launch_fold(const FoldArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_loss(const LossArgs& a, bool bf16, int grid, int block, cudaStream_t s);
 cudaError_t launch_materialise(const DrawArgs& a, int32_t* const idx[GCP_MAX_MODES], float* x, float* w,
                                int8_t* cls, int64_t first, int64_t count, int32_t* status, cudaStream_t s);

@@ -69,7 +69,14 @@ class gcp_epoch_params(ctypes.Structure):
 
 class gcp_tuning(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("chunks", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_min_hits", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_min_hits", ctypes.c_int32),
+                ("max_replicas", ctypes.c_int32), ("replica_target", ctypes.c_int32)]
+
+
+class gcp_launch_info(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("chunks", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_mode_mask", ctypes.c_uint32),
+                ("replicas", ctypes.c_int32 * MAX_MODES)]
 
 
 _i32, _i64 = ctypes.c_int32, ctypes.c_int64
@@ -82,7 +89,7 @@ _SIGS = {
     "gcp_destroy": ([_vp], ctypes.c_int),
     "gcp_get_device_status": ([_vp, _P(_i32)], ctypes.c_int),
     "gcp_set_tuning": ([_vp, _P(gcp_tuning)], ctypes.c_int),
-    "gcp_get_launch": ([_vp, _P(gcp_factors), _i64, _P(gcp_tuning)], ctypes.c_int),
+    "gcp_get_launch": ([_vp, _P(gcp_factors), _i64, _P(gcp_launch_info)], ctypes.c_int),
     "gcp_sample": ([_vp, _P(gcp_sampling), _P(gcp_samples), _vp], ctypes.c_int),
     "gcp_reserve": ([_vp, _P(gcp_sampling), _vp], ctypes.c_int),
     "gcp_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _P(gcp_samples), _vp, _P8, _vp], ctypes.c_int),
@@ -317,20 +324,31 @@ def gcp_get_device_status(h: Handle) -> int:
     return int(v.value)
 
 
-def gcp_set_tuning(h: Handle, lanes=0, chunks=0, block=0, grid_blocks=0, smem_bytes=-1, smem_min_hits=-1,
-                   reset=False):
+TUNING_FIELDS = ("lanes", "chunks", "block", "grid_blocks", "smem_bytes", "smem_min_hits", "max_replicas",
+                 "replica_target")
+TUNING_DEFAULT = dict(lanes=0, chunks=0, block=0, grid_blocks=0, smem_bytes=-1, smem_min_hits=-1,
+                      max_replicas=-1, replica_target=0)
+
+
+def gcp_set_tuning(h: Handle, reset: bool = False, **kw):
+    """Sets the handle's launch shape (fields of gcp_tuning; missing = automatic)."""
     if reset:
         _check(_lib.gcp_set_tuning(h.ptr, None), "gcp_set_tuning")
         return
-    t = gcp_tuning(lanes, chunks, block, grid_blocks, smem_bytes, smem_min_hits)
+    vals = dict(TUNING_DEFAULT)
+    for k, v in kw.items():
+        if k not in vals:
+            raise TypeError(f"unknown tuning field {k}")
+        vals[k] = int(v)
+    t = gcp_tuning(*[vals[f] for f in TUNING_FIELDS])
     _check(_lib.gcp_set_tuning(h.ptr, ctypes.byref(t)), "gcp_set_tuning")
 
 
 def gcp_get_launch(h: Handle, F: Factors, n_draws: int) -> dict:
-    t = gcp_tuning()
+    t = gcp_launch_info()
     _check(_lib.gcp_get_launch(h.ptr, ctypes.byref(F._c()), int(n_draws), ctypes.byref(t)), "gcp_get_launch")
     return dict(lanes=t.lanes, chunks=t.chunks, block=t.block, grid_blocks=t.grid_blocks,
-                smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_min_hits)
+                smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_mode_mask, replicas=list(t.replicas)[: h.d])
 
 
 def gcp_sample(h: Handle, S: Sampling, out: Optional[SampleList] = None, stream=None) -> SampleList:

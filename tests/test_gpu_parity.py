@@ -210,10 +210,10 @@ def test_every_launch_shape_agrees():
         SO = oracle.sample(XO, oracle.UNIFORM, 0, 5003, 3, 1)
         ref = oracle.grad(dims, f64(A), 0, SO)
         for (lanes, chunks) in shapes:
-            for smem in (0, -1, 65536):
+            for acc in (dict(max_replicas=0), dict(), dict(max_replicas=8, replica_target=1),
+                        dict(max_replicas=0, smem_bytes=65536, smem_min_hits=0)):
                 for grid in (0, 3):
-                    g.gcp_set_tuning(h, lanes=lanes, chunks=chunks, smem_bytes=smem, grid_blocks=grid,
-                                     smem_min_hits=0 if smem else -1)
+                    g.gcp_set_tuning(h, lanes=lanes, chunks=chunks, grid_blocks=grid, **acc)
                     G = run_grad(h, F, 0, S=S)
                     assert_grad_close(grad_to_numpy(G, rank), ref)
         g.gcp_set_tuning(h, reset=True)
@@ -283,3 +283,20 @@ def test_loss_estimate(kind, loss):
     g.gcp_loss_est(h, F, loss, L, out2)
     torch.cuda.synchronize()
     assert out2.item() == out.item()
+
+
+def test_autotuner_keeps_results():
+    """The autotuner picks a shape; the tuned gradient still matches the oracle."""
+    from paper_1906_01687_gb300.autotune import autotune
+    g = gcp()
+    dims = (40, 50, 60)
+    X, XT, XO = dense_case(dims, 22)
+    h = g.Handle(XT)
+    A = rng_factors(dims, 10, 23, scale=0.6)
+    F = g.Factors(A)
+    S = g.Sampling(g.SAMPLER_UNIFORM, 0, 20000, seed=2, stream=4)
+    res = autotune(h, F, 0, S, launches=3)
+    assert res["tried"] > 4 and res["seconds"] > 0
+    G = run_grad(h, F, 0, S=S)
+    SO = oracle.sample(XO, oracle.UNIFORM, 0, 20000, 2, 4)
+    assert_grad_close(grad_to_numpy(G, 10), oracle.grad(dims, f64(A), 0, SO))
