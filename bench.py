@@ -174,23 +174,20 @@ def reference_arm(args):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
-def time_grad_kernel(torch, gcp, h, F, G, spec, stream, launches=200):
-    """Average device duration of one gradient launch, from CUDA events on the
-    launching stream around each launch, all queued behind a sleep so that
-    the launches run back to back."""
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(launches)]
+def time_grad_kernel(torch, gcp, run, stream, launches=200):
+    """Average device duration of the fused-gradient kernel: the library
+    records CUDA events on the launching stream around each kernel launch of
+    `launches` GCP-Adam iterations, queued behind a sleep so that they run
+    back to back as in the replayed epochs."""
+    gcp.gcp_profile(run.h, True, launches)
     with torch.cuda.stream(stream):
         torch.cuda._sleep(200_000_000)
-        for i, (a, b) in enumerate(evs):
-            s = gcp.Sampling(spec.kind, spec.p, spec.q, spec.seed, 10_000 + i, spec.problem, spec.oversample)
-            a.record(stream)
-            gcp.gcp_grad(h, F, gcp.LOSS_GAUSSIAN, G, S=s, stream=stream)
-            b.record(stream)
+        for _ in range(launches):
+            run.iteration()
     stream.synchronize()
-    times = [a.elapsed_time(b) for a, b in evs]
-    for g in G:
-        g.zero_()
-    return statistics.mean(times) * 1e-3, statistics.median(times) * 1e-3
+    ms, n = gcp.gcp_profile_read(run.h)
+    gcp.gcp_profile(run.h, False)
+    return ms * 1e-3 / n, n
 
 
 def ours_arm(args):
@@ -212,7 +209,11 @@ def ours_arm(args):
     seed = 1687 + rank
     with torch.cuda.stream(stream):
         run = GcpAdam(XT, A0, gcp.LOSS_GAUSSIAN, gcp.SAMPLER_UNIFORM, 0, S_DRAWS, 0, EST_DRAWS, seed=seed,
-                      est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream, autotune=not args.no_autotune)
+                      est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream,
+                      autotune=not (args.no_autotune or args.tuning))
+        if args.tuning:
+            gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
+            run.tuned = {"best": json.loads(args.tuning), "given": True}
         run.capture()
     for _ in range(args.warmup):
         run.run_epoch()
@@ -271,8 +272,7 @@ def ours_arm(args):
     e2e_value = entries / e2e_elapsed
 
     # the dominant kernel (the fused sampled gradient), timed alone
-    G = run.F.like()
-    mean_s, median_s = time_grad_kernel(torch, gcp, run.h, run.F, G, run.spec, stream)
+    mean_s, n_timed = time_grad_kernel(torch, gcp, run, stream)
     peak, peak_kind = peaks()
     achieved = BYTES_PER_DRAW * S_DRAWS / mean_s / 1e9
     launch = gcp.gcp_get_launch(run.h, run.F, S_DRAWS)
@@ -290,15 +290,18 @@ def ours_arm(args):
                        "parallelism": f"replicas{world}", "grad_launch": launch,
                        "autotuned": run.tuned},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * ((3 if any(r > 1 for r in launch["replicas"]) else 2) * TAU + 2),
+            "gpu_launches": args.steps * (2 * TAU + 2),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "gcp_grad (fused sampled gradient)",
+                         "frac": achieved / peak, "traffic": None, "kernel": "grad_kernel (fused sample/gather/model/derivative/MTTKRP scatter)",
                          "bytes_per_draw": BYTES_PER_DRAW, "draws_per_launch": S_DRAWS,
-                         "launch_us_mean": mean_s * 1e6, "launch_us_median": median_s * 1e6,
+                         "launch_us_mean": mean_s * 1e6, "launches_timed": n_timed,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "final_state": {k: st[k] for k in ("F", "t", "iter", "alpha", "bad")}}
     clocks = clk.summary()
     line["clocks"] = clocks
+    if not args.no_forms:
+        line["forms"] = {"bf16": forms_bf16(torch, gcp, synth, stream),
+                         "batched": forms_batched(torch, gcp, synth, stream)}
     if not args.no_cpu_baseline:
         rate, sample = oracle_epoch_rate(oracle_tensor(X32), A0, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -306,6 +309,125 @@ def ours_arm(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the other forms, each beside the plain FP32 single-problem path
+# ---------------------------------------------------------------------------
+
+def _time_calls(torch, fn, stream, reps):
+    """Median device time of fn() from CUDA events around each call, queued behind a sleep."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(100_000_000)
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+    stream.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
+
+
+def forms_bf16(torch, gcp, synth, stream):
+    """FP32 vs BF16 factor storage on the count tensor (6186x24x77x32, 5.33M
+    nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): gradient
+    throughput and error against the FP64 oracle on the same draws."""
+    import oracle
+    from paper_1906_01687_gb300.autotune import autotune
+    dims = (6186, 24, 77, 32)
+    idx, vals, _ = synth.count_tensor()
+    h = gcp.Handle(gcp.DataTensor.coo(dims, idx, vals))
+    A = [(a * 0.3).astype(np.float32) for a in synth.initial_guess(dims, 10, 4, positive=True)]
+    spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, 100_000, 100_000, 1687, 0)
+    XO = oracle.Tensor(dims, coo=np.stack([i.astype(np.int64) for i in idx], axis=1), vals=vals.astype(np.float64))
+    SO = oracle.sample(XO, oracle.STRATIFIED, 100_000, 100_000, 1687, 0)
+    ref = oracle.grad(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SO)
+    out = {"workload": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
+           "metric": "entries/s of gcp_grad (zero pass + gradient)"}
+    for name, bf16 in (("fp32", False), ("bf16", True)):
+        F = gcp.Factors(A, bf16=bf16)
+        autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream)
+        G = F.like()
+        t = _time_calls(torch, lambda: gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream), stream, 50)
+        for x in G:
+            x.zero_()
+        gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream)
+        stream.synchronize()
+        got = [x[:, :10].double().cpu().numpy() for x in G]
+        err = math.sqrt(sum(np.linalg.norm(a - b) ** 2 for a, b in zip(got, ref)) /
+                        sum(np.linalg.norm(b) ** 2 for b in ref))
+        out[name] = {"value": 200_000 / t, "us_per_call": t * 1e6, "grad_rel_err_vs_fp64_oracle": err}
+    out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
+    return out
+
+
+def forms_batched(torch, gcp, synth, stream, tau=20, epochs=3):
+    """64 independent dense problems (d in {3,4}, dims U[50,2000] with at most
+    2e7 entries, ranks {4,8,16,32,64}, mixed losses, 1e4-1e5 draws/iteration):
+    one batched launch per step under one CUDA graph, against the same 64
+    problems run one after another (each its own graph-replayed epoch)."""
+    from paper_1906_01687_gb300.adam import GcpAdam
+    from paper_1906_01687_gb300.batch import GcpAdamBatch
+    shapes = synth.batched_problems()
+    specs = []
+    gen = torch.Generator(device="cuda")
+    for i, sh in enumerate(shapes):
+        gen.manual_seed(1911 + i)
+        d, r = len(sh["dims"]), sh["rank"]
+        fac = [torch.randn((n, r), generator=gen, device="cuda") * (1.0 / r) ** (1.0 / (2 * d)) for n in sh["dims"]]
+        letters = "ijkl"[:d]
+        M = torch.einsum(",".join(f"{c}z" for c in letters) + "->" + letters, *fac)
+        if sh["loss"] == "gaussian":
+            X = M + 0.1 * torch.randn(M.shape, generator=gen, device="cuda")
+        elif sh["loss"] == "bernoulli_logit":
+            X = (torch.rand(M.shape, generator=gen, device="cuda") < torch.sigmoid(M)).float()
+        else:
+            X = torch.poisson(torch.exp(M.clamp(max=10.0)), generator=gen)
+        X = gcp.DataTensor(tuple(sh["dims"]), vals=X.reshape(-1).contiguous())
+        A0 = synth.initial_guess(sh["dims"], r, 500 + i, target_norm=float(torch.linalg.vector_norm(X.vals)))
+        specs.append(dict(X=X, A0=A0, loss=gcp.LOSSES[sh["loss"]], s=sh["s"], est=10_000, seed=1687 + i,
+                          est_seed=7, problem=i))
+    draws = sum(sp["s"] for sp in specs)
+    torch.cuda.synchronize()
+    batch = GcpAdamBatch(specs, tau=tau, alpha=1e-3, kappa=1_000_000, stream=stream, autotune=True)
+    batch.capture()
+    batch.run_epoch()
+    stream.synchronize()
+    t_batch = _time_calls(torch, batch.run_epoch, stream, epochs)
+    singles = []
+    for i, sp in enumerate(specs):
+        run = GcpAdam(sp["X"], sp["A0"], sp["loss"], gcp.SAMPLER_UNIFORM, 0, sp["s"], 0, sp["est"], seed=sp["seed"],
+                      est_seed=7, alpha=1e-3, tau=tau, kappa=1_000_000, problem=i, stream=stream)
+        run.capture()
+        singles.append(run)
+    for run in singles:
+        run.run_epoch()
+    stream.synchronize()
+    t_seq = _time_calls(torch, lambda: [run.run_epoch() for run in singles], stream, epochs)
+    # accuracy: after the same number of epochs, each batched problem vs its single run
+    errs = []
+    batch2 = GcpAdamBatch(specs, tau=tau, alpha=1e-3, kappa=1_000_000, stream=stream)
+    for _ in range(2):
+        batch2.run_epoch()
+    for i in range(0, len(specs), 8):
+        single = GcpAdam(specs[i]["X"], specs[i]["A0"], specs[i]["loss"], gcp.SAMPLER_UNIFORM, 0, specs[i]["s"], 0,
+                         specs[i]["est"], seed=specs[i]["seed"], est_seed=7, alpha=1e-3, tau=tau, kappa=1_000_000,
+                         problem=i, stream=stream)
+        single.run_epoch()
+        single.run_epoch()
+        a, b = batch2.factors(i), single.factors()
+        errs.append(math.sqrt(sum(np.linalg.norm(x - y) ** 2 for x, y in zip(a, b)) /
+                              sum(np.linalg.norm(y) ** 2 for y in b)))
+    entries = tau * draws
+    return {"workload": f"64 dense problems, d 3-4, dims 50-2000 (<= 2e7 entries), ranks 4-64, mixed losses, "
+                        f"{draws} draws/iteration in total, tau {tau}",
+            "metric": "sampled-gradient entries/s over one epoch (all problems)",
+            "batched": {"value": entries / t_batch, "ms_per_epoch": t_batch * 1e3, "launches_per_iteration": 2,
+                        "tuning": batch.tuned},
+            "sequential": {"value": entries / t_seq, "ms_per_epoch": t_seq * 1e3,
+                           "launches_per_iteration": 2 * len(specs)},
+            "batched_over_sequential": t_seq / t_batch,
+            "factor_rel_diff_vs_single_runs_after_2_epochs_max": max(errs)}
 
 
 def main():
@@ -317,6 +439,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form comparisons")
+    ap.add_argument("--tuning", default=None, help="JSON gcp_tuning fields to use instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

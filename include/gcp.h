@@ -291,6 +291,18 @@ gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
                          float *const C[GCP_MAX_MODES], const gcp_adam_params *prm,
                          gcp_adam_state *state, gcp_stream_t stream);
 
+/* One GCP-Adam iteration (Alg. 4, inner loop body): the sampled gradient of
+   gcp_grad for spec S (with stream_dev as there) followed by the Adam step
+   of gcp_adam_step, fused so that replica slabs of the gradient are folded
+   inside the Adam kernel (two kernel launches per iteration, three with a
+   stratified spec's zero pass counted as one).  G must be zero on entry and
+   is left zero; B, C, state as for gcp_adam_step.  Same results as
+   gcp_grad followed by gcp_adam_step up to the summation order. */
+gcp_status gcp_iteration(gcp_handle *h, const gcp_factors *F, gcp_loss loss, const gcp_sampling *S,
+                         const int64_t *stream_dev, float *const G[GCP_MAX_MODES], float *const B[GCP_MAX_MODES],
+                         float *const C[GCP_MAX_MODES], const gcp_adam_params *prm, gcp_adam_state *state,
+                         gcp_stream_t stream);
+
 /* Saves the epoch-start copy of {A, B, C} into {SA, SB, SC} (same layouts)
    and sets F_old = F (the "save copies" step that opens each epoch of
    Alg. 4).  Call once after the first loss estimate. */
@@ -311,6 +323,68 @@ gcp_status gcp_epoch_end(const gcp_factors *F, int32_t d, const int64_t *dims,
                          float *const SA[GCP_MAX_MODES], float *const SB[GCP_MAX_MODES],
                          float *const SC[GCP_MAX_MODES], const gcp_epoch_params *ep,
                          gcp_adam_state *state, gcp_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many independent decompositions (multi-start runs, uneven  */
+/* shapes, ranks and losses) advanced together, one kernel launch per step  */
+/* for all of them.  Alg. 4 run per problem; no data crosses problems.      */
+/* ------------------------------------------------------------------------ */
+
+/* One problem of a batch.  X dense (uniform sampling, Alg. 1) with d <= 4;
+   F as for gcp_grad (bf16 allowed); S a uniform spec whose q draws are taken
+   per iteration and whose seed and problem words key the Philox draws (the
+   stream word is read from state->iter on the device); est the problem's
+   fixed loss-estimate list; G, B, C, SA, SB, SC the gradient, moments and
+   epoch snapshots with F's layout (G zero on entry); state its optimizer
+   state.  All device memory is caller-owned and must outlive the batch. */
+typedef struct gcp_batch_problem {
+    gcp_tensor X;
+    gcp_factors F;
+    int32_t loss;
+    int32_t reserved;
+    gcp_sampling S;
+    gcp_samples est;
+    float *G[GCP_MAX_MODES];
+    float *B[GCP_MAX_MODES];
+    float *C[GCP_MAX_MODES];
+    float *SA[GCP_MAX_MODES];
+    float *SB[GCP_MAX_MODES];
+    float *SC[GCP_MAX_MODES];
+    gcp_adam_params adam;
+    gcp_epoch_params epoch;
+    gcp_adam_state *state;
+} gcp_batch_problem;
+
+typedef struct gcp_batch gcp_batch; /* opaque: the device-side problem table */
+
+/* Validates count problems (host array) and uploads their table to device
+   memory owned by the batch (cudaMalloc; waits for the stream).  Errors:
+   GCP_ERR_INVALID_ARG for any invalid problem (sparse X, d > 4, a
+   non-uniform spec, misaligned pointers), GCP_ERR_NO_MEMORY. */
+gcp_status gcp_batch_create(gcp_batch **out, const gcp_batch_problem *problems, int32_t count, gcp_stream_t stream);
+gcp_status gcp_batch_destroy(gcp_batch *b);
+
+/* Launch shape of the batched gradient: threads per block (multiple of 32,
+   <= 256; 0 = 256) and blocks (0 = one resident wave). */
+gcp_status gcp_batch_set_tuning(gcp_batch *b, int32_t block, int32_t grid_blocks);
+
+/* The sampled gradients of every problem (Eq. (4.3), Alg. 1), one launch:
+   warps take 32 consecutive draws of one problem at a time from a table of
+   all problems' draws. */
+gcp_status gcp_batch_grad(gcp_batch *b, gcp_stream_t stream);
+
+/* The Adam step of every problem (as gcp_adam_step), one launch. */
+gcp_status gcp_batch_adam_step(gcp_batch *b, gcp_stream_t stream);
+
+/* gcp_batch_grad then gcp_batch_adam_step. */
+gcp_status gcp_batch_iteration(gcp_batch *b, gcp_stream_t stream);
+
+/* Every problem's F-hat on its fixed list into its state->F (FP64), one launch. */
+gcp_status gcp_batch_loss_est(gcp_batch *b, gcp_stream_t stream);
+
+/* gcp_epoch_begin / gcp_epoch_end for every problem, one launch each. */
+gcp_status gcp_batch_epoch_begin(gcp_batch *b, gcp_stream_t stream);
+gcp_status gcp_batch_epoch_end(gcp_batch *b, gcp_stream_t stream);
 
 /* Rounds A[k] into A_bf16[k] (round to nearest even) for every mode. */
 gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *dims,
@@ -359,6 +433,17 @@ gcp_status gcp_set_tuning(gcp_handle *h, const gcp_tuning *t);
 /* Reports the launch shape gcp_grad would use for these factors and draw
    count (after automatic choices).  out: host. */
 gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, gcp_launch_info *out);
+
+/* Kernel timing for benchmarks.  With enable = 1 the handle creates
+   capacity pairs of CUDA events (at most 65536; allocation, so call it
+   outside stream capture) and records one pair on the launching stream
+   around every fused-gradient kernel launch that follows (gcp_grad,
+   gcp_iteration), until the pairs are used up; enable = 0 destroys them.
+   gcp_profile_read synchronises those events and returns the summed device
+   time of the recorded launches in milliseconds and their count, then
+   starts a new count.  host outputs. */
+gcp_status gcp_profile(gcp_handle *h, int32_t enable, int32_t capacity);
+gcp_status gcp_profile_read(gcp_handle *h, double *total_ms, int64_t *launches);
 
 /* A static string naming a status code. */
 const char *gcp_status_string(gcp_status s);

@@ -58,8 +58,8 @@ class GcpAdam:
     # -- one epoch of launches --------------------------------------------
     def iteration(self):
         """One sampled gradient + Adam step (draws from the device iteration counter)."""
-        gcp.gcp_grad(self.h, self.F, self.loss, self.G, S=self.spec, stream_dev=self.state[3:4], stream=self.stream)
-        gcp.gcp_adam_step(self.F, self.G, self.B, self.C, self.state, stream=self.stream, **self.adam)
+        gcp.gcp_iteration(self.h, self.F, self.loss, self.spec, self.G, self.B, self.C, self.state,
+                          stream_dev=self.state[3:4], stream=self.stream, **self.adam)
 
     def end_epoch(self):
         gcp.gcp_loss_est(self.h, self.F, self.loss, self.est, self.state[0:1], stream=self.stream)
@@ -79,8 +79,8 @@ class GcpAdam:
             G, B, C, SA, SB, SC = (F.like() for _ in range(6))
             st = gcp.new_state(self.F.A[0].device)
         gcp.gcp_state_init(st, 0.0, stream=self.stream)
-        gcp.gcp_grad(self.h, F, self.loss, G, S=self.spec, stream_dev=st[3:4], stream=self.stream)
-        gcp.gcp_adam_step(F, G, B, C, st, stream=self.stream, **self.adam)
+        gcp.gcp_iteration(self.h, F, self.loss, self.spec, G, B, C, st, stream_dev=st[3:4], stream=self.stream,
+                          **self.adam)
         gcp.gcp_loss_est(self.h, F, self.loss, self.est, st[0:1], stream=self.stream)
         gcp.gcp_epoch_end(F, B, C, SA, SB, SC, st, self.tau, self.nu, self.kappa, stream=self.stream)
         self.stream.synchronize()

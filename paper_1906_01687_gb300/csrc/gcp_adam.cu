@@ -78,8 +78,19 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
         const int64_t loc = i4 - mt.off4[k];
         const int col = static_cast<int>((loc * 4) % mt.ld);
         float4* g4 = reinterpret_cast<float4*>(mt.G[k]) + loc;
+        float4 g = *g4;
+        if (a.reps[k] > 1) {  // fold the replica slabs of this mode (fixed order), leaving them zero
+            float4* r = reinterpret_cast<float4*>(a.R[k]) + loc;
+            for (uint32_t q = 0; q < a.reps[k]; ++q) {
+                const float4 v = r[q * a.rep_stride4[k]];
+                g.x += v.x;
+                g.y += v.y;
+                g.z += v.z;
+                g.w += v.w;
+                r[q * a.rep_stride4[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
         if (!s_done && col < mt.rank) {
-            const float4 g = *g4;
             float4* a4p = reinterpret_cast<float4*>(mt.A[k]) + loc;
             float4* b4p = reinterpret_cast<float4*>(mt.B[k]) + loc;
             float4* c4p = reinterpret_cast<float4*>(mt.C[k]) + loc;

@@ -53,6 +53,10 @@ struct gcp_handle {
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
+    // optional CUDA-event timing of the fused-gradient kernel
+    cudaEvent_t* prof_ev = nullptr;
+    int32_t prof_cap = 0;
+    int32_t prof_used = 0;
 };
 
 namespace {
@@ -525,10 +529,57 @@ gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream
     return GCP_OK;
 }
 
+static void profile_free(gcp_handle* h)
+{
+    if (!h->prof_ev) return;
+    for (int i = 0; i < 2 * h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
+    delete[] h->prof_ev;
+    h->prof_ev = nullptr;
+    h->prof_cap = h->prof_used = 0;
+}
+
+gcp_status gcp_profile(gcp_handle* h, int32_t enable, int32_t capacity)
+{
+    if (!h || (enable && (capacity < 1 || capacity > 65536))) return GCP_ERR_INVALID_ARG;
+    GCP_CUDA_TRY(cudaDeviceSynchronize());
+    profile_free(h);
+    if (!enable) return GCP_OK;
+    h->prof_ev = new (std::nothrow) cudaEvent_t[2 * static_cast<size_t>(capacity)];
+    if (!h->prof_ev) return GCP_ERR_NO_MEMORY;
+    for (int i = 0; i < 2 * capacity; ++i) {
+        if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) {
+            h->prof_cap = i / 2;
+            profile_free(h);
+            return GCP_ERR_CUDA;
+        }
+        h->prof_cap = (i + 1) / 2;
+    }
+    h->prof_cap = capacity;
+    h->prof_used = 0;
+    return GCP_OK;
+}
+
+gcp_status gcp_profile_read(gcp_handle* h, double* total_ms, int64_t* launches)
+{
+    if (!h || !total_ms || !launches) return GCP_ERR_INVALID_ARG;
+    double sum = 0.0;
+    for (int i = 0; i < h->prof_used; ++i) {
+        GCP_CUDA_TRY(cudaEventSynchronize(h->prof_ev[2 * i + 1]));
+        float ms = 0.f;
+        GCP_CUDA_TRY(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = h->prof_used;
+    h->prof_used = 0;
+    return GCP_OK;
+}
+
 gcp_status gcp_destroy(gcp_handle* h)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
+    profile_free(h);
     cudaFree(h->recs);
     cudaFree(h->d_status);
     cudaFree(h->table);
@@ -628,9 +679,9 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
     return GCP_OK;
 }
 
-gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
-                    const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
-                    gcp_stream_t stream)
+static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
+                            const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
+                            cudaStream_t s, FoldArgs* deferred_fold)
 {
     if (!h || (S == nullptr) == (list == nullptr)) return GCP_ERR_INVALID_ARG;
     if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
@@ -639,7 +690,6 @@ gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gc
     if (!modes_ok(G, h->X.d)) return GCP_ERR_INVALID_ARG;
     st = S ? check_spec(h, S) : check_list(h, list);
     if (st != GCP_OK) return st;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last_stream = s;
     GradArgs a{};
     a.dr = make_draw_args(h, S, list, stream_dev);
@@ -678,28 +728,51 @@ gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gc
         a.smem_off[k] = sh.off[k];
         a.reps[k] = sh.reps[k];
         const int64_t slab = h->X.dims[k] * F->ld;
+        if (deferred_fold) {
+            deferred_fold->reps[k] = 1;
+            deferred_fold->R[k] = nullptr;
+        }
         if (sh.reps[k] > 1) {
             a.G[k] = h->rep_ws + ws_off;
             a.rep_stride[k] = static_cast<uint64_t>(slab);
-            const int m = fold.nmodes++;
-            fold.R[m] = h->rep_ws + ws_off;
-            fold.G[m] = G[k];
-            fold.reps[m] = sh.reps[k];
-            fold.rep_stride4[m] = static_cast<uint64_t>(slab / 4);
-            fold.off4[m + 1] = fold.off4[m] + slab / 4;
+            if (deferred_fold) {  // per mode, indexed by k
+                deferred_fold->reps[k] = sh.reps[k];
+                deferred_fold->R[k] = h->rep_ws + ws_off;
+                deferred_fold->rep_stride4[k] = static_cast<uint64_t>(slab / 4);
+            } else {  // compacted over the replicated modes
+                const int m = fold.nmodes++;
+                fold.R[m] = h->rep_ws + ws_off;
+                fold.G[m] = G[k];
+                fold.reps[m] = sh.reps[k];
+                fold.rep_stride4[m] = static_cast<uint64_t>(slab / 4);
+                fold.off4[m + 1] = fold.off4[m] + slab / 4;
+            }
             ws_off += slab * sh.reps[k];
         } else {
             a.G[k] = G[k];
             a.rep_stride[k] = 0;
         }
     }
+    const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
+    if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));
     GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.grid, sh.block, sh.smem, s));
-    if (fold.nmodes > 0) {
+    if (timed) {
+        GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s));
+        h->prof_used++;
+    }
+    if (!deferred_fold && fold.nmodes > 0) {
         const int64_t total4 = fold.off4[fold.nmodes];
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total4 + 255) / 256, int64_t(h->num_sms) * 8)));
         GCP_CUDA_TRY(launch_fold(fold, grid, s));
     }
     return GCP_OK;
+}
+
+gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
+                    const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
+                    gcp_stream_t stream)
+{
+    return grad_impl(h, F, loss, S, list, stream_dev, G, reinterpret_cast<cudaStream_t>(stream), nullptr);
 }
 
 gcp_status gcp_loss_est(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_samples* list,
@@ -759,7 +832,43 @@ gcp_status gcp_adam_step(const gcp_factors* F, int32_t d, const int64_t* dims, f
     a.lower = prm->lower;
     a.eps_inside_sqrt = prm->eps_inside_sqrt;
     a.st = state;
+    for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
     GCP_CUDA_TRY(launch_adam(a, elementwise_grid(a.mt), reinterpret_cast<cudaStream_t>(stream)));
+    return GCP_OK;
+}
+
+gcp_status gcp_iteration(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
+                         const int64_t* stream_dev, float* const G[GCP_MAX_MODES], float* const B[GCP_MAX_MODES],
+                         float* const C[GCP_MAX_MODES], const gcp_adam_params* prm, gcp_adam_state* state,
+                         gcp_stream_t stream)
+{
+    if (!h || !S) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_modes(F, h->X.d, h->X.dims);
+    if (st != GCP_OK) return st;
+    if (!prm || !state || !aligned(state, 8) || !modes_ok(B, h->X.d) || !modes_ok(C, h->X.d)) return GCP_ERR_INVALID_ARG;
+    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
+        return GCP_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    FoldArgs fold{};
+    st = grad_impl(h, F, loss, S, nullptr, stream_dev, G, s, &fold);
+    if (st != GCP_OK) return st;
+    AdamArgs a{};
+    a.mt = mode_table(F, h->X.d, h->X.dims);
+    for (int k = 0; k < h->X.d; ++k) {
+        a.mt.G[k] = G[k];
+        a.mt.B[k] = B[k];
+        a.mt.C[k] = C[k];
+        a.reps[k] = fold.reps[k] > 1 ? fold.reps[k] : 1;
+        a.R[k] = fold.R[k];
+        a.rep_stride4[k] = fold.rep_stride4[k];
+    }
+    a.beta1 = prm->beta1;
+    a.beta2 = prm->beta2;
+    a.eps = prm->eps;
+    a.lower = prm->lower;
+    a.eps_inside_sqrt = prm->eps_inside_sqrt;
+    a.st = state;
+    GCP_CUDA_TRY(launch_adam(a, elementwise_grid(a.mt), s));
     return GCP_OK;
 }
 

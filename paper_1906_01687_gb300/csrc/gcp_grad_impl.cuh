@@ -41,6 +41,11 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int d = D <= 4 ? D : a.dr.d;
     const int ld = a.ld, rank = a.rank;
+    // this CTA's destination of each mode (its replica slab, or G_k itself)
+    float* gdst[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        gdst[k] = k < d ? a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k] : nullptr;
 
     // warp-uniform loop over batches of 32 draws
     for (int64_t wb = warp_global * 32; wb < a.dr.n_total; wb += nwarps * 32) {
@@ -117,8 +122,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
                         atomicAdd(s + 2, upd.z);
                         atomicAdd(s + 3, upd.w);
                     } else {
-                        float* gk = a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k];
-                        atomicAdd(reinterpret_cast<float4*>(gk + static_cast<size_t>(ix[k]) * ld + col), upd);
+                        atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd);
                     }
                 }
             }

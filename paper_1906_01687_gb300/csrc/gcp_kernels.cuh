@@ -89,6 +89,11 @@ struct AdamArgs {
     float beta1, beta2, eps, lower;
     int32_t eps_inside_sqrt;
     gcp_adam_state* st;
+    // replica slabs still to be folded into G (gcp_iteration): mode k's gradient
+    // is G_k + sum_r R_k[r] when reps[k] > 1; the slabs are zeroed after use
+    uint32_t reps[GCP_MAX_MODES];
+    uint64_t rep_stride4[GCP_MAX_MODES];
+    float* R[GCP_MAX_MODES];
 };
 
 struct EpochArgs {

@@ -79,6 +79,13 @@ class gcp_launch_info(ctypes.Structure):
                 ("replicas", ctypes.c_int32 * MAX_MODES)]
 
 
+class gcp_batch_problem(ctypes.Structure):
+    _fields_ = [("X", gcp_tensor), ("F", gcp_factors), ("loss", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("S", gcp_sampling), ("est", gcp_samples), ("G", _P8), ("B", _P8), ("C", _P8), ("SA", _P8),
+                ("SB", _P8), ("SC", _P8), ("adam", gcp_adam_params), ("epoch", gcp_epoch_params),
+                ("state", _vp)]
+
+
 _i32, _i64 = ctypes.c_int32, ctypes.c_int64
 _P = ctypes.POINTER
 _SIGS = {
@@ -90,15 +97,28 @@ _SIGS = {
     "gcp_get_device_status": ([_vp, _P(_i32)], ctypes.c_int),
     "gcp_set_tuning": ([_vp, _P(gcp_tuning)], ctypes.c_int),
     "gcp_get_launch": ([_vp, _P(gcp_factors), _i64, _P(gcp_launch_info)], ctypes.c_int),
+    "gcp_profile": ([_vp, _i32, _i32], ctypes.c_int),
+    "gcp_profile_read": ([_vp, _P(ctypes.c_double), _P(_i64)], ctypes.c_int),
     "gcp_sample": ([_vp, _P(gcp_sampling), _P(gcp_samples), _vp], ctypes.c_int),
     "gcp_reserve": ([_vp, _P(gcp_sampling), _vp], ctypes.c_int),
     "gcp_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _P(gcp_samples), _vp, _P8, _vp], ctypes.c_int),
     "gcp_loss_est": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_samples), _vp, _vp], ctypes.c_int),
     "gcp_state_init": ([_vp, ctypes.c_float, _vp], ctypes.c_int),
     "gcp_adam_step": ([_P(gcp_factors), _i32, _P(_i64), _P8, _P8, _P8, _P(gcp_adam_params), _vp, _vp], ctypes.c_int),
+    "gcp_iteration": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _vp, _P8, _P8, _P8,
+                       _P(gcp_adam_params), _vp, _vp], ctypes.c_int),
     "gcp_epoch_begin": ([_P(gcp_factors), _i32, _P(_i64), _P8, _P8, _P8, _P8, _P8, _vp, _vp], ctypes.c_int),
     "gcp_epoch_end": ([_P(gcp_factors), _i32, _P(_i64), _P8, _P8, _P8, _P8, _P8, _P(gcp_epoch_params), _vp, _vp],
                       ctypes.c_int),
+    "gcp_batch_create": ([_P(_vp), _P(gcp_batch_problem), _i32, _vp], ctypes.c_int),
+    "gcp_batch_destroy": ([_vp], ctypes.c_int),
+    "gcp_batch_set_tuning": ([_vp, _i32, _i32], ctypes.c_int),
+    "gcp_batch_grad": ([_vp, _vp], ctypes.c_int),
+    "gcp_batch_adam_step": ([_vp, _vp], ctypes.c_int),
+    "gcp_batch_iteration": ([_vp, _vp], ctypes.c_int),
+    "gcp_batch_loss_est": ([_vp, _vp], ctypes.c_int),
+    "gcp_batch_epoch_begin": ([_vp, _vp], ctypes.c_int),
+    "gcp_batch_epoch_end": ([_vp, _vp], ctypes.c_int),
     "gcp_factors_to_bf16": ([_P(gcp_factors), _i32, _P(_i64), _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -351,6 +371,18 @@ def gcp_get_launch(h: Handle, F: Factors, n_draws: int) -> dict:
                 smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_mode_mask, replicas=list(t.replicas)[: h.d])
 
 
+def gcp_profile(h: Handle, enable: bool, capacity: int = 1024):
+    """Records CUDA events around each following fused-gradient kernel launch."""
+    _check(_lib.gcp_profile(h.ptr, int(bool(enable)), int(capacity)), "gcp_profile")
+
+
+def gcp_profile_read(h: Handle):
+    """(total device milliseconds, launches) of the recorded gradient kernels."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(_lib.gcp_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(n)), "gcp_profile_read")
+    return ms.value, n.value
+
+
 def gcp_sample(h: Handle, S: Sampling, out: Optional[SampleList] = None, stream=None) -> SampleList:
     if out is None:
         out = SampleList.empty(h.d, S.count(), device=h.X.vals.device if h.X.vals is not None else h.X.idx[0].device)
@@ -413,6 +445,16 @@ def gcp_adam_step(F: Factors, G, B, C, state: torch.Tensor, beta1=0.9, beta2=0.9
                               _ptr(state), _stream(stream)), "gcp_adam_step")
 
 
+def gcp_iteration(h: Handle, F: Factors, loss: int, S: Sampling, G, B, C, state: torch.Tensor,
+                  stream_dev: Optional[torch.Tensor] = None, beta1=0.9, beta2=0.999, eps=1e-8, lower=-math.inf,
+                  eps_inside_sqrt=True, stream=None):
+    """One fused GCP-Adam iteration: sampled gradient + Adam step (G zero on entry and exit)."""
+    prm = _adam_params(beta1, beta2, eps, lower, eps_inside_sqrt)
+    _check(_lib.gcp_iteration(h.ptr, ctypes.byref(F._c()), int(loss), ctypes.byref(S._c()), _ptr(stream_dev),
+                              _p8(G), _p8(B), _p8(C), ctypes.byref(prm), _ptr(state), _stream(stream)),
+           "gcp_iteration")
+
+
 def gcp_epoch_begin(F: Factors, B, C, SA, SB, SC, state: torch.Tensor, stream=None):
     d = len(F.dims)
     dims = (_i64 * d)(*F.dims)
@@ -433,3 +475,72 @@ def gcp_factors_to_bf16(F: Factors, stream=None):
     d = len(F.dims)
     dims = (_i64 * d)(*F.dims)
     _check(_lib.gcp_factors_to_bf16(ctypes.byref(F._c()), d, dims, _stream(stream)), "gcp_factors_to_bf16")
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """gcp_batch_create / gcp_batch_destroy over a list of problem dicts with
+    keys X (DataTensor, dense), F (Factors), loss, S (uniform Sampling), est
+    (SampleList), G, B, C, SA, SB, SC (buffer lists), state, and optional
+    adam (dict of beta1, beta2, eps, lower, eps_inside_sqrt) and epoch (dict
+    of tau, nu, kappa)."""
+
+    def __init__(self, problems, stream=None):
+        self.problems = problems  # keeps every device buffer alive
+        arr = (gcp_batch_problem * len(problems))()
+        for i, p in enumerate(problems):
+            c = arr[i]
+            c.X = p["X"]._c()
+            c.F = p["F"]._c()
+            c.loss = int(p["loss"])
+            c.S = p["S"]._c()
+            c.est = p["est"]._c()
+            for name in ("G", "B", "C", "SA", "SB", "SC"):
+                setattr(c, name, _p8(p[name]))
+            ad = dict(beta1=0.9, beta2=0.999, eps=1e-8, lower=-math.inf, eps_inside_sqrt=True)
+            ad.update(p.get("adam", {}))
+            c.adam = _adam_params(**ad)
+            ep = dict(tau=1000, nu=0.1, kappa=1)
+            ep.update(p.get("epoch", {}))
+            c.epoch = gcp_epoch_params(int(ep["tau"]), float(ep["nu"]), int(ep["kappa"]))
+            c.state = p["state"].data_ptr()
+        self._b = ctypes.c_void_p()
+        _check(_lib.gcp_batch_create(ctypes.byref(self._b), arr, len(problems), _stream(stream)), "gcp_batch_create")
+
+    def close(self):
+        if self._b:
+            _lib.gcp_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, block=0, grid_blocks=0):
+        _check(_lib.gcp_batch_set_tuning(self._b, int(block), int(grid_blocks)), "gcp_batch_set_tuning")
+
+    def _call(self, name, stream):
+        _check(getattr(_lib, name)(self._b, _stream(stream)), name)
+
+    def grad(self, stream=None):
+        self._call("gcp_batch_grad", stream)
+
+    def adam_step(self, stream=None):
+        self._call("gcp_batch_adam_step", stream)
+
+    def iteration(self, stream=None):
+        self._call("gcp_batch_iteration", stream)
+
+    def loss_est(self, stream=None):
+        self._call("gcp_batch_loss_est", stream)
+
+    def epoch_begin(self, stream=None):
+        self._call("gcp_batch_epoch_begin", stream)
+
+    def epoch_end(self, stream=None):
+        self._call("gcp_batch_epoch_end", stream)

@@ -71,3 +71,20 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gcp.gcp_epoch_params) == 16
     assert ctypes.sizeof(gcp.gcp_tuning) == 32
     assert ctypes.sizeof(gcp.gcp_launch_info) == 56
+
+
+def test_ctypes_layouts_match_the_c_compiler(tmp_path):
+    """Every struct of include/gcp.h has the same size in C (gcc) and in the binding."""
+    from paper_1906_01687_gb300 import gcp
+    names = ["gcp_tensor", "gcp_factors", "gcp_sampling", "gcp_samples", "gcp_adam_params", "gcp_epoch_params",
+             "gcp_adam_state", "gcp_tuning", "gcp_launch_info", "gcp_batch_problem"]
+    src = tmp_path / "sizes.c"
+    src.write_text('#include "gcp.h"\n#include <stdio.h>\nint main(void){\n' +
+                   "".join(f'printf("%zu\\n", sizeof({n}));\n' for n in names) + "return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sizes = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    for n, size in zip(names, sizes):
+        if hasattr(gcp, n):
+            assert ctypes.sizeof(getattr(gcp, n)) == size, n
+    assert dict(zip(names, sizes))["gcp_adam_state"] == 64

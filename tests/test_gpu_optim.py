@@ -231,3 +231,55 @@ def test_planted_recovery_on_gpu():
                   est_seed=8, alpha=0.01, tau=100)
     run.fit(max_epochs=40)
     assert cosine_score(true, run.factors()) >= 0.9
+
+
+@pytest.mark.parametrize("kind", ["uniform", "stratified"])
+def test_fused_iteration_equals_grad_then_adam(kind):
+    """gcp_iteration (gradient + Adam with the replica fold inside Adam) gives
+    the factors of gcp_grad followed by gcp_adam_step on the same draws."""
+    g = gcp()
+    if kind == "uniform":
+        dims = (60, 50, 40, 30)
+        X = np.random.default_rng(3).standard_normal(dims).astype(np.float32)
+        h = g.Handle(g.DataTensor.dense(X))
+        S = g.Sampling(g.SAMPLER_UNIFORM, 0, 50000, seed=3, stream=5)
+    else:
+        dims = (300, 40, 25)
+        idx, vals = sparse_random(dims, 20000, 9)
+        h = g.Handle(g.DataTensor.coo(dims, idx, vals))
+        S = g.Sampling(g.SAMPLER_STRATIFIED, 20000, 20000, seed=3, stream=5)
+    A = rng_factors(dims, 10, 4, scale=0.5)
+    runs = []
+    for fused in (True, False):
+        F = g.Factors(A)
+        G, B, C, st = F.like(), F.like(), F.like(), g.new_state()
+        g.gcp_state_init(st, 0.01)
+        for it in range(3):
+            Sit = g.Sampling(S.kind, S.p, S.q, S.seed, it)
+            if fused:
+                g.gcp_iteration(h, F, g.LOSS_POISSON_LOG, Sit, G, B, C, st)
+            else:
+                g.gcp_grad(h, F, g.LOSS_POISSON_LOG, G, S=Sit)
+                g.gcp_adam_step(F, G, B, C, st)
+        torch.cuda.synchronize()
+        assert all(torch.count_nonzero(x).item() == 0 for x in G)
+        runs.append(flat(F.A, 10))
+        assert g.read_state(st)["t"] == 3
+    np.testing.assert_allclose(runs[0], runs[1], rtol=1e-4, atol=1e-6)
+
+
+def test_profile_events_count_gradient_kernels():
+    g = gcp()
+    dims = (30, 20, 10)
+    X = np.random.default_rng(1).standard_normal(dims).astype(np.float32)
+    h = g.Handle(g.DataTensor.dense(X))
+    F = g.Factors(rng_factors(dims, 8, 2))
+    G = F.like()
+    g.gcp_profile(h, True, 4)
+    for i in range(6):  # only the first 4 launches are timed
+        g.gcp_grad(h, F, 0, G, S=g.Sampling(g.SAMPLER_UNIFORM, 0, 5000, seed=1, stream=i))
+    ms, n = g.gcp_profile_read(h)
+    assert n == 4 and ms > 0
+    ms, n = g.gcp_profile_read(h)
+    assert n == 0
+    g.gcp_profile(h, False)
