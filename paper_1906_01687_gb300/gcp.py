@@ -103,6 +103,7 @@ _SIGS = {
     "gcp_reserve": ([_vp, _P(gcp_sampling), _vp], ctypes.c_int),
     "gcp_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _P(gcp_samples), _vp, _P8, _vp], ctypes.c_int),
     "gcp_loss_est": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_samples), _vp, _vp], ctypes.c_int),
+    "gcp_loss_est_noalloc": ([_i32, _P(gcp_factors), ctypes.c_int, _P(gcp_samples), _vp, _vp], ctypes.c_int),
     "gcp_state_init": ([_vp, ctypes.c_float, _vp], ctypes.c_int),
     "gcp_adam_step": ([_P(gcp_factors), _i32, _P(_i64), _P8, _P8, _P8, _P(gcp_adam_params), _vp, _vp], ctypes.c_int),
     "gcp_iteration": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _vp, _P8, _P8, _P8,
@@ -411,6 +412,15 @@ def gcp_loss_est(h: Handle, F: Factors, loss: int, samples: SampleList, out: tor
     assert out.dtype == torch.float64 and out.is_cuda
     _check(_lib.gcp_loss_est(h.ptr, ctypes.byref(F._c(gather_bf16)), int(loss), ctypes.byref(samples._c()),
                              _ptr(out), _stream(stream)), "gcp_loss_est")
+
+
+def gcp_loss_est_noalloc(d: int, F: Factors, loss: int, samples: SampleList, out: torch.Tensor, stream=None,
+                         gather_bf16: Optional[bool] = None):
+    """gcp_loss_est without a handle and without any allocation by the library
+    (scratch in a static device array; overlapping calls race)."""
+    assert out.dtype == torch.float64 and out.is_cuda
+    _check(_lib.gcp_loss_est_noalloc(int(d), ctypes.byref(F._c(gather_bf16)), int(loss), ctypes.byref(samples._c()),
+                                     _ptr(out), _stream(stream)), "gcp_loss_est_noalloc")
 
 
 STATE_FIELDS = ("F", "F_old", "t", "iter", "alpha", "bad", "done", "status")
