@@ -55,6 +55,28 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The slowest rank's time: every rank's value, all-reduced with MAX."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank):
+    """Rank r fits its own replica: initial-guess seed 3 + r, draw seed 1687 + r
+    (the estimate set, seed 7, is shared by all replicas)."""
+    return 3 + rank, 1687 + rank
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -204,9 +226,9 @@ def ours_arm(args):
     stream = torch.cuda.Stream(device=dev)
 
     X32, _ = synth.dense_100_4()
-    A0 = synth.initial_guess(DIMS, RANK, seed=3 + rank, target_norm=float(np.linalg.norm(X32)))
+    init_seed, seed = replica_seeds(rank)
+    A0 = synth.initial_guess(DIMS, RANK, seed=init_seed, target_norm=float(np.linalg.norm(X32)))
     XT = gcp.DataTensor.dense(X32, device=dev)
-    seed = 1687 + rank
     with torch.cuda.stream(stream):
         run = GcpAdam(XT, A0, gcp.LOSS_GAUSSIAN, gcp.SAMPLER_UNIFORM, 0, S_DRAWS, 0, EST_DRAWS, seed=seed,
                       est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream,
@@ -233,14 +255,10 @@ def ours_arm(args):
             run.run_epoch()
         end.record(stream)
         barrier()
-    elapsed = start.elapsed_time(end) * 1e-3
+    elapsed = max_over_ranks(start.elapsed_time(end) * 1e-3, world, dev)
     st = run.status()
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
     entries = args.steps * TAU * S_DRAWS * world
-    value = entries / elapsed
+    value = whole_job_rate(args.steps * TAU * S_DRAWS, world, elapsed)
 
     # end to end through the public API with host buffers: H2D of X and of the
     # initial factors from pinned memory, the epoch, D2H of F-hat and the factors
@@ -264,11 +282,7 @@ def ours_arm(args):
                 a_host.copy_(a_dev[:, :RANK], non_blocking=True)
     e_end.record(stream)
     barrier()
-    e2e_elapsed = e_start.elapsed_time(e_end) * 1e-3
-    if world > 1:
-        t = torch.tensor([e2e_elapsed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_elapsed = float(t.item())
+    e2e_elapsed = max_over_ranks(e_start.elapsed_time(e_end) * 1e-3, world, dev)
     e2e_value = entries / e2e_elapsed
 
     # the dominant kernel (the fused sampled gradient), timed alone

@@ -54,11 +54,20 @@ typedef enum gcp_status {
 
 /* Elementwise losses f(x, m) and g = df/dm.  Gaussian is Section 1's
    (x - m)^2; Bernoulli-logit log(1 + e^m) - x m and Poisson-log e^m - x m are
-   the log-link losses of the GCP paper this one builds on (HoKoDu20). */
+   the log-link losses of the GCP paper this one builds on (HoKoDu20).  The
+   paper's own odds / identity-link losses (Section 1; Sections 5.2-5.4) need
+   m > 0 and are evaluated at m + 1e-10: Bernoulli-odds log(m + 1) - x log m,
+   Poisson-identity m - x log m, Gamma x / m + log m, and the beta-divergence
+   with beta = 1/2 as Section 5.3 prints it, 2 m^(1/2) + 2 x m^(-1/2).  Use
+   them with nonnegative factors (lower = 0 in the Adam step). */
 typedef enum gcp_loss {
     GCP_LOSS_GAUSSIAN = 0,
     GCP_LOSS_BERNOULLI_LOGIT = 1,
-    GCP_LOSS_POISSON_LOG = 2
+    GCP_LOSS_POISSON_LOG = 2,
+    GCP_LOSS_BERNOULLI_ODDS = 3,
+    GCP_LOSS_POISSON_IDENTITY = 4,
+    GCP_LOSS_GAMMA = 5,
+    GCP_LOSS_BETA_HALF = 6
 } gcp_loss;
 
 /* Samplers: Alg. 1 (uniform, Section 4.1), Alg. 2 (stratified, Section 4.2),
@@ -423,6 +432,9 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
                    keep same-address contention low (-1 = 32; 0 or 1 = off);
      replica_target expected updates per 16-byte address per launch above
                    which a mode is replicated (0 = 64).
+   group_draws = 1: each group of lanes generates and takes its own draw
+   (32 / lanes draws per warp step) instead of a warp generating 32 draws and
+   its groups walking them in turn (0): more warps for small draw counts.
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -433,6 +445,8 @@ typedef struct gcp_tuning {
     int32_t smem_min_hits;
     int32_t max_replicas;
     int32_t replica_target;
+    int32_t group_draws;
+    int32_t reserved;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */
@@ -444,6 +458,8 @@ typedef struct gcp_launch_info {
     int32_t smem_bytes;
     uint32_t smem_mode_mask;
     int32_t replicas[GCP_MAX_MODES];
+    int32_t group_draws;
+    int32_t reserved;
 } gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch

@@ -27,6 +27,8 @@ _lib = None
 # classes, losses and samplers: the same numbering the C file defines
 UNIFORM, STRATIFIED, SEMI_STRATIFIED = 0, 1, 2
 GAUSSIAN, BERNOULLI_LOGIT, POISSON_LOG = 0, 1, 2
+BERNOULLI_ODDS, POISSON_IDENTITY, GAMMA, BETA_HALF = 3, 4, 5, 6
+M_EPS = 1e-10  # odds/identity-link losses are evaluated at m + M_EPS
 CLS_UNIFORM, CLS_STRAT_NZ, CLS_STRAT_ZERO, CLS_SEMI_NZ, CLS_SEMI_ZERO = 0, 1, 2, 3, 4
 TAG_UNIFORM, TAG_NONZERO, TAG_ZERO_CANDIDATE, TAG_SEMI_ZERO = 0, 1, 2, 3
 OK, ERR_ARG, ERR_SHORTFALL = 0, 1, 4

@@ -51,6 +51,15 @@
 #define ORC_GAUSSIAN 0
 #define ORC_BERNOULLI_LOGIT 1
 #define ORC_POISSON_LOG 2
+#define ORC_BERNOULLI_ODDS 3
+#define ORC_POISSON_IDENTITY 4
+#define ORC_GAMMA 5
+#define ORC_BETA_HALF 6
+
+/* The losses with an odds or identity link need m > 0; they are evaluated
+   at m + ORC_M_EPS, so that m = 0 (reachable under the projection
+   max(A, 0) of Alg. 4) stays finite. */
+#define ORC_M_EPS 1e-10
 
 /* status codes */
 #define ORC_OK 0
@@ -133,13 +142,24 @@ uint64_t orc_linear_key(int d, const int64_t *dims, const int64_t *idx)
 /* Losses f(x,m) and g = df/dm.                                             */
 /* Gaussian: Section 1, f = (x-m)^2.  Bernoulli-logit and Poisson-log are   */
 /* the log-link forms of the cited GCP paper (HoKoDu20); this paper prints  */
-/* only their odds/identity-link forms.  Pinned by closed forms and finite  */
-/* differences in the CPU tests.                                            */
+/* the odds/identity-link forms, also here: Bernoulli-odds, Poisson-        */
+/* identity, Gamma (Section 1) and the beta-divergence with beta = 1/2 as   */
+/* Section 5.3 prints it.  Pinned by scipy's distributions, closed forms    */
+/* and finite differences in the CPU tests.                                 */
 /* ------------------------------------------------------------------------ */
 
 double orc_loss_f(int loss, double x, double m)
 {
+    double mp = m + ORC_M_EPS;
     switch (loss) {
+    case ORC_BERNOULLI_ODDS: /* Section 1: log(m + 1) - x log m, m the odds */
+        return log(mp + 1.0) - x * log(mp);
+    case ORC_POISSON_IDENTITY: /* Section 1: m - x log m */
+        return mp - x * log(mp);
+    case ORC_GAMMA: /* Section 1 and Section 5.2's caption: x / m + log m */
+        return x / mp + log(mp);
+    case ORC_BETA_HALF: /* Section 5.3: 2 m^(1/2) + 2 x m^(-1/2) */
+        return 2.0 * sqrt(mp) + 2.0 * x / sqrt(mp);
     case ORC_GAUSSIAN:
         return (x - m) * (x - m);
     case ORC_BERNOULLI_LOGIT: {
@@ -155,7 +175,16 @@ double orc_loss_f(int loss, double x, double m)
 
 double orc_loss_g(int loss, double x, double m)
 {
+    double mp = m + ORC_M_EPS;
     switch (loss) {
+    case ORC_BERNOULLI_ODDS:
+        return 1.0 / (mp + 1.0) - x / mp;
+    case ORC_POISSON_IDENTITY:
+        return 1.0 - x / mp;
+    case ORC_GAMMA:
+        return -x / (mp * mp) + 1.0 / mp;
+    case ORC_BETA_HALF:
+        return 1.0 / sqrt(mp) - x / (mp * sqrt(mp));
     case ORC_GAUSSIAN:
         return 2.0 * (m - x);
     case ORC_BERNOULLI_LOGIT: {

@@ -35,9 +35,11 @@ def candidate_shapes(rank: int) -> list:
 def candidates(rank: int) -> list:
     out = []
     for L, NC in candidate_shapes(rank):
-        for block in (128, 256):
-            for reps, target in ((0, 0), (-1, 0), (8, 128), (32, 16)):
-                out.append(dict(lanes=L, chunks=NC, block=block, max_replicas=reps, replica_target=target))
+        for group in ((0, 1) if L > 1 else (0,)):
+            for block in (128, 256):
+                for reps, target in ((0, 0), (-1, 0), (8, 128), (32, 16)):
+                    out.append(dict(lanes=L, chunks=NC, block=block, max_replicas=reps, replica_target=target,
+                                    group_draws=group))
         out.append(dict(lanes=L, chunks=NC, block=256, max_replicas=0, smem_bytes=48 * 1024, smem_min_hits=10))
     return out
 

@@ -57,6 +57,8 @@ __device__ __forceinline__ float adam_one(float& a, float& b, float& c, float g,
 
 __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float s_alpha, s_c1, s_c2;
     __shared__ int s_done;
     if (threadIdx.x == 0) {
@@ -117,13 +119,14 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
 
 cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s)
 {
-    adam_kernel<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(adam_kernel, dim3(grid), dim3(256), 0, s, a);
 }
 
 // epoch_begin (snapshot) and epoch_end (accept or revert)
 __global__ void __launch_bounds__(256) epoch_kernel(const EpochArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_fail;
     if (threadIdx.x == 0) {
         const double F = a.st->F, Fo = a.st->F_old;
@@ -175,8 +178,7 @@ __global__ void __launch_bounds__(256) epoch_kernel(const EpochArgs a)
 
 cudaError_t launch_epoch(const EpochArgs& a, int grid, cudaStream_t s)
 {
-    epoch_kernel<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(epoch_kernel, dim3(grid), dim3(256), 0, s, a);
 }
 
 __global__ void state_init_kernel(gcp_adam_state* st, float alpha)
@@ -201,6 +203,8 @@ cudaError_t launch_state_init(gcp_adam_state* st, float alpha, cudaStream_t s)
 
 __global__ void __launch_bounds__(256) to_bf16_kernel(const ModeTable mt)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t total4 = mt.off4[mt.d];
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
@@ -212,8 +216,7 @@ __global__ void __launch_bounds__(256) to_bf16_kernel(const ModeTable mt)
 
 cudaError_t launch_to_bf16(const ModeTable& mt, int grid, cudaStream_t s)
 {
-    to_bf16_kernel<<<grid, 256, 0, s>>>(mt);
-    return cudaGetLastError();
+    return launch_pdl(to_bf16_kernel, dim3(grid), dim3(256), 0, s, mt);
 }
 
 }  // namespace gcpk

@@ -20,8 +20,8 @@ static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
 static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
-static_assert(sizeof(gcp_tuning) == 32, "gcp_tuning layout");
-static_assert(sizeof(gcp_launch_info) == 56, "gcp_launch_info layout");
+static_assert(sizeof(gcp_tuning) == 40, "gcp_tuning layout");
+static_assert(sizeof(gcp_launch_info) == 64, "gcp_launch_info layout");
 
 struct gcp_handle {
     gcp_tensor X{};
@@ -49,7 +49,7 @@ struct gcp_handle {
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
     int partials_cap = 0;
-    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0};
+    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0};
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
@@ -289,6 +289,7 @@ struct Shape {
     uint32_t off[GCP_MAX_MODES] = {};
     uint32_t reps[GCP_MAX_MODES] = {};
     int64_t rep_floats = 0;  // replica workspace the shape needs
+    int group = 0;           // group_draws layout
 };
 
 int next_pow2(int v)
@@ -348,7 +349,9 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     }
     sh->block = t.block > 0 ? t.block : 256;
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
-    const int64_t warps = (n_total + 31) / 32;
+    sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;
+    const int64_t per_warp = sh->group ? 32 / sh->L : 32;
+    const int64_t warps = (n_total + per_warp - 1) / per_warp;
     const int64_t blocks_needed = std::max<int64_t>(1, (warps + sh->block / 32 - 1) / (sh->block / 32));
 
     // shared-memory accumulation of small, often-hit G_k (off unless tuned on:
@@ -610,12 +613,13 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     if (!t) {
-        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0};
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0};
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1)) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
-    if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0)
+    if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
+        t->group_draws < 0 || t->group_draws > 1)
         return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
@@ -636,6 +640,7 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     out->grid_blocks = sh.grid;
     out->smem_bytes = static_cast<int32_t>(sh.smem);
     out->smem_mode_mask = sh.mask;
+    out->group_draws = sh.group;
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
@@ -684,7 +689,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
                             cudaStream_t s, FoldArgs* deferred_fold)
 {
     if (!h || (S == nullptr) == (list == nullptr)) return GCP_ERR_INVALID_ARG;
-    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     gcp_status st = check_factors(h, F);
     if (st != GCP_OK) return st;
     if (!modes_ok(G, h->X.d)) return GCP_ERR_INVALID_ARG;
@@ -720,6 +725,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     a.loss = loss;
     a.smem_floats = static_cast<int32_t>(sh.smem / 4);
     a.smem_mask = sh.mask;
+    a.group_draws = sh.group;
     FoldArgs fold{};
     int64_t ws_off = 0;
     for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
@@ -779,7 +785,7 @@ gcp_status gcp_loss_est(gcp_handle* h, const gcp_factors* F, gcp_loss loss, cons
                         double* out_dev, gcp_stream_t stream)
 {
     if (!h || !out_dev || !aligned(out_dev, 8)) return GCP_ERR_INVALID_ARG;
-    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     gcp_status st = check_factors(h, F);
     if (st != GCP_OK) return st;
     st = check_list(h, list);

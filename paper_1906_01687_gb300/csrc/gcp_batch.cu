@@ -97,6 +97,8 @@ __device__ __forceinline__ float4 brow(const BatchDesc& P, int k, uint32_t row, 
 
 __global__ void __launch_bounds__(256) batch_grad_kernel(const BatchArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ int64_t s_work[];
     for (int i = threadIdx.x; i <= a.count; i += blockDim.x) s_work[i] = a.work_begin[i];
     __syncthreads();
@@ -196,6 +198,8 @@ __device__ __forceinline__ int mode_in_problem(const BatchDesc& P, int64_t loc4)
 // done flag are read once per block into shared memory.
 __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ int64_t s_param[];  // count + 1 prefixes, then 4 floats per problem
     float* s_prob = reinterpret_cast<float*>(s_param + a.count + 1);
     for (int i = threadIdx.x; i <= a.count; i += blockDim.x) s_param[i] = a.param_begin4[i];
@@ -263,6 +267,8 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
 // block order.
 __global__ void __launch_bounds__(256) batch_loss_kernel(const BatchArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double warp_sums[8];
     const int pb = find_problem(a.est_block_begin, a.count, blockIdx.x);
     const BatchDesc& P = a.desc[pb];
@@ -312,6 +318,8 @@ __global__ void __launch_bounds__(256) batch_loss_kernel(const BatchArgs a)
 // Every problem's epoch begin (snapshot) or end (accept or revert).
 __global__ void __launch_bounds__(256) batch_epoch_kernel(const BatchArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ int64_t s_param[];
     int* s_fail = reinterpret_cast<int*>(s_param + a.count + 1);
     for (int i = threadIdx.x; i <= a.count; i += blockDim.x) s_param[i] = a.param_begin4[i];
@@ -407,7 +415,7 @@ gcp_status fill_desc(const gcp_batch_problem& p, BatchDesc* o)
     const gcp_factors& F = p.F;
     if (X.sparse || X.d < 1 || X.d > kBatchMaxD || !X.vals) return GCP_ERR_INVALID_ARG;
     if (F.rank < 1 || F.rank > 256 || F.ld < F.rank || F.ld % 4 != 0) return GCP_ERR_INVALID_ARG;
-    if (p.loss < GCP_LOSS_GAUSSIAN || p.loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
+    if (p.loss < GCP_LOSS_GAUSSIAN || p.loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     if (p.S.kind != GCP_SAMPLER_UNIFORM || p.S.q < 0 || p.S.q > (int64_t(1) << 40)) return GCP_ERR_INVALID_ARG;
     if (!al(p.state, 8)) return GCP_ERR_INVALID_ARG;
     if (!(p.adam.beta1 >= 0.f && p.adam.beta1 < 1.f && p.adam.beta2 >= 0.f && p.adam.beta2 < 1.f)) return GCP_ERR_INVALID_ARG;
@@ -580,16 +588,16 @@ gcp_status gcp_batch_grad(gcp_batch* b, gcp_stream_t stream)
     const int64_t want = (b->total_work + warps_per_block - 1) / warps_per_block;
     const int grid = b->grid > 0 ? b->grid
                                  : static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(b->num_sms) * std::max(bps, 1))));
-    batch_grad_kernel<<<grid, block, smem, reinterpret_cast<cudaStream_t>(stream)>>>(batch_args(b, 0));
-    return to_status(cudaGetLastError());
+    return to_status(launch_pdl(batch_grad_kernel, dim3(grid), dim3(block), smem, reinterpret_cast<cudaStream_t>(stream),
+                                batch_args(b, 0)));
 }
 
 gcp_status gcp_batch_adam_step(gcp_batch* b, gcp_stream_t stream)
 {
     if (!b) return GCP_ERR_INVALID_ARG;
     const size_t smem = sizeof(int64_t) * (b->count + 1) + sizeof(float) * 4 * b->count;
-    batch_adam_kernel<<<elementwise_blocks(b), 256, smem, reinterpret_cast<cudaStream_t>(stream)>>>(batch_args(b, 0));
-    return to_status(cudaGetLastError());
+    return to_status(launch_pdl(batch_adam_kernel, dim3(elementwise_blocks(b)), dim3(256), smem,
+                                reinterpret_cast<cudaStream_t>(stream), batch_args(b, 0)));
 }
 
 gcp_status gcp_batch_iteration(gcp_batch* b, gcp_stream_t stream)
@@ -602,17 +610,16 @@ gcp_status gcp_batch_iteration(gcp_batch* b, gcp_stream_t stream)
 gcp_status gcp_batch_loss_est(gcp_batch* b, gcp_stream_t stream)
 {
     if (!b) return GCP_ERR_INVALID_ARG;
-    batch_loss_kernel<<<static_cast<unsigned>(b->est_blocks), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        batch_args(b, 0));
-    return to_status(cudaGetLastError());
+    return to_status(launch_pdl(batch_loss_kernel, dim3(static_cast<unsigned>(b->est_blocks)), dim3(256), 0,
+                                reinterpret_cast<cudaStream_t>(stream), batch_args(b, 0)));
 }
 
 static gcp_status batch_epoch(gcp_batch* b, int begin, gcp_stream_t stream)
 {
     if (!b) return GCP_ERR_INVALID_ARG;
     const size_t smem = sizeof(int64_t) * (b->count + 1) + sizeof(int) * b->count;
-    batch_epoch_kernel<<<elementwise_blocks(b), 256, smem, reinterpret_cast<cudaStream_t>(stream)>>>(batch_args(b, begin));
-    return to_status(cudaGetLastError());
+    return to_status(launch_pdl(batch_epoch_kernel, dim3(elementwise_blocks(b)), dim3(256), smem,
+                                reinterpret_cast<cudaStream_t>(stream), batch_args(b, begin)));
 }
 
 gcp_status gcp_batch_epoch_begin(gcp_batch* b, gcp_stream_t stream) { return batch_epoch(b, 1, stream); }

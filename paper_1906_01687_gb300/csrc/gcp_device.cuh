@@ -80,21 +80,57 @@ __device__ __forceinline__ void draw_index(const uint32_t* __restrict__ dims, ui
 // ---------------------------------------------------------------------------
 // Losses: f(x,m) and g(x,m) = df/dm, FP32.
 // ---------------------------------------------------------------------------
+constexpr float kMEps = 1e-10f;  // odds/identity-link losses are evaluated at m + kMEps
+
 __device__ __forceinline__ float loss_g(int loss, float x, float m)
 {
-    if (loss == GCP_LOSS_GAUSSIAN) return 2.0f * (m - x);
-    if (loss == GCP_LOSS_BERNOULLI_LOGIT) return 1.0f / (1.0f + expf(-m)) - x;
-    return expf(m) - x;  // Poisson-log
+    switch (loss) {
+    case GCP_LOSS_GAUSSIAN: return 2.0f * (m - x);
+    case GCP_LOSS_BERNOULLI_LOGIT: return 1.0f / (1.0f + expf(-m)) - x;
+    case GCP_LOSS_POISSON_LOG: return expf(m) - x;
+    case GCP_LOSS_BERNOULLI_ODDS: {
+        const float mp = m + kMEps;
+        return 1.0f / (mp + 1.0f) - x / mp;
+    }
+    case GCP_LOSS_POISSON_IDENTITY: return 1.0f - x / (m + kMEps);
+    case GCP_LOSS_GAMMA: {
+        const float mp = m + kMEps;
+        return -x / (mp * mp) + 1.0f / mp;
+    }
+    default: {  // GCP_LOSS_BETA_HALF
+        const float mp = m + kMEps;
+        const float r = rsqrtf(mp);
+        return r - x * r / mp;
+    }
+    }
 }
 
 __device__ __forceinline__ float loss_f(int loss, float x, float m)
 {
-    if (loss == GCP_LOSS_GAUSSIAN) {
+    switch (loss) {
+    case GCP_LOSS_GAUSSIAN: {
         const float r = x - m;
         return r * r;
     }
-    if (loss == GCP_LOSS_BERNOULLI_LOGIT) return fmaxf(m, 0.0f) + log1pf(expf(-fabsf(m))) - x * m;
-    return expf(m) - x * m;
+    case GCP_LOSS_BERNOULLI_LOGIT: return fmaxf(m, 0.0f) + log1pf(expf(-fabsf(m))) - x * m;
+    case GCP_LOSS_POISSON_LOG: return expf(m) - x * m;
+    case GCP_LOSS_BERNOULLI_ODDS: {
+        const float mp = m + kMEps;
+        return log1pf(mp) - x * logf(mp);
+    }
+    case GCP_LOSS_POISSON_IDENTITY: {
+        const float mp = m + kMEps;
+        return mp - x * logf(mp);
+    }
+    case GCP_LOSS_GAMMA: {
+        const float mp = m + kMEps;
+        return x / mp + logf(mp);
+    }
+    default: {  // GCP_LOSS_BETA_HALF
+        const float mp = m + kMEps;
+        return 2.0f * sqrtf(mp) + 2.0f * x * rsqrtf(mp);
+    }
+    }
 }
 
 // y of a drawn entry: the semi-stratified nonzero subtracts the x = 0 term.
@@ -138,6 +174,16 @@ __device__ __forceinline__ float4 mul4(float4 a, float4 b)
 }
 __device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
 __device__ __forceinline__ float sum4(float4 a) { return (a.x + a.y) + (a.z + a.w); }
+
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialization attribute may begin while its predecessor in the
+// stream is still running; pdl_wait() blocks until that predecessor has
+// completed and its writes are visible (a no-op after a normal launch), and
+// pdl_trigger() lets the successor begin launching.  Every kernel of the path
+// calls pdl_wait() before its first global-memory access, so the overlap
+// covers launch and block scheduling only, never data.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Sticky status word: keep the first error.
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code)

@@ -1,4 +1,5 @@
 // Host-side dispatch of the fused sampled-gradient kernel instantiations.
+#include "gcp_device.cuh"
 #include "gcp_kernels.cuh"
 
 namespace gcpk {
@@ -40,11 +41,13 @@ cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int 
         if (e != cudaSuccess) return e;
     }
     void* args[] = {const_cast<GradArgs*>(&a)};
-    return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
+    return launch_pdl_ptr(f, dim3(grid), dim3(block), smem, s, args);
 }
 
 __global__ void __launch_bounds__(256) fold_kernel(const FoldArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t total4 = a.off4[a.nmodes];
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
@@ -70,8 +73,7 @@ __global__ void __launch_bounds__(256) fold_kernel(const FoldArgs a)
 
 cudaError_t launch_fold(const FoldArgs& a, int grid, cudaStream_t s)
 {
-    fold_kernel<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(fold_kernel, dim3(grid), dim3(256), 0, s, a);
 }
 
 }  // namespace gcpk

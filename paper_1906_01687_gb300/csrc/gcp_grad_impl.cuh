@@ -8,7 +8,10 @@
 // dense value gather): the random DRAM reads of 32 draws are in flight at
 // once.  Then the warp splits into groups of L lanes; a group walks its L
 // draws, each lane holding NC float4 column chunks of every mode's row (so
-// L * NC * 4 >= rank).  m_i is reduced across the group with shuffles; the
+// L * NC * 4 >= rank).  With group_draws the warp instead takes 32 / L draws
+// at a time, one per group, each group's lanes computing the same
+// descriptor: L times more warps for the same draws, for small launches
+// that are bound by latency rather than by instructions.  m_i is reduced across the group with shuffles; the
 // row updates go either to shared-memory accumulators (modes whose whole G_k
 // fits and is hit often: flushed once per CTA) or straight to global memory
 // with 16-byte vector atomics (red.global.add.v4.f32).  A mode whose rows
@@ -26,6 +29,8 @@ namespace gcpk {
 template <int D, int L, int NC, bool BF16>
 __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
@@ -47,13 +52,18 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
     for (int k = 0; k < D; ++k)
         gdst[k] = k < d ? a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k] : nullptr;
 
-    // warp-uniform loop over batches of 32 draws
-    for (int64_t wb = warp_global * 32; wb < a.dr.n_total; wb += nwarps * 32) {
+    // warp-uniform loop over batches of draws: 32 per warp step (each lane
+    // makes one descriptor, each group walks its L draws), or with
+    // group_draws 32 / L per step (each group makes its own draw's descriptor
+    // in all its lanes and takes it at once: more warps, shorter chains)
+    const int per_warp = a.group_draws ? 32 / L : 32;
+    const int steps = a.group_draws ? 1 : L;
+    for (int64_t wb = warp_global * per_warp; wb < a.dr.n_total; wb += nwarps * per_warp) {
         Draw<D> my;
-        make_draw<D>(a.dr, wb + lane, stream, my);
+        make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
 #pragma unroll 1
-        for (int b = 0; b < L; ++b) {
-            const int src = gbase + b;
+        for (int b = 0; b < steps; ++b) {
+            const int src = a.group_draws ? lane : gbase + b;
             uint32_t ix[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) ix[k] = __shfl_sync(kFull, my.ix[k], src);

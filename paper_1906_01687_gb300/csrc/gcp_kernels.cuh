@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "../../include/gcp.h"
@@ -49,6 +50,8 @@ struct GradArgs {
     uint64_t rep_stride[GCP_MAX_MODES];  // floats between replicas
     uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
     uint32_t smem_off[GCP_MAX_MODES];
+    int32_t group_draws;           // 1: each group of L lanes takes its own draw (32/L draws per warp step)
+    int32_t pad2;
 };
 
 // Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).
@@ -130,6 +133,38 @@ struct ZeroArgs {
     int8_t* out_cls;
     float w_zero;
 };
+
+// Launches a kernel with programmatic stream serialization (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+inline cudaError_t launch_pdl_ptr(const void* kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, void** args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
 
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int grid, int block, size_t smem,

@@ -13,6 +13,8 @@ namespace gcpk {
 template <int D, bool BF16>
 __global__ void __launch_bounds__(256) loss_kernel(const LossArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     __shared__ double warp_sums[8];
     __shared__ int is_last;
@@ -58,17 +60,10 @@ __global__ void __launch_bounds__(256) loss_kernel(const LossArgs a)
 cudaError_t launch_loss(const LossArgs& a, bool bf16, int grid, int block, cudaStream_t s)
 {
     const int d = a.dr.d;
-    if (d == 3) {
-        if (bf16) loss_kernel<3, true><<<grid, block, 0, s>>>(a);
-        else loss_kernel<3, false><<<grid, block, 0, s>>>(a);
-    } else if (d == 4) {
-        if (bf16) loss_kernel<4, true><<<grid, block, 0, s>>>(a);
-        else loss_kernel<4, false><<<grid, block, 0, s>>>(a);
-    } else {
-        if (bf16) loss_kernel<8, true><<<grid, block, 0, s>>>(a);
-        else loss_kernel<8, false><<<grid, block, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+    const dim3 g(grid), b(block);
+    if (d == 3) return bf16 ? launch_pdl(loss_kernel<3, true>, g, b, 0, s, a) : launch_pdl(loss_kernel<3, false>, g, b, 0, s, a);
+    if (d == 4) return bf16 ? launch_pdl(loss_kernel<4, true>, g, b, 0, s, a) : launch_pdl(loss_kernel<4, false>, g, b, 0, s, a);
+    return bf16 ? launch_pdl(loss_kernel<8, true>, g, b, 0, s, a) : launch_pdl(loss_kernel<8, false>, g, b, 0, s, a);
 }
 
 }  // namespace gcpk

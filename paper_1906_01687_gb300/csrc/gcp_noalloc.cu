@@ -66,7 +66,7 @@ extern "C" gcp_status gcp_loss_est_noalloc(int32_t d, const gcp_factors* F, gcp_
 {
     using namespace gcpk;
     if (d < 1 || d > GCP_MAX_MODES || !F || !list || !out_dev || !aligned_to(out_dev, 8)) return GCP_ERR_INVALID_ARG;
-    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_POISSON_LOG) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     if (F->rank < 1 || F->rank > 256 || F->ld < F->rank || F->ld % 4 != 0) return GCP_ERR_INVALID_ARG;
     for (int k = 0; k < d; ++k) {
         const void* a = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);

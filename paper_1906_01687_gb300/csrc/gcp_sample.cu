@@ -148,6 +148,8 @@ struct MatArgs {
 template <int D>
 __global__ void materialise_kernel(const MatArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= a.count) return;
     const int64_t j = a.first + t;
@@ -175,10 +177,9 @@ cudaError_t launch_materialise(const DrawArgs& dr, int32_t* const idx[GCP_MAX_MO
     a.count = count;
     const int block = 256;
     const unsigned grid = static_cast<unsigned>((count + block - 1) / block);
-    if (dr.d == 3) materialise_kernel<3><<<grid, block, 0, s>>>(a);
-    else if (dr.d == 4) materialise_kernel<4><<<grid, block, 0, s>>>(a);
-    else materialise_kernel<8><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    if (dr.d == 3) return launch_pdl(materialise_kernel<3>, dim3(grid), dim3(block), 0, s, a);
+    if (dr.d == 4) return launch_pdl(materialise_kernel<4>, dim3(grid), dim3(block), 0, s, a);
+    return launch_pdl(materialise_kernel<8>, dim3(grid), dim3(block), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,6 +227,8 @@ __device__ __forceinline__ uint64_t zero_stream(const ZeroArgs& a)
 template <int D>
 __global__ void __launch_bounds__(kZeroBlock) zero_count_kernel(const ZeroArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int warp_counts[kZeroBlock / 32];
     const uint64_t stream = zero_stream(a);
     const int64_t tile = blockIdx.x;
@@ -285,6 +288,8 @@ __device__ __forceinline__ int64_t block_exclusive_scan_1024(int64_t v, int64_t*
 template <int D>
 __global__ void __launch_bounds__(1024) zero_scan_kernel(const ZeroArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int64_t sh_warp[33];
     int64_t running = 0;
 #pragma unroll 1
@@ -329,6 +334,8 @@ __global__ void __launch_bounds__(1024) zero_scan_kernel(const ZeroArgs a)
 template <int D>
 __global__ void __launch_bounds__(kZeroBlock) zero_scatter_kernel(const ZeroArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned words[kZeroTile / 32];
     __shared__ int prefix[kZeroTile / 32];
     const int64_t tile = blockIdx.x;
@@ -364,21 +371,21 @@ __global__ void __launch_bounds__(kZeroBlock) zero_scatter_kernel(const ZeroArgs
 }
 
 template <int D>
-static void zero_launch(const ZeroArgs& a, cudaStream_t s)
+static cudaError_t zero_launch(const ZeroArgs& a, cudaStream_t s)
 {
-    const unsigned tiles = static_cast<unsigned>(a.first_tiles);
-    zero_count_kernel<D><<<tiles, kZeroBlock, 0, s>>>(a);
-    zero_scan_kernel<D><<<1, 1024, 0, s>>>(a);
-    zero_scatter_kernel<D><<<tiles, kZeroBlock, 0, s>>>(a);
+    const dim3 tiles(static_cast<unsigned>(a.first_tiles));
+    cudaError_t e = launch_pdl(zero_count_kernel<D>, tiles, dim3(kZeroBlock), 0, s, a);
+    if (e == cudaSuccess) e = launch_pdl(zero_scan_kernel<D>, dim3(1), dim3(1024), 0, s, a);
+    if (e == cudaSuccess) e = launch_pdl(zero_scatter_kernel<D>, tiles, dim3(kZeroBlock), 0, s, a);
+    return e;
 }
 
 cudaError_t launch_zero_sampling(const ZeroArgs& a, cudaStream_t s)
 {
     if (a.q <= 0) return cudaSuccess;
-    if (a.d == 3) zero_launch<3>(a, s);
-    else if (a.d == 4) zero_launch<4>(a, s);
-    else zero_launch<8>(a, s);
-    return cudaGetLastError();
+    if (a.d == 3) return zero_launch<3>(a, s);
+    if (a.d == 4) return zero_launch<4>(a, s);
+    return zero_launch<8>(a, s);
 }
 
 }  // namespace gcpk

@@ -29,9 +29,12 @@ STREAM_EST = 0xFFFFFFFFFFFFFFFF
 # enums (include/gcp.h)
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NO_MEMORY, ERR_SAMPLE_SHORTFALL, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = range(8)
 LOSS_GAUSSIAN, LOSS_BERNOULLI_LOGIT, LOSS_POISSON_LOG = 0, 1, 2
+LOSS_BERNOULLI_ODDS, LOSS_POISSON_IDENTITY, LOSS_GAMMA, LOSS_BETA_HALF = 3, 4, 5, 6
 SAMPLER_UNIFORM, SAMPLER_STRATIFIED, SAMPLER_SEMI_STRATIFIED = 0, 1, 2
 CLS_UNIFORM, CLS_STRAT_NZ, CLS_STRAT_ZERO, CLS_SEMI_NZ, CLS_SEMI_ZERO = range(5)
-LOSSES = {"gaussian": LOSS_GAUSSIAN, "bernoulli_logit": LOSS_BERNOULLI_LOGIT, "poisson_log": LOSS_POISSON_LOG}
+LOSSES = {"gaussian": LOSS_GAUSSIAN, "bernoulli_logit": LOSS_BERNOULLI_LOGIT, "poisson_log": LOSS_POISSON_LOG,
+          "bernoulli_odds": LOSS_BERNOULLI_ODDS, "poisson_identity": LOSS_POISSON_IDENTITY, "gamma": LOSS_GAMMA,
+          "beta_half": LOSS_BETA_HALF}
 SAMPLERS = {"uniform": SAMPLER_UNIFORM, "stratified": SAMPLER_STRATIFIED, "semi_stratified": SAMPLER_SEMI_STRATIFIED}
 
 _vp = ctypes.c_void_p
@@ -70,13 +73,15 @@ class gcp_epoch_params(ctypes.Structure):
 class gcp_tuning(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("chunks", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_min_hits", ctypes.c_int32),
-                ("max_replicas", ctypes.c_int32), ("replica_target", ctypes.c_int32)]
+                ("max_replicas", ctypes.c_int32), ("replica_target", ctypes.c_int32),
+                ("group_draws", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gcp_launch_info(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("chunks", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_mode_mask", ctypes.c_uint32),
-                ("replicas", ctypes.c_int32 * MAX_MODES)]
+                ("replicas", ctypes.c_int32 * MAX_MODES), ("group_draws", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class gcp_batch_problem(ctypes.Structure):
@@ -346,9 +351,9 @@ def gcp_get_device_status(h: Handle) -> int:
 
 
 TUNING_FIELDS = ("lanes", "chunks", "block", "grid_blocks", "smem_bytes", "smem_min_hits", "max_replicas",
-                 "replica_target")
+                 "replica_target", "group_draws", "reserved")
 TUNING_DEFAULT = dict(lanes=0, chunks=0, block=0, grid_blocks=0, smem_bytes=-1, smem_min_hits=-1,
-                      max_replicas=-1, replica_target=0)
+                      max_replicas=-1, replica_target=0, group_draws=0, reserved=0)
 
 
 def gcp_set_tuning(h: Handle, reset: bool = False, **kw):
@@ -369,7 +374,8 @@ def gcp_get_launch(h: Handle, F: Factors, n_draws: int) -> dict:
     t = gcp_launch_info()
     _check(_lib.gcp_get_launch(h.ptr, ctypes.byref(F._c()), int(n_draws), ctypes.byref(t)), "gcp_get_launch")
     return dict(lanes=t.lanes, chunks=t.chunks, block=t.block, grid_blocks=t.grid_blocks,
-                smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_mode_mask, replicas=list(t.replicas)[: h.d])
+                smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_mode_mask, replicas=list(t.replicas)[: h.d],
+                group_draws=t.group_draws)
 
 
 def gcp_profile(h: Handle, enable: bool, capacity: int = 1024):

@@ -250,17 +250,23 @@ def initial_guess(dims, rank, seed, target_norm=None, positive=False, dtype=np.f
 def batched_problems(count=64, seed=1911, dim_lo=50, dim_hi=2000, max_entries=20_000_000,
                      ranks=(4, 8, 16, 32, 64), losses=("gaussian", "bernoulli_logit", "poisson_log"),
                      s_lo=10_000, s_hi=100_000):
-    """Shapes of independent dense problems: d in {3,4}, dims ~ U[dim_lo, dim_hi]
-    redrawn until prod(dims) <= max_entries, rank from ``ranks``, loss mixed,
-    samples per iteration log-uniform in [s_lo, s_hi]."""
+    """Shapes of independent dense problems: d in {3,4}; each dim uniform in
+    [dim_lo, cap] where cap = min(dim_hi, the largest value that still lets the
+    remaining dims reach dim_lo within max_entries), dims then shuffled (plain
+    rejection of whole shapes almost never accepts a 4-way shape); rank from
+    ``ranks``; loss mixed; draws per iteration log-uniform in [s_lo, s_hi]."""
     rng = np.random.default_rng(seed)
     out = []
     for b in range(count):
         d = int(rng.integers(3, 5))
-        while True:
-            dims = tuple(int(v) for v in rng.integers(dim_lo, dim_hi + 1, d))
-            if np.prod(np.array(dims, dtype=np.float64)) <= max_entries:
-                break
+        dims, prod = [], 1
+        for k in range(d):
+            remaining = d - k - 1
+            cap = int(min(dim_hi, max_entries // (prod * dim_lo ** remaining)))
+            n = int(rng.integers(dim_lo, max(dim_lo, cap) + 1))
+            dims.append(n)
+            prod *= n
+        dims = tuple(int(v) for v in rng.permutation(dims))
         rank = int(ranks[rng.integers(0, len(ranks))])
         loss = losses[b % len(losses)]
         s = int(round(math.exp(rng.uniform(math.log(s_lo), math.log(s_hi)))))
@@ -289,3 +295,38 @@ def planted_for_loss(dims, rank, loss, seed, dtype=np.float32):
     else:
         raise ValueError(loss)
     return X.astype(dtype), factors
+
+
+# ---------------------------------------------------------------------------
+# the paper's test-problem recipes for its odds / identity-link losses
+# ---------------------------------------------------------------------------
+
+def gamma_problem(dims=(200, 150, 100, 50), rank=5, seed=1912):
+    """App. C: factor entries uniform(0,1); x_i ~ gamma with shape 1 and mean
+    m_i (an exponential draw).  Returns (X float32, factors)."""
+    rng = np.random.default_rng(seed)
+    factors = [rng.random((n, rank)) for n in dims]
+    M = dense_from_factors(factors)
+    X = rng.exponential(M)
+    return X.astype(np.float32), factors
+
+
+def binary_odds_problem(dims=(200, 150, 100, 50), rank=5, delta=0.15, p_high=0.9, p_low=0.0025, seed=1913):
+    """App. D: factors 1..r-1 sparse (density delta, nonzero entries
+    N(root_d(p_high / (1 - p_high)), 0.5^2)), factor r dense with entries
+    root_d(p_low / (1 - p_low)); x_i ~ Bernoulli(m_i / (1 + m_i)) with m the
+    odds.  Dense generation (for moderate sizes).  Returns (X float32, factors)."""
+    rng = np.random.default_rng(seed)
+    d = len(dims)
+    hi = (p_high / (1 - p_high)) ** (1.0 / d)
+    lo = (p_low / (1 - p_low)) ** (1.0 / d)
+    factors = []
+    for n in dims:
+        a = np.zeros((n, rank))
+        mask = rng.random((n, rank - 1)) < delta
+        a[:, : rank - 1] = np.where(mask, np.abs(rng.normal(hi, 0.5, (n, rank - 1))), 0.0)
+        a[:, rank - 1] = lo
+        factors.append(a)
+    M = dense_from_factors(factors)
+    X = (rng.random(M.shape) < M / (1.0 + M)).astype(np.float32)
+    return X, factors

@@ -283,3 +283,18 @@ def test_profile_events_count_gradient_kernels():
     ms, n = g.gcp_profile_read(h)
     assert n == 0
     g.gcp_profile(h, False)
+
+
+def test_gamma_problem_fits_with_projection():
+    """App. C's gamma problem (scaled down): GCP-Adam with the gamma loss and
+    the projection max(A, 0) lowers F-hat and keeps the factors nonnegative."""
+    from paper_1906_01687_gb300 import synth
+    from paper_1906_01687_gb300.adam import GcpAdam
+    g = gcp()
+    X, true = synth.gamma_problem(dims=(20, 15, 10, 5), rank=3)
+    A0 = synth.initial_guess(X.shape, 3, 4, target_norm=float(np.linalg.norm(X)), positive=True)
+    run = GcpAdam(g.DataTensor.dense(X), A0, g.LOSS_GAMMA, g.SAMPLER_UNIFORM, 0, 500, 0, 5000, seed=3, est_seed=4,
+                  alpha=0.01, tau=100, lower=0.0)
+    st = run.fit(max_epochs=10)
+    assert run.history[-1] < run.history[0] and math.isfinite(run.history[-1])
+    assert all((a >= 0).all() for a in run.factors())

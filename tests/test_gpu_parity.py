@@ -211,7 +211,8 @@ def test_every_launch_shape_agrees():
         ref = oracle.grad(dims, f64(A), 0, SO)
         for (lanes, chunks) in shapes:
             for acc in (dict(max_replicas=0), dict(), dict(max_replicas=8, replica_target=1),
-                        dict(max_replicas=0, smem_bytes=65536, smem_min_hits=0)):
+                        dict(max_replicas=0, smem_bytes=65536, smem_min_hits=0), dict(group_draws=1),
+                        dict(group_draws=1, max_replicas=0)):
                 for grid in (0, 3):
                     g.gcp_set_tuning(h, lanes=lanes, chunks=chunks, grid_blocks=grid, **acc)
                     G = run_grad(h, F, 0, S=S)
@@ -300,3 +301,46 @@ def test_autotuner_keeps_results():
     G = run_grad(h, F, 0, S=S)
     SO = oracle.sample(XO, oracle.UNIFORM, 0, 20000, 2, 4)
     assert_grad_close(grad_to_numpy(G, 10), oracle.grad(dims, f64(A), 0, SO))
+
+
+# ---------------------------------------------------------------------------
+# the paper's odds / identity-link losses, on nonnegative models
+# ---------------------------------------------------------------------------
+POSITIVE = [3, 4, 5, 6]
+POS_IDS = {3: "bernoulli_odds", 4: "poisson_identity", 5: "gamma", 6: "beta_half"}
+
+
+@pytest.mark.parametrize("loss", POSITIVE, ids=POS_IDS.get)
+@pytest.mark.parametrize("kind", ["uniform", "stratified", "semi_stratified"])
+def test_positive_losses_gradient_and_estimate(loss, kind):
+    g = gcp()
+    rs = np.random.default_rng(30 + loss)
+    rank = 6
+    if kind == "uniform":
+        dims = (20, 30, 40)
+        X = rs.exponential(1.0, dims).astype(np.float32) if loss in (5, 6) else rs.poisson(1.0, dims).astype(np.float32)
+        if loss == 3:
+            X = (X > 0).astype(np.float32)
+        h = g.Handle(g.DataTensor.dense(X))
+        XO = oracle.Tensor(dims, dense=X.astype(np.float64))
+        p, q = 0, 4001
+    else:
+        dims = (40, 30, 20, 6)
+        idx, vals = sparse_random(dims, 6000, 31, binary=(loss == 3))
+        h = g.Handle(g.DataTensor.coo(dims, idx, vals))
+        XO = oracle_sparse(dims, idx, vals)
+        p, q = 2001, 2002
+    A = [(rs.uniform(0.2, 1.0, (n, rank)) * (1.0 / rank) ** (1 / len(dims))).astype(np.float32) for n in dims]
+    F = g.Factors(A)
+    S = g.Sampling(g.SAMPLERS[kind], p, q, seed=5, stream=2)
+    G = run_grad(h, F, loss, S=S)
+    SO = oracle.sample(XO, g.SAMPLERS[kind], p, q, 5, 2)
+    assert_grad_close(grad_to_numpy(G, rank), oracle.grad(dims, f64(A), loss, SO),
+                      oracle.grad_abs(dims, f64(A), loss, SO))
+    L = g.gcp_sample(h, g.Sampling(g.SAMPLERS[kind], p, q, seed=6, stream=g.STREAM_EST))
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.gcp_loss_est(h, F, loss, L, out)
+    torch.cuda.synchronize()
+    SE = oracle.sample(XO, g.SAMPLERS[kind], p, q, 6, 2**64 - 1)
+    assert abs(out.item() - oracle.loss_estimate(dims, f64(A), loss, SE)) <= \
+        LOSS_RTOL * oracle.loss_abs(dims, f64(A), loss, SE)

@@ -272,3 +272,43 @@ def test_abs_scales_bound_the_sums():
     Gabs = oracle.grad_abs(dims, Apos, oracle.GAUSSIAN, Spos)
     for g, ga in zip(G, Gabs):
         np.testing.assert_allclose(-g, ga, rtol=1e-12)
+
+
+def numpy_g_positive(loss, X, M):
+    Mp = M + oracle.M_EPS
+    if loss == oracle.BERNOULLI_ODDS:
+        return 1.0 / (Mp + 1.0) - X / Mp
+    if loss == oracle.POISSON_IDENTITY:
+        return 1.0 - X / Mp
+    if loss == oracle.GAMMA:
+        return -X / Mp ** 2 + 1.0 / Mp
+    return Mp ** -0.5 - X * Mp ** -1.5
+
+
+@pytest.mark.parametrize("loss", [oracle.BERNOULLI_ODDS, oracle.POISSON_IDENTITY, oracle.GAMMA, oracle.BETA_HALF])
+def test_positive_losses_full_gradient_and_derivative(loss):
+    """Odds/identity-link losses on a nonnegative model: the full gradient is
+    the einsum MTTKRP of Y, and the sampled gradient is dF-hat/dA."""
+    dims = (3, 4, 5)
+    rng = np.random.default_rng(50 + loss)
+    A = [rng.uniform(0.2, 1.0, (n, 2)) for n in dims]
+    M = einsum_model(A)
+    X = rng.poisson(1.0, dims).astype(float) if loss != oracle.GAMMA else rng.exponential(M)
+    if loss == oracle.BERNOULLI_ODDS:
+        X = (X > 0).astype(float)
+    G, _ = oracle.full_grad(dims, A, loss, X)
+    Y = numpy_g_positive(loss, X, M)
+    for k in range(3):
+        np.testing.assert_allclose(G[k], einsum_mttkrp(Y, A, k), rtol=1e-11, atol=1e-11)
+    S = random_sample_list(dims, X, 30, 60)
+    Gs = oracle.grad(dims, A, loss, S)
+    h = 1e-6
+    for k in range(3):
+        for i in range(dims[k]):
+            for j in range(2):
+                Ap = [a.copy() for a in A]
+                Am = [a.copy() for a in A]
+                Ap[k][i, j] += h
+                Am[k][i, j] -= h
+                fd = (oracle.loss_estimate(dims, Ap, loss, S) - oracle.loss_estimate(dims, Am, loss, S)) / (2 * h)
+                assert Gs[k][i, j] == pytest.approx(fd, rel=2e-5, abs=2e-6)

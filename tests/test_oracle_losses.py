@@ -75,3 +75,54 @@ def test_entry_forms(loss):
         assert oracle.entry_f(loss, cls, x, m, w) == pytest.approx(w * f)
     assert oracle.entry_y(loss, oracle.CLS_SEMI_NZ, x, m, w) == pytest.approx(w * (g - g0))
     assert oracle.entry_f(loss, oracle.CLS_SEMI_NZ, x, m, w) == pytest.approx(w * (f - f0))
+
+
+# ---------------------------------------------------------------------------
+# the paper's own odds / identity-link losses (Section 1, Sections 5.2-5.4)
+# ---------------------------------------------------------------------------
+POSITIVE_LOSSES = [oracle.BERNOULLI_ODDS, oracle.POISSON_IDENTITY, oracle.GAMMA, oracle.BETA_HALF]
+
+
+@pytest.mark.parametrize("m", [0.05, 0.7, 1.0, 3.0])
+@pytest.mark.parametrize("x", [0.0, 1.0])
+def test_bernoulli_odds_is_negative_log_likelihood(x, m):
+    # m is the odds of a one: P(x = 1) = m / (1 + m)
+    nll = -stats.bernoulli.logpmf(int(x), m / (1.0 + m))
+    assert oracle.loss_f(oracle.BERNOULLI_ODDS, x, m) == pytest.approx(nll, rel=1e-8)
+
+
+@pytest.mark.parametrize("m", [0.3, 1.0, 4.5])
+@pytest.mark.parametrize("x", [0, 1, 5])
+def test_poisson_identity_is_negative_log_likelihood(x, m):
+    nll = -stats.poisson.logpmf(x, m) - special.gammaln(x + 1)
+    assert oracle.loss_f(oracle.POISSON_IDENTITY, float(x), m) == pytest.approx(nll, rel=1e-8, abs=1e-9)
+
+
+@pytest.mark.parametrize("m", [0.3, 1.0, 4.5])
+@pytest.mark.parametrize("x", [0.2, 1.0, 7.0])
+def test_gamma_is_exponential_negative_log_likelihood(x, m):
+    # gamma with shape k = 1 (App. C) and mean m is the exponential distribution
+    nll = -stats.expon.logpdf(x, scale=m)
+    assert oracle.loss_f(oracle.GAMMA, x, m) == pytest.approx(nll, rel=1e-8)
+
+
+def test_beta_half_closed_form():
+    for x, m in [(0.0, 4.0), (1.0, 1.0), (9.0, 0.25)]:
+        assert oracle.loss_f(oracle.BETA_HALF, x, m) == pytest.approx(2 * math.sqrt(m) + 2 * x / math.sqrt(m), rel=1e-8)
+    # minimised at m = x
+    fs = [oracle.loss_f(oracle.BETA_HALF, 2.0, m) for m in (1.5, 2.0, 2.5)]
+    assert fs[1] < fs[0] and fs[1] < fs[2]
+
+
+@pytest.mark.parametrize("loss", POSITIVE_LOSSES)
+@pytest.mark.parametrize("x", [0.0, 1.0, 2.5])
+@pytest.mark.parametrize("m", [0.2, 0.9, 3.0])
+def test_positive_loss_g_is_derivative(loss, x, m):
+    h = 1e-6
+    fd = (oracle.loss_f(loss, x, m + h) - oracle.loss_f(loss, x, m - h)) / (2 * h)
+    assert oracle.loss_g(loss, x, m) == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("loss", POSITIVE_LOSSES)
+def test_positive_losses_finite_at_zero_model(loss):
+    assert math.isfinite(oracle.loss_f(loss, 1.0, 0.0)) and math.isfinite(oracle.loss_g(loss, 1.0, 0.0))

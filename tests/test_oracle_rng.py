@@ -104,3 +104,4 @@ def test_linear_key_is_row_major():
     ref = np.arange(np.prod(dims)).reshape(dims)
     for ix in [(0, 0, 0), (3, 4, 5), (1, 2, 3), (2, 0, 5)]:
         assert oracle.linear_key(dims, ix) == ref[ix]
+
