@@ -102,6 +102,9 @@ typedef struct gcp_tensor {
     int64_t nnz;                      /* sparse only */
     const float *vals;
     const int32_t *idx[GCP_MAX_MODES];
+    const float *weights;             /* dense only: entry weights v of weighted GCP (Eq. (4.5)),
+                                         prod(dims) FP32, row-major, device; NULL = all ones.
+                                         A weight of 0 marks a missing entry. */
 } gcp_tensor;
 
 /* Factor matrices A_k of the CP model (Eq. (1.1)).  Mode k is an n_k x ld
@@ -226,7 +229,9 @@ int64_t gcp_sample_count(const gcp_sampling *S);
    weight w (omega/s, eta/p, zeta/q or omega/q, computed in FP64 on the host
    and rounded once) and its class.  out->n must equal gcp_sample_count(S).
    stratified needs a sparse X with prod(dims) < 2^64 (else
-   GCP_ERR_UNSUPPORTED); uniform needs a dense X.  May allocate library
+   GCP_ERR_UNSUPPORTED); uniform over a sparse X looks each drawn index up
+   among the nonzeros (value or 0; also prod(dims) < 2^64); uniform over a
+   dense X with entry weights gives the draw weight (omega/s) v_i.  May allocate library
    scratch on the first stratified call (cudaMalloc): make that first call
    before any stream capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
    the device status; the unfilled zero slots then hold weight 0. */

@@ -76,8 +76,11 @@ def _load():
     lib.orc_is_nonzero.restype = i32
     lib.orc_sample_count.argtypes = [i32, i64, i64]
     lib.orc_sample_count.restype = i64
-    lib.orc_sample.argtypes = [i32, vp, i32, vp, i64, vp, vp, vp, i32, i64, i64,
+    lib.orc_sample.argtypes = [i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, i32, i64, i64,
                                u64, u64, u64, f64, vp, vp, vp, vp, P(i64)]
+    lib.orc_sorted_pairs.argtypes = [i32, vp, i64, vp, vp, vp, vp]
+    lib.orc_sparse_value.argtypes = [i64, vp, vp, u64]
+    lib.orc_sparse_value.restype = f64
     lib.orc_sample.restype = i32
     lib.orc_entry_y.argtypes = [i32, i32, f64, f64, f64]
     lib.orc_entry_y.restype = f64
@@ -176,8 +179,9 @@ class Tensor:
     sparse: ``coo`` is nnz x d (int64), ``vals`` nnz values or None (all ones).
     """
 
-    def __init__(self, dims, dense=None, coo=None, vals=None):
+    def __init__(self, dims, dense=None, coo=None, vals=None, weights=None):
         self.dims = _i64(dims)
+        self.weights = None if weights is None else _f64(np.asarray(weights).reshape(-1))
         self.d = len(self.dims)
         self.sparse = coo is not None
         if self.sparse:
@@ -192,6 +196,15 @@ class Tensor:
         else:
             self.dense = _f64(np.asarray(dense).reshape(-1))
             self.coo, self.vals, self.nnz, self._keys = None, None, 0, None
+
+    def sorted_pairs(self):
+        """(keys, values) of the nonzeros sorted by key: the value lookup of uniform sampling."""
+        if getattr(self, "_pairs", None) is None:
+            keys = np.zeros(self.nnz, dtype=np.uint64)
+            vals = np.zeros(self.nnz)
+            _load().orc_sorted_pairs(self.d, _p(self.dims), self.nnz, _p(self.coo), _p(self.vals), _p(keys), _p(vals))
+            self._pairs = (keys, vals)
+        return self._pairs
 
     def sorted_keys(self) -> np.ndarray:
         """Sorted row-major linear keys of the nonzeros (Section 4.2's lookup list)."""
@@ -254,8 +267,11 @@ def sample(X: Tensor, kind: int, p: int, q: int, seed: int, stream: int,
     cls = np.zeros(n, dtype=np.int8)
     used = ctypes.c_int64(0)
     keys = X.sorted_keys() if (X.sparse and kind == STRATIFIED) else None
-    st = lib.orc_sample(X.d, _p(X.dims), int(X.sparse), _p(X.dense), X.nnz, _p(X.coo), _p(X.vals),
-                        _p(keys), kind, p, q, seed, problem, stream, rho,
+    svals = None
+    if X.sparse and kind == UNIFORM:
+        keys, svals = X.sorted_pairs()
+    st = lib.orc_sample(X.d, _p(X.dims), int(X.sparse), _p(X.dense), _p(X.weights), X.nnz, _p(X.coo), _p(X.vals),
+                        _p(keys), _p(svals), kind, p, q, seed, problem, stream, rho,
                         _p(idx), _p(x), _p(w), _p(cls), ctypes.byref(used))
     if st == ERR_SHORTFALL:
         raise RuntimeError(f"stratified zero sampling fell short after {used.value} candidates")

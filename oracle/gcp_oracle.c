@@ -239,6 +239,44 @@ void orc_sorted_keys(int d, const int64_t *dims, int64_t nnz, const int64_t *coo
     qsort(keys, (size_t)nnz, sizeof(uint64_t), cmp_u64);
 }
 
+/* Sorts (key, value) pairs by key: the value lookup of uniform sampling
+   over a sparse tensor.  vals NULL means all ones. */
+typedef struct { uint64_t key; double val; } orc_pair;
+
+static int cmp_pair(const void *a, const void *b)
+{
+    uint64_t x = ((const orc_pair *)a)->key, y = ((const orc_pair *)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void orc_sorted_pairs(int d, const int64_t *dims, int64_t nnz, const int64_t *coo_idx, const double *vals,
+                      uint64_t *keys_out, double *vals_out)
+{
+    orc_pair *p = (orc_pair *)malloc((size_t)nnz * sizeof(orc_pair));
+    for (int64_t e = 0; e < nnz; ++e) {
+        p[e].key = orc_linear_key(d, dims, coo_idx + e * d);
+        p[e].val = vals ? vals[e] : 1.0;
+    }
+    qsort(p, (size_t)nnz, sizeof(orc_pair), cmp_pair);
+    for (int64_t e = 0; e < nnz; ++e) {
+        keys_out[e] = p[e].key;
+        vals_out[e] = p[e].val;
+    }
+    free(p);
+}
+
+/* x at a linear key of a sparse tensor: its value, or 0 when not a nonzero. */
+double orc_sparse_value(int64_t nnz, const uint64_t *sorted_keys, const double *sorted_vals, uint64_t key)
+{
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (sorted_keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < nnz && sorted_keys[lo] == key) ? sorted_vals[lo] : 0.0;
+}
+
 int orc_is_nonzero(int64_t nnz, const uint64_t *sorted_keys, uint64_t key)
 {
     int64_t lo = 0, hi = nnz; /* search [lo, hi) */
@@ -269,9 +307,9 @@ int64_t orc_sample_count(int kind, int64_t p, int64_t q)
 }
 
 int orc_sample(int d, const int64_t *dims, int sparse,
-               const double *dense_vals,
+               const double *dense_vals, const double *dense_weights,
                int64_t nnz, const int64_t *coo_idx, const double *coo_vals,
-               const uint64_t *sorted_keys,
+               const uint64_t *sorted_keys, const double *sorted_vals,
                int kind, int64_t p, int64_t q,
                uint64_t seed, uint64_t problem, uint64_t stream, double rho,
                int64_t *idx_out, double *x_out, double *w_out, int8_t *cls_out,
@@ -283,13 +321,20 @@ int orc_sample(int d, const int64_t *dims, int sparse,
     if (candidates_used) *candidates_used = 0;
 
     if (kind == ORC_UNIFORM) {
-        /* Alg. 1 (dense tensor): s = q draws, weight omega / s. */
-        if (sparse) return ORC_ERR_ARG;
+        /* Alg. 1: s = q draws, weight omega / s; a sparse tensor's value is
+           looked up among its nonzeros.  With entry weights v (Eq. (4.5),
+           dense tensors) the draw's weight is (omega / s) v_i. */
         for (int64_t j = 0; j < q; ++j) {
             int64_t *ix = idx_out + j * d;
             orc_draw_multi_index(d, dims, seed, problem, stream, ORC_TAG_UNIFORM, (uint64_t)j, ix);
-            x_out[j] = dense_vals[orc_linear_key(d, dims, ix)];
-            w_out[j] = omega / (double)q;
+            uint64_t key = orc_linear_key(d, dims, ix);
+            if (sparse) {
+                x_out[j] = orc_sparse_value(nnz, sorted_keys, sorted_vals, key);
+                w_out[j] = omega / (double)q;
+            } else {
+                x_out[j] = dense_vals[key];
+                w_out[j] = (omega / (double)q) * (dense_weights ? dense_weights[key] : 1.0);
+            }
             cls_out[j] = ORC_CLS_UNIFORM;
         }
         return ORC_OK;

@@ -13,7 +13,7 @@
 
 using namespace gcpk;
 
-static_assert(sizeof(gcp_tensor) == 152, "gcp_tensor layout");
+static_assert(sizeof(gcp_tensor) == 160, "gcp_tensor layout");
 static_assert(sizeof(gcp_factors) == 144, "gcp_factors layout");
 static_assert(sizeof(gcp_sampling) == 56, "gcp_sampling layout");
 static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
@@ -36,6 +36,7 @@ struct gcp_handle {
     int num_sms = 0;
     // nonzero-key hash (stratified)
     unsigned long long* table = nullptr;
+    float* table_vals = nullptr;
     uint64_t table_mask = 0;
     // stratified zero list and its pass scratch
     int64_t zq_cap = 0;
@@ -117,7 +118,8 @@ gcp_status check_spec(const gcp_handle* h, const gcp_sampling* S)
     if (S->p > (int64_t(1) << 40) || S->q > (int64_t(1) << 40)) return GCP_ERR_INVALID_ARG;
     switch (S->kind) {
     case GCP_SAMPLER_UNIFORM:
-        if (h->X.sparse) return GCP_ERR_UNSUPPORTED;  // uniform sampling of a sparse tensor needs a value lookup
+        // over a sparse tensor each draw's value is looked up by its linear key
+        if (h->X.sparse && !h->omega_fits_u64) return GCP_ERR_UNSUPPORTED;
         return GCP_OK;
     case GCP_SAMPLER_STRATIFIED:
         if (!h->X.sparse) return GCP_ERR_INVALID_ARG;
@@ -143,6 +145,10 @@ DrawArgs make_draw_args(const gcp_handle* h, const gcp_sampling* S, const gcp_sa
         a.strides[k] = h->strides[k];
     }
     a.X = h->X.sparse ? nullptr : h->X.vals;
+    a.W = h->X.sparse ? nullptr : h->X.weights;
+    a.table = h->table;
+    a.table_vals = h->table_vals;
+    a.table_mask = h->table_mask;
     a.nz_rec = h->recs;
     a.rec_int4 = h->rec_int4;
     a.nnz = h->X.nnz;
@@ -161,7 +167,7 @@ DrawArgs make_draw_args(const gcp_handle* h, const gcp_sampling* S, const gcp_sa
     a.stream = S->stream;
     const double omega = h->omega, eta = static_cast<double>(h->X.nnz);
     if (S->kind == GCP_SAMPLER_UNIFORM) {
-        a.src = kSrcUniformDense;
+        a.src = h->X.sparse ? kSrcUniformSparse : kSrcUniformDense;
         a.p = 0;
         a.n_total = S->q;
         a.w_first = S->q > 0 ? static_cast<float>(omega / static_cast<double>(S->q)) : 0.0f;
@@ -195,10 +201,11 @@ gcp_status ensure_hash(gcp_handle* h, cudaStream_t s)
     uint64_t cap = 1024;
     while (cap < 2 * static_cast<uint64_t>(h->X.nnz)) cap <<= 1;
     GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->table), cap * sizeof(unsigned long long)));
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->table_vals), cap * sizeof(float)));
     h->table_mask = cap - 1;
     GCP_CUDA_TRY(cudaMemsetAsync(h->table, 0xFF, cap * sizeof(unsigned long long), s));
-    GCP_CUDA_TRY(launch_hash_build(h->recs, h->rec_int4, h->X.d, h->strides, h->X.nnz, h->table, h->table_mask,
-                                   h->d_status, s));
+    GCP_CUDA_TRY(launch_hash_build(h->recs, h->rec_int4, h->X.d, h->strides, h->X.nnz, h->table, h->table_vals,
+                                   h->table_mask, h->d_status, s));
     return GCP_OK;
 }
 
@@ -485,6 +492,7 @@ gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream
         h->X.idx[k] = nullptr;
     }
     if (!X->sparse) h->X.nnz = 0;
+    if (X->sparse) h->X.weights = nullptr;
     uint64_t om = 0;
     h->omega_fits_u64 = omega_u64(h->X, &om);
     h->omega = 1.0;
@@ -583,6 +591,7 @@ gcp_status gcp_destroy(gcp_handle* h)
     cudaFree(h->recs);
     cudaFree(h->d_status);
     cudaFree(h->table);
+    cudaFree(h->table_vals);
     cudaFree(h->zidx_base);
     cudaFree(h->zcount);
     cudaFree(h->mask_words);
@@ -653,6 +662,10 @@ gcp_status gcp_sample(gcp_handle* h, const gcp_sampling* S, const gcp_samples* o
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last_stream = s;
     if (out->n == 0) return GCP_OK;
+    if (S->kind == GCP_SAMPLER_UNIFORM && h->X.sparse) {
+        st = ensure_hash(h, s);
+        if (st != GCP_OK) return st;
+    }
     DrawArgs dr = make_draw_args(h, S, nullptr, nullptr);
     if (S->kind != GCP_SAMPLER_STRATIFIED) {
         GCP_CUDA_TRY(launch_materialise(dr, out->idx, out->x, out->w, out->cls, 0, dr.n_total, h->d_status, s));
@@ -672,6 +685,9 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
     if (st != GCP_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last_stream = s;
+    if (S->kind == GCP_SAMPLER_UNIFORM && h->X.sparse) {
+        if ((st = ensure_hash(h, s)) != GCP_OK) return st;
+    }
     if (S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
         if ((st = ensure_hash(h, s)) != GCP_OK) return st;
         if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 1023) / 1024)) != GCP_OK) return st;
@@ -693,6 +709,10 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     st = S ? check_spec(h, S) : check_list(h, list);
     if (st != GCP_OK) return st;
     h->last_stream = s;
+    if (S && S->kind == GCP_SAMPLER_UNIFORM && h->X.sparse) {
+        st = ensure_hash(h, s);
+        if (st != GCP_OK) return st;
+    }
     GradArgs a{};
     a.dr = make_draw_args(h, S, list, stream_dev);
     if (a.dr.n_total == 0) return GCP_OK;

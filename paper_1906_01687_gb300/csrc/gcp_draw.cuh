@@ -7,6 +7,40 @@
 
 namespace gcpk {
 
+// ---------------------------------------------------------------------------
+// Nonzero-key hash: open addressing with linear probing over a power-of-two
+// table at most half full; slot = splitmix64 finaliser of the key (Steele,
+// Lea, Flood: "Fast splittable pseudorandom number generators", 2014).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// The slot holding key, or -1 when key is not a nonzero.
+__device__ __forceinline__ int64_t hash_find(const unsigned long long* __restrict__ table, uint64_t mask,
+                                             uint64_t key)
+{
+    uint64_t slot = mix64(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long v = __ldg(table + slot);
+        if (v == key) return static_cast<int64_t>(slot);
+        if (v == kEmptyKey) return -1;
+        slot = (slot + 1) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ bool hash_contains(const unsigned long long* __restrict__ table, uint64_t mask,
+                                              uint64_t key)
+{
+    return hash_find(table, mask, key) >= 0;
+}
+
 template <int D>
 struct Draw {
     uint32_t ix[D];
@@ -43,16 +77,22 @@ __device__ __forceinline__ void make_draw(const DrawArgs& a, int64_t j, uint64_t
         return;
     }
 
-    if (a.src == kSrcUniformDense) {
-        // Alg. 1: i_k = randi(n_k); x = X(i); weight omega / s
+    if (a.src == kSrcUniformDense || a.src == kSrcUniformSparse) {
+        // Alg. 1: i_k = randi(n_k); x = X(i); weight omega / s (times v_i with entry weights)
         draw_index<D>(a.dims, a.seed, a.problem, stream, kTagUniform, static_cast<uint64_t>(j), a.d, o.ix);
         uint64_t lin = 0;
 #pragma unroll
         for (int k = 0; k < D; ++k)
             if (k < a.d) lin += static_cast<uint64_t>(o.ix[k]) * a.strides[k];
-        o.x = __ldg(a.X + lin);
         o.w = a.w_first;
         o.cls = GCP_CLS_UNIFORM;
+        if (a.src == kSrcUniformDense) {
+            o.x = __ldg(a.X + lin);
+            if (a.W) o.w *= __ldg(a.W + lin);
+        } else {  // a sparse tensor: the value of a nonzero, else 0
+            const int64_t slot = hash_find(a.table, a.table_mask, lin);
+            o.x = slot >= 0 ? __ldg(a.table_vals + slot) : 0.0f;
+        }
         return;
     }
 

@@ -14,7 +14,8 @@ namespace gcpk {
 enum Source : int32_t {
     kSrcUniformDense = 0,  // Alg. 1 over a dense tensor, generated in-kernel
     kSrcSparse = 1,        // Algs. 2/3: nonzeros generated in-kernel, zeros generated (semi) or listed (stratified)
-    kSrcList = 2           // a materialised list
+    kSrcList = 2,          // a materialised list
+    kSrcUniformSparse = 3  // Alg. 1 over a sparse tensor: values looked up in the nonzero hash
 };
 
 struct DrawArgs {
@@ -31,6 +32,10 @@ struct DrawArgs {
     float w_first;        // uniform: omega/s; sparse: eta/p
     float w_second;       // stratified: zeta/q; semi: omega/q
     const float* X;       // dense values
+    const float* W;       // dense entry weights (Eq. (4.5)), or null
+    const unsigned long long* table;  // nonzero key hash (kSrcUniformSparse)
+    const float* table_vals;          // the value of each occupied slot
+    uint64_t table_mask;
     const int4* nz_rec;   // packed nonzero records
     int64_t nnz;
     const int32_t* zidx[GCP_MAX_MODES];  // stratified zero list (scratch)
@@ -178,7 +183,8 @@ cudaError_t launch_materialise(const DrawArgs& a, int32_t* const idx[GCP_MAX_MOD
                                int8_t* cls, int64_t first, int64_t count, int32_t* status, cudaStream_t s);
 cudaError_t launch_zero_sampling(const ZeroArgs& a, cudaStream_t s);
 cudaError_t launch_hash_build(const int4* recs, int rec_int4, int d, const uint64_t* strides, int64_t nnz,
-                              unsigned long long* table, uint64_t mask, int32_t* status, cudaStream_t s);
+                              unsigned long long* table, float* table_vals, uint64_t mask, int32_t* status,
+                              cudaStream_t s);
 cudaError_t launch_pack_records(const gcp_tensor& X, int4* recs, int rec_int4, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_epoch(const EpochArgs& a, int grid, cudaStream_t s);

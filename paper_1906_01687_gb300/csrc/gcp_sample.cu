@@ -5,7 +5,6 @@
 
 namespace gcpk {
 
-constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
 
 // ---------------------------------------------------------------------------
 // Packed nonzero records: the d indices then the value's bits, padded to
@@ -54,37 +53,13 @@ cudaError_t launch_pack_records(const gcp_tensor& X, int4* recs, int rec_int4, c
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Nonzero-key hash: open addressing with linear probing over a power-of-two
-// table at most half full; slot = splitmix64 finaliser of the key (Steele,
-// Lea, Flood: "Fast splittable pseudorandom number generators", 2014).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t mix64(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ bool hash_contains(const unsigned long long* __restrict__ table, uint64_t mask,
-                                              uint64_t key)
-{
-    uint64_t slot = mix64(key) & mask;
-    for (uint64_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long v = __ldg(table + slot);
-        if (v == key) return true;
-        if (v == kEmptyKey) return false;
-        slot = (slot + 1) & mask;
-    }
-    return false;
-}
-
 struct HashArgs {
     const int4* recs;
     int32_t rec_int4, d;
     uint64_t strides[GCP_MAX_MODES];
     int64_t nnz;
     unsigned long long* table;
+    float* table_vals;
     uint64_t mask;
     int32_t* status;
 };
@@ -110,14 +85,19 @@ __global__ void hash_build_kernel(const HashArgs a)
     uint64_t slot = mix64(key) & a.mask;
     for (uint64_t probe = 0; probe <= a.mask; ++probe) {
         const unsigned long long prev = atomicCAS(a.table + slot, kEmptyKey, static_cast<unsigned long long>(key));
-        if (prev == kEmptyKey || prev == key) return;
+        if (prev == kEmptyKey) {
+            a.table_vals[slot] = __int_as_float(words[a.d]);  // the value stored after the indices
+            return;
+        }
+        if (prev == key) return;
         slot = (slot + 1) & a.mask;
     }
     set_status(a.status, GCP_ERR_NO_MEMORY);  // table full: cannot happen at load <= 1/2
 }
 
 cudaError_t launch_hash_build(const int4* recs, int rec_int4, int d, const uint64_t* strides, int64_t nnz,
-                              unsigned long long* table, uint64_t mask, int32_t* status, cudaStream_t s)
+                              unsigned long long* table, float* table_vals, uint64_t mask, int32_t* status,
+                              cudaStream_t s)
 {
     HashArgs a{};
     a.recs = recs;
@@ -126,6 +106,7 @@ cudaError_t launch_hash_build(const int4* recs, int rec_int4, int d, const uint6
     for (int k = 0; k < d; ++k) a.strides[k] = strides[k];
     a.nnz = nnz;
     a.table = table;
+    a.table_vals = table_vals;
     a.mask = mask;
     a.status = status;
     const int block = 256;

@@ -43,7 +43,7 @@ _P8 = _vp * MAX_MODES
 
 class gcp_tensor(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("sparse", ctypes.c_int32), ("dims", ctypes.c_int64 * MAX_MODES),
-                ("nnz", ctypes.c_int64), ("vals", _vp), ("idx", _P8)]
+                ("nnz", ctypes.c_int64), ("vals", _vp), ("idx", _P8), ("weights", _vp)]
 
 
 class gcp_factors(ctypes.Structure):
@@ -190,6 +190,7 @@ class DataTensor:
     dims: tuple
     vals: Optional[torch.Tensor] = None
     idx: Optional[List[torch.Tensor]] = None
+    weights: Optional[torch.Tensor] = None  # dense entry weights (Eq. (4.5)), None = all ones
 
     @property
     def sparse(self) -> bool:
@@ -208,12 +209,14 @@ class DataTensor:
         t.vals = None if self.vals is None else self.vals.data_ptr()
         if self.sparse:
             t.idx = _p8(self.idx)
+        t.weights = None if self.weights is None else self.weights.data_ptr()
         return t
 
     @staticmethod
-    def dense(X, device="cuda") -> "DataTensor":
+    def dense(X, device="cuda", weights=None) -> "DataTensor":
         x = torch.as_tensor(X).to(device=device, dtype=torch.float32).contiguous()
-        return DataTensor(tuple(x.shape), vals=x.reshape(-1))
+        w = None if weights is None else torch.as_tensor(weights).to(device=device, dtype=torch.float32).contiguous()
+        return DataTensor(tuple(x.shape), vals=x.reshape(-1), weights=None if w is None else w.reshape(-1))
 
     @staticmethod
     def coo(dims, idx, vals=None, device="cuda") -> "DataTensor":

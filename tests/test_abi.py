@@ -63,7 +63,7 @@ def test_host_side_validation_without_gpu(lib_path):
 
 def test_struct_layouts_match_header():
     from paper_1906_01687_gb300 import gcp
-    assert ctypes.sizeof(gcp.gcp_tensor) == 152
+    assert ctypes.sizeof(gcp.gcp_tensor) == 160
     assert ctypes.sizeof(gcp.gcp_factors) == 144
     assert ctypes.sizeof(gcp.gcp_sampling) == 56
     assert ctypes.sizeof(gcp.gcp_samples) == 96

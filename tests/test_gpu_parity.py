@@ -344,3 +344,44 @@ def test_positive_losses_gradient_and_estimate(loss, kind):
     SE = oracle.sample(XO, g.SAMPLERS[kind], p, q, 6, 2**64 - 1)
     assert abs(out.item() - oracle.loss_estimate(dims, f64(A), loss, SE)) <= \
         LOSS_RTOL * oracle.loss_abs(dims, f64(A), loss, SE)
+
+
+# ---------------------------------------------------------------------------
+# uniform sampling of a sparse tensor; entry weights (weighted GCP, Eq. (4.5))
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("loss", [0, 2], ids=LOSS_IDS.get)
+def test_uniform_over_sparse_tensor(loss):
+    g = gcp()
+    dims = (40, 30, 20, 6)
+    idx, vals = sparse_random(dims, 30000, 41)
+    h = g.Handle(g.DataTensor.coo(dims, idx, vals))
+    XO = oracle_sparse(dims, idx, vals)
+    S = g.Sampling(g.SAMPLER_UNIFORM, 0, 20001, seed=8, stream=3)
+    L = g.gcp_sample(h, S)
+    torch.cuda.synchronize()
+    SO = oracle.sample(XO, oracle.UNIFORM, 0, 20001, 8, 3)
+    assert_lists_equal(L, SO)
+    assert (SO.x != 0).sum() > 100  # the draws do hit nonzeros
+    A = rng_factors(dims, 8, 42, scale=0.5)
+    G = run_grad(h, g.Factors(A), loss, S=S)
+    assert_grad_close(grad_to_numpy(G, 8), oracle.grad(dims, f64(A), loss, SO), oracle.grad_abs(dims, f64(A), loss, SO))
+
+
+def test_entry_weights_dense():
+    g = gcp()
+    dims = (20, 30, 40)
+    rs = np.random.default_rng(43)
+    X = rs.standard_normal(dims).astype(np.float32)
+    v = (rs.random(dims) * (rs.random(dims) < 0.7)).astype(np.float32)
+    h = g.Handle(g.DataTensor.dense(X, weights=v))
+    XO = oracle.Tensor(dims, dense=X.astype(np.float64), weights=v.astype(np.float64))
+    S = g.Sampling(g.SAMPLER_UNIFORM, 0, 10001, seed=9, stream=4)
+    L = g.gcp_sample(h, S)
+    torch.cuda.synchronize()
+    SO = oracle.sample(XO, oracle.UNIFORM, 0, 10001, 9, 4)
+    np.testing.assert_array_equal(np.stack([i.cpu().numpy() for i in L.idx], axis=1), SO.idx)
+    np.testing.assert_allclose(L.w.cpu().numpy(), SO.w, rtol=2e-7)  # (omega/s) v in FP32 vs FP64
+    A = rng_factors(dims, 5, 44, scale=0.5)
+    G = run_grad(h, g.Factors(A), g.LOSS_BERNOULLI_LOGIT, S=S)
+    assert_grad_close(grad_to_numpy(G, 5), oracle.grad(dims, f64(A), oracle.BERNOULLI_LOGIT, SO))

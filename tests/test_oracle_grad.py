@@ -312,3 +312,40 @@ def test_positive_losses_full_gradient_and_derivative(loss):
                 Am[k][i, j] -= h
                 fd = (oracle.loss_estimate(dims, Ap, loss, S) - oracle.loss_estimate(dims, Am, loss, S)) / (2 * h)
                 assert Gs[k][i, j] == pytest.approx(fd, rel=2e-5, abs=2e-6)
+
+
+def test_weighted_uniform_sampling_unbiased():
+    """With entry weights v the uniform sampler's gradient is unbiased for the
+    weighted full gradient of Eq. (4.5)."""
+    dims = (3, 4, 5)
+    X, A = problem(dims, 2, oracle.BERNOULLI_LOGIT, 70)
+    v = np.random.default_rng(71).random(dims) * (np.random.default_rng(72).random(dims) < 0.7)
+    G_full, _ = oracle.full_grad(dims, A, oracle.BERNOULLI_LOGIT, X, weights=v)
+    T = oracle.Tensor(dims, dense=X, weights=v)
+    N = 3000
+    gs = np.array([np.concatenate([g.reshape(-1) for g in
+                                   oracle.grad(dims, A, oracle.BERNOULLI_LOGIT, oracle.sample(T, oracle.UNIFORM, 0, 30, 5, t))])
+                   for t in range(N)])
+    full = np.concatenate([g.reshape(-1) for g in G_full])
+    se = gs.std(axis=0, ddof=1) / np.sqrt(N)
+    assert np.all(np.abs(gs.mean(axis=0) - full) <= 5 * se + 1e-12)
+
+
+def test_uniform_over_sparse_enumeration_identity():
+    """Every index once (weight 1) through the sparse value lookup gives the
+    full gradient of the dense equivalent."""
+    dims = (3, 4, 5)
+    X, A = problem(dims, 2, oracle.POISSON_LOG, 73, density=0.3)
+    coo, vals = coo_of(X)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    keys, svals = T.sorted_pairs()
+    lib = oracle._load()
+    idx = all_indices(dims)
+    x = np.array([lib.orc_sparse_value(T.nnz, oracle._p(keys), oracle._p(svals), oracle.linear_key(dims, ix))
+                  for ix in idx])
+    np.testing.assert_array_equal(x, X.reshape(-1))
+    S = Samples(idx, x, np.ones(len(idx)), np.full(len(idx), oracle.CLS_UNIFORM))
+    Gs = oracle.grad(dims, A, oracle.POISSON_LOG, S)
+    G, _ = oracle.full_grad(dims, A, oracle.POISSON_LOG, X)
+    for k in range(3):
+        np.testing.assert_allclose(Gs[k], G[k], rtol=1e-12, atol=1e-12)

@@ -150,3 +150,25 @@ def test_sorted_keys_membership():
     lib = oracle._load()
     for key in range(flat.size):
         assert bool(lib.orc_is_nonzero(T.nnz, oracle._p(keys), key)) == (flat[key] != 0)
+
+
+def test_uniform_over_sparse_tensor_matches_twin():
+    """Alg. 1 on a sparse tensor: the value of a drawn index is its nonzero's
+    value, or 0 (a Python dict lookup in the twin)."""
+    dims = (6, 5, 4, 3)
+    X, coo, vals = sparse_problem(dims, 0.3, 7)
+    T = oracle.Tensor(dims, coo=coo, vals=vals)
+    S = oracle.sample(T, oracle.UNIFORM, 0, 500, 3, 2)
+    compare(S, twin_sample(dims, X, None, None, oracle.UNIFORM, 0, 500, 3, 2))
+
+
+def test_uniform_with_entry_weights_matches_twin():
+    """Weighted GCP (Eq. (4.5)) under Alg. 1: the draw's weight is (omega/s) v_i."""
+    dims = (5, 6, 7)
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal(dims)
+    v = rng.random(dims) * (rng.random(dims) < 0.8)
+    S = oracle.sample(oracle.Tensor(dims, dense=X, weights=v), oracle.UNIFORM, 0, 300, 4, 1)
+    twin = twin_sample(dims, X, None, None, oracle.UNIFORM, 0, 300, 4, 1)
+    twin = [(ix, x, w * v[tuple(ix)], c) for ix, x, w, c in twin]
+    compare(S, twin)
