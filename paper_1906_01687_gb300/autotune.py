@@ -17,7 +17,7 @@ import torch
 
 from . import gcp
 
-COMPILED = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (16, 1), (32, 1), (32, 2)]
+COMPILED = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (16, 1), (32, 1), (32, 2)]
 
 
 def candidate_shapes(rank: int) -> list:

@@ -81,17 +81,8 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
         const int col = static_cast<int>((loc * 4) % mt.ld);
         float4* g4 = reinterpret_cast<float4*>(mt.G[k]) + loc;
         float4 g = *g4;
-        if (a.reps[k] > 1) {  // fold the replica slabs of this mode (fixed order), leaving them zero
-            float4* r = reinterpret_cast<float4*>(a.R[k]) + loc;
-            for (uint32_t q = 0; q < a.reps[k]; ++q) {
-                const float4 v = r[q * a.rep_stride4[k]];
-                g.x += v.x;
-                g.y += v.y;
-                g.z += v.z;
-                g.w += v.w;
-                r[q * a.rep_stride4[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
+        if (a.reps[k] > 1)  // fold the replica slabs of this mode, leaving them zero
+            g = add4(g, fold_replicas(reinterpret_cast<float4*>(a.R[k]) + loc, a.reps[k], a.rep_stride4[k]));
         if (!s_done && col < mt.rank) {
             float4* a4p = reinterpret_cast<float4*>(mt.A[k]) + loc;
             float4* b4p = reinterpret_cast<float4*>(mt.B[k]) + loc;

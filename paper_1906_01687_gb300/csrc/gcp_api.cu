@@ -351,6 +351,14 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
         sh->L = 32;
         sh->NC = 2;
     }
+    if (!grad_has_config(sh->D, sh->L, sh->NC)) {  // automatic choices must be compiled pairs
+        sh->L = 32;
+        sh->NC = chunks <= 32 ? 1 : 2;
+        if (chunks <= 4) {
+            sh->L = 1;
+            sh->NC = chunks;
+        }
+    }
     sh->block = t.block > 0 ? t.block : 256;
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
     sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;

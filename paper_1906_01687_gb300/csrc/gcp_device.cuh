@@ -174,6 +174,34 @@ __device__ __forceinline__ float4 mul4(float4 a, float4 b)
 }
 __device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
 __device__ __forceinline__ float sum4(float4 a) { return (a.x + a.y) + (a.z + a.w); }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+// Sum of reps replica chunks r[0], r[stride], ... (each then zeroed), with
+// four loads in flight; the summation order is fixed by reps and stride.
+__device__ __forceinline__ float4 fold_replicas(float4* r, uint32_t reps, uint64_t stride)
+{
+    float4 acc[4] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                     make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t q = 0;
+    for (; q + 4 <= reps; q += 4) {
+        const float4 v0 = r[(q + 0) * stride], v1 = r[(q + 1) * stride];
+        const float4 v2 = r[(q + 2) * stride], v3 = r[(q + 3) * stride];
+        r[(q + 0) * stride] = zero;
+        r[(q + 1) * stride] = zero;
+        r[(q + 2) * stride] = zero;
+        r[(q + 3) * stride] = zero;
+        acc[0] = add4(acc[0], v0);
+        acc[1] = add4(acc[1], v1);
+        acc[2] = add4(acc[2], v2);
+        acc[3] = add4(acc[3], v3);
+    }
+    for (; q < reps; ++q) {
+        acc[0] = add4(acc[0], r[q * stride]);
+        r[q * stride] = zero;
+    }
+    return add4(add4(acc[0], acc[1]), add4(acc[2], acc[3]));
+}
 
 // Programmatic dependent launch.  A kernel launched with the programmatic
 // stream-serialization attribute may begin while its predecessor in the

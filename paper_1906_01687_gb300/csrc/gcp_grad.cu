@@ -58,16 +58,7 @@ __global__ void __launch_bounds__(256) fold_kernel(const FoldArgs a)
         const int64_t loc = i4 - a.off4[m];
         float4* g = reinterpret_cast<float4*>(a.G[m]) + loc;
         float4* r = reinterpret_cast<float4*>(a.R[m]) + loc;
-        float4 acc = *g;
-        for (uint32_t k = 0; k < a.reps[m]; ++k) {
-            const float4 v = r[k * a.rep_stride4[m]];
-            acc.x += v.x;
-            acc.y += v.y;
-            acc.z += v.z;
-            acc.w += v.w;
-            r[k * a.rep_stride4[m]] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        *g = acc;
+        *g = add4(*g, fold_replicas(r, a.reps[m], a.rep_stride4[m]));
     }
 }
 

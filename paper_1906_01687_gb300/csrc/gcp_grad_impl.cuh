@@ -75,25 +75,41 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
             // m_i = sum_j prod_k A_k(i_k, j) over this lane's chunks of the d rows.
             // With one chunk per lane the rows stay in registers for the scatter;
             // with several they are re-read there (L1 hits) to keep registers low.
+            // For 3 and 4 modes with one chunk, the pairwise products of the rows
+            // serve both m and the leave-one-out products of the scatter.
             constexpr bool kKeep = NC == 1;
-            float4 r[D][kKeep ? 1 : 1];
+            constexpr bool kPairs = kKeep && (D == 3 || D == 4);
+            float4 r[D];
+            float4 p01 = make_float4(0.f, 0.f, 0.f, 0.f), p23 = p01;
             float part = 0.0f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int col = (gl * NC + c) * 4;
-                float4 prod = make_float4(1.f, 1.f, 1.f, 1.f);
+                float4 v[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    float4 v;
                     if (k >= d) {
-                        v = make_float4(1.f, 1.f, 1.f, 1.f);
+                        v[k] = make_float4(1.f, 1.f, 1.f, 1.f);
                     } else if (valid && col < rank) {
-                        v = load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col);
+                        v[k] = load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col);
                     } else {
-                        v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    if (kKeep) r[k][0] = v;
-                    prod = mul4(prod, v);
+                    if (kKeep) r[k] = v[k];
+                }
+                float4 prod;
+                if constexpr (kPairs) {
+                    p01 = mul4(v[0], v[1]);
+                    if constexpr (D == 4) {
+                        p23 = mul4(v[2], v[3]);
+                        prod = mul4(p01, p23);
+                    } else {
+                        prod = mul4(p01, v[2]);
+                    }
+                } else {
+                    prod = v[0];
+#pragma unroll
+                    for (int k = 1; k < D; ++k) prod = mul4(prod, v[k]);
                 }
                 part += sum4(prod);
             }
@@ -106,33 +122,51 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
             for (int c = 0; c < NC; ++c) {
                 const int col = (gl * NC + c) * 4;
                 if (col >= rank) continue;
-                float4 rc[D];
+                // upd[k] = y prod_{l != k} A_l(i_l, cols)
+                float4 upd[D];
+                if constexpr (kPairs) {
+                    if constexpr (D == 4) {
+                        const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
+                        upd[0] = mul4(yp23, r[1]);
+                        upd[1] = mul4(yp23, r[0]);
+                        upd[2] = mul4(yp01, r[3]);
+                        upd[3] = mul4(yp01, r[2]);
+                    } else {
+                        const float4 yr2 = scale4(y, r[2]);
+                        upd[0] = mul4(yr2, r[1]);
+                        upd[1] = mul4(yr2, r[0]);
+                        upd[2] = scale4(y, p01);
+                    }
+                } else {
+                    float4 rc[D];
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if (kKeep) rc[k] = r[k][0];
-                    else rc[k] = k < d ? load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col)
-                                       : make_float4(1.f, 1.f, 1.f, 1.f);
+                    for (int k = 0; k < D; ++k) {
+                        if (kKeep) rc[k] = r[k];
+                        else rc[k] = k < d ? load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col)
+                                           : make_float4(1.f, 1.f, 1.f, 1.f);
+                    }
+                    // prefix and suffix products
+                    float4 pre[D], suf[D];
+                    pre[0] = make_float4(y, y, y, y);
+#pragma unroll
+                    for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
+                    suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+                    for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) upd[k] = mul4(pre[k], suf[k]);
                 }
-                // leave-one-out products prod_{l != k} A_l(i_l, cols), via prefix and suffix products
-                float4 pre[D], suf[D];
-                pre[0] = make_float4(y, y, y, y);
-#pragma unroll
-                for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
-                suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
-#pragma unroll
-                for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     if (k >= d) continue;
-                    const float4 upd = mul4(pre[k], suf[k]);
                     if ((a.smem_mask >> k) & 1u) {
                         float* s = sG + a.smem_off[k] + static_cast<size_t>(ix[k]) * ld + col;
-                        atomicAdd(s + 0, upd.x);
-                        atomicAdd(s + 1, upd.y);
-                        atomicAdd(s + 2, upd.z);
-                        atomicAdd(s + 3, upd.w);
+                        atomicAdd(s + 0, upd[k].x);
+                        atomicAdd(s + 1, upd[k].y);
+                        atomicAdd(s + 2, upd[k].z);
+                        atomicAdd(s + 3, upd[k].w);
                     } else {
-                        atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd);
+                        atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd[k]);
                     }
                 }
             }
@@ -155,7 +189,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
 }
 
 #define GCP_GRAD_CONFIGS(X) \
-    X(1, 1) X(1, 2) X(1, 3) X(1, 4) X(2, 2) X(4, 1) X(4, 2) X(8, 1) X(8, 2) X(16, 1) X(32, 1) X(32, 2)
+    X(1, 1) X(1, 2) X(1, 3) X(1, 4) X(2, 1) X(2, 2) X(4, 1) X(4, 2) X(8, 1) X(8, 2) X(16, 1) X(32, 1) X(32, 2)
 
 template <int D, bool BF16>
 const void* grad_kernel_ptr(int L, int NC)
