@@ -274,6 +274,17 @@ gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
                     const int64_t *stream_dev, float *const G[GCP_MAX_MODES],
                     gcp_stream_t stream);
 
+/* The full (non-stochastic) gradient G_k = Y_(k) Z_k of a dense X
+   (Eq. (4.2); with entry weights, Eq. (4.5)): every index of Omega taken once
+   with weight 1 (or v_i) through the gradient kernel, accumulated into G as
+   gcp_grad does.  O(r prod(dims)) work: for moderate tensors. */
+gcp_status gcp_full_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss, float *const G[GCP_MAX_MODES],
+                         gcp_stream_t stream);
+
+/* The exact objective F(X, M) of Eq. (1.2) (weighted: Eq. (4.5)) of a dense X
+   over every index, FP32 terms summed in FP64, into *out_dev. */
+gcp_status gcp_full_loss(gcp_handle *h, const gcp_factors *F, gcp_loss loss, double *out_dev, gcp_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Loss estimate: Eqs. (5.1)-(5.2)                                          */
 /* ------------------------------------------------------------------------ */

@@ -799,6 +799,74 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     return GCP_OK;
 }
 
+// The gradient kernel over an arbitrary prepared draw source (no sampling spec).
+static gcp_status grad_from_args(gcp_handle* h, const gcp_factors* F, gcp_loss loss, GradArgs a,
+                                 float* const G[GCP_MAX_MODES], cudaStream_t s)
+{
+    Shape sh;
+    gcp_status st = choose_shape(h, F, a.dr.n_total, &sh);
+    if (st != GCP_OK) return st;
+    a.ld = F->ld;
+    a.rank = F->rank;
+    a.loss = loss;
+    a.smem_floats = 0;
+    a.smem_mask = 0;
+    a.group_draws = sh.group;
+    for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
+    for (int k = 0; k < h->X.d; ++k) {
+        a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);
+        a.G[k] = G[k];
+        a.rep_stride[k] = 0;
+    }
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.grid, sh.block, 0, s));
+    return GCP_OK;
+}
+
+gcp_status gcp_full_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, float* const G[GCP_MAX_MODES],
+                         gcp_stream_t stream)
+{
+    if (!h || h->X.sparse) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_factors(h, F);
+    if (st != GCP_OK) return st;
+    if (!modes_ok(G, h->X.d)) return GCP_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    GradArgs a{};
+    gcp_sampling none{};
+    a.dr = make_draw_args(h, &none, nullptr, nullptr);
+    a.dr.src = kSrcEnumerate;
+    a.dr.n_total = static_cast<int64_t>(h->omega);
+    return grad_from_args(h, F, loss, a, G, s);
+}
+
+gcp_status gcp_full_loss(gcp_handle* h, const gcp_factors* F, gcp_loss loss, double* out_dev, gcp_stream_t stream)
+{
+    if (!h || h->X.sparse || !out_dev || !aligned(out_dev, 8)) return GCP_ERR_INVALID_ARG;
+    if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
+    gcp_status st = check_factors(h, F);
+    if (st != GCP_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    LossArgs a{};
+    gcp_sampling none{};
+    a.dr = make_draw_args(h, &none, nullptr, nullptr);
+    a.dr.src = kSrcEnumerate;
+    a.dr.n_total = static_cast<int64_t>(h->omega);
+    a.ld = F->ld;
+    a.rank = F->rank;
+    a.loss = loss;
+    for (int k = 0; k < h->X.d; ++k)
+        a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);
+    a.partials = h->partials;
+    a.ticket = h->ticket;
+    a.out = out_dev;
+    const int64_t want = std::max<int64_t>(1, (a.dr.n_total + 255) / 256);
+    const int grid = static_cast<int>(std::min<int64_t>(want, std::min<int64_t>(h->partials_cap, int64_t(h->num_sms) * 4)));
+    GCP_CUDA_TRY(launch_loss(a, F->bf16 != 0, grid, 256, s));
+    return GCP_OK;
+}
+
 gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
                     const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
                     gcp_stream_t stream)

@@ -77,6 +77,21 @@ __device__ __forceinline__ void make_draw(const DrawArgs& a, int64_t j, uint64_t
         return;
     }
 
+    if (a.src == kSrcEnumerate) {
+        // draw j is the index with row-major linear index j (Eqs. (1.2), (4.2) over all of Omega)
+        uint64_t rem = static_cast<uint64_t>(j);
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+            if (k < a.d) {
+                o.ix[k] = static_cast<uint32_t>(rem % a.dims[k]);
+                rem /= a.dims[k];
+            }
+        }
+        o.x = __ldg(a.X + j);
+        o.w = a.W ? __ldg(a.W + j) : 1.0f;
+        o.cls = GCP_CLS_UNIFORM;
+        return;
+    }
     if (a.src == kSrcUniformDense || a.src == kSrcUniformSparse) {
         // Alg. 1: i_k = randi(n_k); x = X(i); weight omega / s (times v_i with entry weights)
         draw_index<D>(a.dims, a.seed, a.problem, stream, kTagUniform, static_cast<uint64_t>(j), a.d, o.ix);

@@ -15,7 +15,8 @@ enum Source : int32_t {
     kSrcUniformDense = 0,  // Alg. 1 over a dense tensor, generated in-kernel
     kSrcSparse = 1,        // Algs. 2/3: nonzeros generated in-kernel, zeros generated (semi) or listed (stratified)
     kSrcList = 2,          // a materialised list
-    kSrcUniformSparse = 3  // Alg. 1 over a sparse tensor: values looked up in the nonzero hash
+    kSrcUniformSparse = 3, // Alg. 1 over a sparse tensor: values looked up in the nonzero hash
+    kSrcEnumerate = 4      // every index of a dense tensor once, weight 1 (or v_i): the full gradient
 };
 
 struct DrawArgs {

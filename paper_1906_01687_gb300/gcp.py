@@ -107,6 +107,8 @@ _SIGS = {
     "gcp_sample": ([_vp, _P(gcp_sampling), _P(gcp_samples), _vp], ctypes.c_int),
     "gcp_reserve": ([_vp, _P(gcp_sampling), _vp], ctypes.c_int),
     "gcp_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _P(gcp_samples), _vp, _P8, _vp], ctypes.c_int),
+    "gcp_full_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P8, _vp], ctypes.c_int),
+    "gcp_full_loss": ([_vp, _P(gcp_factors), ctypes.c_int, _vp, _vp], ctypes.c_int),
     "gcp_loss_est": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_samples), _vp, _vp], ctypes.c_int),
     "gcp_loss_est_noalloc": ([_i32, _P(gcp_factors), ctypes.c_int, _P(gcp_samples), _vp, _vp], ctypes.c_int),
     "gcp_state_init": ([_vp, ctypes.c_float, _vp], ctypes.c_int),
@@ -413,6 +415,17 @@ def gcp_grad(h: Handle, F: Factors, loss: int, G: Sequence[torch.Tensor], S: Opt
     lp = ctypes.byref(samples._c()) if samples is not None else None
     _check(_lib.gcp_grad(h.ptr, ctypes.byref(F._c(gather_bf16)), int(loss), sp, lp, _ptr(stream_dev), _p8(G),
                          _stream(stream)), "gcp_grad")
+
+
+def gcp_full_grad(h: Handle, F: Factors, loss: int, G, stream=None):
+    """Full gradient G_k = Y_(k) Z_k of a dense tensor over every index (accumulates into G)."""
+    _check(_lib.gcp_full_grad(h.ptr, ctypes.byref(F._c()), int(loss), _p8(G), _stream(stream)), "gcp_full_grad")
+
+
+def gcp_full_loss(h: Handle, F: Factors, loss: int, out: torch.Tensor, stream=None):
+    """Exact objective F(X, M) of a dense tensor into out (device float64)."""
+    assert out.dtype == torch.float64 and out.is_cuda
+    _check(_lib.gcp_full_loss(h.ptr, ctypes.byref(F._c()), int(loss), _ptr(out), _stream(stream)), "gcp_full_loss")
 
 
 def gcp_loss_est(h: Handle, F: Factors, loss: int, samples: SampleList, out: torch.Tensor, stream=None,

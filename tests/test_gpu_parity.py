@@ -385,3 +385,37 @@ def test_entry_weights_dense():
     A = rng_factors(dims, 5, 44, scale=0.5)
     G = run_grad(h, g.Factors(A), g.LOSS_BERNOULLI_LOGIT, S=S)
     assert_grad_close(grad_to_numpy(G, 5), oracle.grad(dims, f64(A), oracle.BERNOULLI_LOGIT, SO))
+
+
+# ---------------------------------------------------------------------------
+# the full (non-stochastic) gradient and objective (Eqs. (1.2), (4.2), (4.5))
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("loss", [0, 1, 2, 5], ids={0: "gaussian", 1: "logit", 2: "poisson", 5: "gamma"}.get)
+@pytest.mark.parametrize("weighted", [False, True])
+def test_full_gradient_and_objective(loss, weighted):
+    g = gcp()
+    dims = (17, 23, 31)
+    rs = np.random.default_rng(60 + loss)
+    if loss == 5:
+        A = [(rs.uniform(0.2, 1.0, (n, 6)) * 0.5).astype(np.float32) for n in dims]
+        X = rs.exponential(1.0, dims).astype(np.float32)
+    else:
+        A = rng_factors(dims, 6, 61, scale=0.5)
+        X = rs.standard_normal(dims).astype(np.float32)
+        if loss == 1:
+            X = (X > 0).astype(np.float32)
+        elif loss == 2:
+            X = np.floor(np.abs(X) * 2).astype(np.float32)
+    v = (rs.random(dims) * (rs.random(dims) < 0.8)).astype(np.float32) if weighted else None
+    h = g.Handle(g.DataTensor.dense(X, weights=v))
+    F = g.Factors(A)
+    G = F.like()
+    g.gcp_full_grad(h, F, loss, G)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.gcp_full_loss(h, F, loss, out)
+    torch.cuda.synchronize()
+    Gref, Fref = oracle.full_grad(dims, f64(A), loss, X.astype(np.float64),
+                                  weights=None if v is None else v.astype(np.float64))
+    assert_grad_close(grad_to_numpy(G, 6), Gref)
+    assert out.item() == pytest.approx(Fref, rel=2e-6)
