@@ -129,3 +129,32 @@ class GcpAdam:
     def factors(self):
         self.stream.synchronize()
         return self.F.numpy()
+
+    # -- checkpoint / resume ----------------------------------------------------
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs: factors (FP32 master), Adam moments,
+        the epoch snapshot and the 64-byte optimizer state.  The draws are a
+        function of (seed, problem, iteration), so a resumed run draws exactly
+        what the uninterrupted run would have."""
+        self.stream.synchronize()
+        cpu = lambda xs: [x.detach().cpu().clone() for x in xs]
+        return dict(A=cpu(self.F.A), B=cpu(self.B), C=cpu(self.C), SA=cpu(self.SA), SB=cpu(self.SB),
+                    SC=cpu(self.SC), state=self.state.detach().cpu().clone(),
+                    spec=dict(kind=self.spec.kind, p=self.spec.p, q=self.spec.q, seed=self.spec.seed,
+                              problem=self.spec.problem))
+
+    def load_state_dict(self, sd: dict):
+        spec = sd["spec"]
+        if (spec["kind"], spec["p"], spec["q"], spec["seed"], spec["problem"]) != (
+                self.spec.kind, self.spec.p, self.spec.q, self.spec.seed, self.spec.problem):
+            raise ValueError("checkpoint belongs to a different sampling spec")
+        with torch.cuda.stream(self.stream):
+            for name in ("B", "C", "SA", "SB", "SC"):
+                for dst, src in zip(getattr(self, name), sd[name]):
+                    dst.copy_(src, non_blocking=True)
+            for dst, src in zip(self.F.A, sd["A"]):
+                dst.copy_(src, non_blocking=True)
+            self.state.copy_(sd["state"], non_blocking=True)
+            if self.F.A_bf16 is not None:
+                gcp.gcp_factors_to_bf16(self.F, stream=self.stream)
+        self.stream.synchronize()

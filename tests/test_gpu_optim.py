@@ -298,3 +298,31 @@ def test_gamma_problem_fits_with_projection():
     st = run.fit(max_epochs=10)
     assert run.history[-1] < run.history[0] and math.isfinite(run.history[-1])
     assert all((a >= 0).all() for a in run.factors())
+
+
+def test_checkpoint_resume_reproduces_run(tmp_path):
+    """Four epochs straight, or two epochs, a checkpoint through torch.save,
+    and two more epochs in a fresh driver: the same draws and, up to the
+    summation order of the atomics, the same factors and state."""
+    from paper_1906_01687_gb300.adam import GcpAdam
+    g = gcp()
+    dims = (20, 30, 40)
+    rs = np.random.default_rng(9)
+    X = rs.standard_normal(dims).astype(np.float32)
+    A0 = rng_factors(dims, 4, 10, scale=0.5)
+    mk = lambda: GcpAdam(g.DataTensor.dense(X), A0, g.LOSS_GAUSSIAN, g.SAMPLER_UNIFORM, 0, 2000, 0, 1000, seed=5,
+                         est_seed=6, alpha=0.01, tau=25)
+    straight = mk()
+    straight.fit(max_epochs=4)
+    first = mk()
+    first.fit(max_epochs=2)
+    path = tmp_path / "ckpt.pt"
+    torch.save(first.state_dict(), path)
+    resumed = mk()
+    resumed.load_state_dict(torch.load(path))
+    resumed.fit(max_epochs=2)
+    a, b = straight.factors(), resumed.factors()
+    num = math.sqrt(sum(np.linalg.norm(x - y) ** 2 for x, y in zip(a, b)))
+    assert num <= 1e-4 * math.sqrt(sum(np.linalg.norm(y) ** 2 for y in a))
+    s1, s2 = straight.status(), resumed.status()
+    assert (s1["t"], s1["iter"], s1["bad"]) == (s2["t"], s2["iter"], s2["bad"])
