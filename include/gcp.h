@@ -451,6 +451,9 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    group_draws = 1: each group of lanes generates and takes its own draw
    (32 / lanes draws per warp step) instead of a warp generating 32 draws and
    its groups walking them in turn (0): more warps for small draw counts.
+   prefetch = 1 (one chunk per lane, 2 or 4 lanes, at most 4 modes): a group
+   issues the row loads of all its draws before consuming any (one round
+   trip to L2 per group walk instead of one per draw; more registers).
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -462,7 +465,7 @@ typedef struct gcp_tuning {
     int32_t max_replicas;
     int32_t replica_target;
     int32_t group_draws;
-    int32_t reserved;
+    int32_t prefetch;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */
@@ -475,7 +478,7 @@ typedef struct gcp_launch_info {
     uint32_t smem_mode_mask;
     int32_t replicas[GCP_MAX_MODES];
     int32_t group_draws;
-    int32_t reserved;
+    int32_t prefetch;
 } gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch

@@ -52,8 +52,7 @@ class GcpAdam:
         self.history = []
         self.tuned = None
         if autotune:
-            from .autotune import autotune as _autotune
-            self.tuned = _autotune(self.h, self.F, loss, self.spec, stream=self.stream)
+            self.tuned = self.autotune()
 
     # -- one epoch of launches --------------------------------------------
     def iteration(self):
@@ -84,6 +83,20 @@ class GcpAdam:
         gcp.gcp_loss_est(self.h, F, self.loss, self.est, st[0:1], stream=self.stream)
         gcp.gcp_epoch_end(F, B, C, SA, SB, SC, st, self.tau, self.nu, self.kappa, stream=self.stream)
         self.stream.synchronize()
+
+    def autotune(self, launches: int = 20):
+        """Chooses the gradient's launch shape by timing whole iterations
+        (gradient + Adam with the replica fold) on throwaway copies."""
+        from .autotune import autotune as _autotune
+        with torch.cuda.stream(self.stream):
+            F = gcp.Factors([a[:, : self.F.rank] for a in self.F.A], bf16=self.F.bf16, device=self.F.A[0].device)
+            G, B, C = F.like(), F.like(), F.like()
+            st = gcp.new_state(self.F.A[0].device)
+            gcp.gcp_state_init(st, 0.0, stream=self.stream)
+
+        def call(spec, stream):
+            gcp.gcp_iteration(self.h, F, self.loss, spec, G, B, C, st, stream=stream, **self.adam)
+        return _autotune(self.h, F, self.loss, self.spec, launches=launches, stream=self.stream, call=call)
 
     def capture(self):
         """Captures one epoch's launches in a CUDA graph (replayed by run_epoch)."""

@@ -35,36 +35,48 @@ def candidate_shapes(rank: int) -> list:
 def candidates(rank: int) -> list:
     out = []
     for L, NC in candidate_shapes(rank):
-        for group in ((0, 1) if L > 1 else (0,)):
+        layouts = [dict(group_draws=0)]
+        if L > 1:
+            layouts.append(dict(group_draws=1))
+        if NC == 1 and L in (2, 4):
+            layouts.append(dict(prefetch=1))
+        for layout in layouts:
             for block in (128, 256):
                 for reps, target in ((0, 0), (-1, 0), (8, 128), (32, 16)):
                     out.append(dict(lanes=L, chunks=NC, block=block, max_replicas=reps, replica_target=target,
-                                    group_draws=group))
+                                    **layout))
         out.append(dict(lanes=L, chunks=NC, block=256, max_replicas=0, smem_bytes=48 * 1024, smem_min_hits=10))
     return out
 
 
-def time_grad(h, F, loss, spec, launches=20, stream=None) -> float:
-    """Median device time (s) of one gcp_grad call for the current tuning."""
+def time_grad(h, F, loss, spec, launches=20, stream=None, call=None) -> float:
+    """Median device time (s) of one gcp_grad call (or of call(spec, stream))
+    for the current tuning."""
     stream = stream or torch.cuda.current_stream()
-    G = F.like()
+    if call is None:
+        G = F.like()
+
+        def call(s, st):
+            gcp.gcp_grad(h, F, loss, G, S=s, stream=st)
     with torch.cuda.stream(stream):
-        gcp.gcp_grad(h, F, loss, G, S=spec, stream=stream)  # allocate any workspace outside the timing
+        call(spec, stream)  # allocate any workspace outside the timing
         stream.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(launches)]
         torch.cuda._sleep(50_000_000)
         for i, (a, b) in enumerate(evs):
             s = gcp.Sampling(spec.kind, spec.p, spec.q, spec.seed, (1 << 62) + i, spec.problem, spec.oversample)
             a.record(stream)
-            gcp.gcp_grad(h, F, loss, G, S=s, stream=stream)
+            call(s, stream)
             b.record(stream)
     stream.synchronize()
     return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
 
 
 def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launches=20, stream=None,
-             log=None) -> dict:
-    """Times every candidate, sets the fastest on the handle, returns it with its time."""
+             log=None, call=None) -> dict:
+    """Times every candidate (gcp_grad, or call(spec, stream) when given, e.g.
+    a whole GCP-Adam iteration), sets the fastest on the handle, returns it
+    with its time."""
     best, best_t = None, float("inf")
     results = []
     for cfg in configs if configs is not None else candidates(F.rank):
@@ -72,7 +84,7 @@ def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launche
             gcp.gcp_set_tuning(h, **cfg)
         except gcp.GcpError:
             continue
-        t = time_grad(h, F, loss, spec, launches, stream)
+        t = time_grad(h, F, loss, spec, launches, stream, call)
         results.append((t, cfg))
         if log:
             log(dict(seconds=t, **cfg))

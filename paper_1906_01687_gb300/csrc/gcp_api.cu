@@ -297,6 +297,7 @@ struct Shape {
     uint32_t reps[GCP_MAX_MODES] = {};
     int64_t rep_floats = 0;  // replica workspace the shape needs
     int group = 0;           // group_draws layout
+    int pf = 0;              // prefetch layout
 };
 
 int next_pow2(int v)
@@ -307,7 +308,7 @@ int next_pow2(int v)
 }
 
 struct OccKey {
-    int D, L, NC, bf16, block;
+    int D, L, NC, bf16, pf, block;
     size_t smem;
     int device;
 };
@@ -319,18 +320,18 @@ std::mutex g_occ_mutex;
 OccEntry g_occ[256];
 int g_occ_n = 0;
 
-int occupancy(int D, int L, int NC, bool bf16, int block, size_t smem, int device)
+int occupancy(int D, int L, int NC, bool bf16, bool pf, int block, size_t smem, int device)
 {
     std::lock_guard<std::mutex> lock(g_occ_mutex);
     for (int i = 0; i < g_occ_n; ++i) {
         const OccKey& k = g_occ[i].key;
-        if (k.D == D && k.L == L && k.NC == NC && k.bf16 == int(bf16) && k.block == block && k.smem == smem &&
-            k.device == device)
+        if (k.D == D && k.L == L && k.NC == NC && k.bf16 == int(bf16) && k.pf == int(pf) && k.block == block &&
+            k.smem == smem && k.device == device)
             return g_occ[i].bps;
     }
     int bps = 0;
-    if (grad_occupancy(D, L, NC, bf16, block, smem, &bps) != cudaSuccess || bps < 1) bps = 1;
-    if (g_occ_n < 256) g_occ[g_occ_n++] = OccEntry{OccKey{D, L, NC, int(bf16), block, smem, device}, bps};
+    if (grad_occupancy(D, L, NC, bf16, pf, block, smem, &bps) != cudaSuccess || bps < 1) bps = 1;
+    if (g_occ_n < 256) g_occ[g_occ_n++] = OccEntry{OccKey{D, L, NC, int(bf16), int(pf), block, smem, device}, bps};
     return bps;
 }
 
@@ -343,7 +344,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     if (t.lanes > 0) {
         sh->L = t.lanes;
         sh->NC = t.chunks > 0 ? t.chunks : 1;
-        if (!grad_has_config(sh->D, sh->L, sh->NC) || sh->L * sh->NC < chunks) return GCP_ERR_INVALID_ARG;
+        if (!grad_has_config(sh->D, sh->L, sh->NC, false) || sh->L * sh->NC < chunks) return GCP_ERR_INVALID_ARG;
     } else if (chunks <= 32) {  // one float4 chunk per lane: measured fastest across ranks
         sh->L = next_pow2(chunks);
         sh->NC = 1;
@@ -351,7 +352,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
         sh->L = 32;
         sh->NC = 2;
     }
-    if (!grad_has_config(sh->D, sh->L, sh->NC)) {  // automatic choices must be compiled pairs
+    if (!grad_has_config(sh->D, sh->L, sh->NC, false)) {  // automatic choices must be compiled pairs
         sh->L = 32;
         sh->NC = chunks <= 32 ? 1 : 2;
         if (chunks <= 4) {
@@ -362,6 +363,8 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     sh->block = t.block > 0 ? t.block : 256;
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
     sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;
+    sh->pf = (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, true) &&
+              h->X.d == sh->D) ? 1 : 0;
     const int64_t per_warp = sh->group ? 32 / sh->L : 32;
     const int64_t warps = (n_total + per_warp - 1) / per_warp;
     const int64_t blocks_needed = std::max<int64_t>(1, (warps + sh->block / 32 - 1) / (sh->block / 32));
@@ -383,7 +386,8 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
         }
     }
     sh->smem = static_cast<size_t>(used);
-    const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->block, sh->smem, h->device);
+    if (sh->pf && sh->smem > 0) sh->pf = 0;  // the prefetch layout accumulates through L2 only
+    const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->pf != 0, sh->block, sh->smem, h->device);
     const int64_t resident = static_cast<int64_t>(h->num_sms) * bps;
     sh->grid = static_cast<int>(t.grid_blocks > 0 ? t.grid_blocks : std::min<int64_t>(blocks_needed, resident));
 
@@ -630,7 +634,8 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
         h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0};
         return GCP_OK;
     }
-    if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1)) return GCP_ERR_INVALID_ARG;
+    if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, false)) return GCP_ERR_INVALID_ARG;
+    if (t->prefetch < 0 || t->prefetch > 1) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
         t->group_draws < 0 || t->group_draws > 1)
@@ -655,6 +660,7 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     out->smem_bytes = static_cast<int32_t>(sh.smem);
     out->smem_mode_mask = sh.mask;
     out->group_draws = sh.group;
+    out->prefetch = sh.pf;
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
@@ -786,7 +792,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     }
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));
-    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.grid, sh.block, sh.smem, s));
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.pf != 0, sh.grid, sh.block, sh.smem, s));
     if (timed) {
         GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s));
         h->prof_used++;
@@ -818,7 +824,7 @@ static gcp_status grad_from_args(gcp_handle* h, const gcp_factors* F, gcp_loss l
         a.G[k] = G[k];
         a.rep_stride[k] = 0;
     }
-    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.grid, sh.block, 0, s));
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, false, sh.grid, sh.block, 0, s));
     return GCP_OK;
 }
 

@@ -26,8 +26,8 @@
 
 namespace gcpk {
 
-template <int D, int L, int NC, bool BF16>
-__global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradArgs a)
+template <int D, int L, int NC, bool BF16, bool PF>
+__global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(const GradArgs a)
 {
     pdl_wait();
     pdl_trigger();
@@ -61,6 +61,60 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
     for (int64_t wb = warp_global * per_warp; wb < a.dr.n_total; wb += nwarps * per_warp) {
         Draw<D> my;
         make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
+        if constexpr (PF) {
+            // prefetch layout (one chunk per lane): the descriptors and row loads
+            // of all L draws of the group are issued before any is consumed, so
+            // the group waits for one round trip to L2 instead of L in turn
+            static_assert(NC == 1 && D <= 4, "prefetch layout: one chunk per lane, at most 4 modes");
+            const int col = gl * 4;
+            uint32_t pix[L][D];
+            float px[L], pw[L];
+            int pcls[L];
+            bool pv[L];
+            float4 rows[L][D];
+#pragma unroll
+            for (int b = 0; b < L; ++b) {
+                const int src = gbase + b;
+#pragma unroll
+                for (int k = 0; k < D; ++k) pix[b][k] = __shfl_sync(kFull, my.ix[k], src);
+                px[b] = __shfl_sync(kFull, my.x, src);
+                pw[b] = __shfl_sync(kFull, my.w, src);
+                pcls[b] = __shfl_sync(kFull, my.cls, src);
+                pv[b] = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    rows[b][k] = (pv[b] && col < rank)
+                                     ? load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(pix[b][k]) * ld + col)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int b = 0; b < L; ++b) {
+                const float4 p01 = mul4(rows[b][0], rows[b][1]);
+                const float4 p23 = D == 4 ? mul4(rows[b][2], rows[b][3]) : rows[b][D - 1];
+                float part = sum4(mul4(p01, p23));
+#pragma unroll
+                for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+                if (!pv[b] || col >= rank) continue;  // no shuffles below this point in the iteration
+                const float y = entry_y(a.loss, pcls[b], px[b], part, pw[b]);
+                float4 upd[D];
+                if constexpr (D == 4) {
+                    const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
+                    upd[0] = mul4(yp23, rows[b][1]);
+                    upd[1] = mul4(yp23, rows[b][0]);
+                    upd[2] = mul4(yp01, rows[b][3]);
+                    upd[3] = mul4(yp01, rows[b][2]);
+                } else {
+                    const float4 yr2 = scale4(y, rows[b][2]);
+                    upd[0] = mul4(yr2, rows[b][1]);
+                    upd[1] = mul4(yr2, rows[b][0]);
+                    upd[2] = scale4(y, p01);
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(pix[b][k]) * ld + col), upd[k]);
+            }
+            continue;
+        }
 #pragma unroll 1
         for (int b = 0; b < steps; ++b) {
             const int src = a.group_draws ? lane : gbase + b;
@@ -191,11 +245,19 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) grad_kernel(const GradA
 #define GCP_GRAD_CONFIGS(X) \
     X(1, 1) X(1, 2) X(1, 3) X(1, 4) X(2, 1) X(2, 2) X(4, 1) X(4, 2) X(8, 1) X(8, 2) X(16, 1) X(32, 1) X(32, 2)
 
+// The prefetch layout exists for one chunk per lane with 2 or 4 lanes (3 or 4 modes).
 template <int D, bool BF16>
-const void* grad_kernel_ptr(int L, int NC)
+const void* grad_kernel_ptr(int L, int NC, bool pf)
 {
+    if (pf) {
+        if constexpr (D <= 4) {
+            if (NC == 1 && L == 2) return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, true>);
+            if (NC == 1 && L == 4) return reinterpret_cast<const void*>(&grad_kernel<D, 4, 1, BF16, true>);
+        }
+        return nullptr;
+    }
 #define GCP_CASE(LL, CC) \
-    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16>);
+    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, false>);
     GCP_GRAD_CONFIGS(GCP_CASE)
 #undef GCP_CASE
     return nullptr;

@@ -173,10 +173,10 @@ inline cudaError_t launch_pdl_ptr(const void* kernel, dim3 grid, dim3 block, siz
 }
 
 // Launchers (defined in the kernel translation units).
-cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int grid, int block, size_t smem,
-                        cudaStream_t s);
-cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int block, size_t smem, int* blocks_per_sm);
-bool grad_has_config(int D, int L, int NC);
+cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, bool pf, int grid, int block,
+                        size_t smem, cudaStream_t s);
+cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, bool pf, int block, size_t smem, int* blocks_per_sm);
+bool grad_has_config(int D, int L, int NC, bool pf);
 
 cudaError_t launch_fold(const FoldArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_loss(const LossArgs& a, bool bf16, int grid, int block, cudaStream_t s);
