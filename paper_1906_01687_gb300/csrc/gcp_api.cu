@@ -389,7 +389,10 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     if (sh->pf && sh->smem > 0) sh->pf = 0;  // the prefetch layout accumulates through L2 only
     const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->pf != 0, sh->block, sh->smem, h->device);
     const int64_t resident = static_cast<int64_t>(h->num_sms) * bps;
-    sh->grid = static_cast<int>(t.grid_blocks > 0 ? t.grid_blocks : std::min<int64_t>(blocks_needed, resident));
+    // one resident wave; the kernel deals batches across all of its blocks
+    // evenly, so a launch that fills at least half the wave takes all of it
+    const int64_t auto_grid = blocks_needed * 2 >= resident ? resident : blocks_needed;
+    sh->grid = static_cast<int>(t.grid_blocks > 0 ? t.grid_blocks : auto_grid);
 
     // replica slabs for modes whose rows each receive many updates per launch
     const int64_t max_reps = t.max_replicas >= 0 ? t.max_replicas : 32;

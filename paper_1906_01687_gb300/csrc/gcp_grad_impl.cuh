@@ -42,7 +42,6 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
-    const int64_t warp_global = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int d = D <= 4 ? D : a.dr.d;
     const int ld = a.ld, rank = a.rank;
@@ -56,9 +55,13 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
     // makes one descriptor, each group walks its L draws), or with
     // group_draws 32 / L per step (each group makes its own draw's descriptor
     // in all its lanes and takes it at once: more warps, shorter chains)
+    // Batches are dealt to warps interleaved across blocks (batch i of a
+    // round goes to block i % gridDim.x), so that every SM of a resident
+    // wave receives the same share even when the draws fill only part of it.
     const int per_warp = a.group_draws ? 32 / L : 32;
     const int steps = a.group_draws ? 1 : L;
-    for (int64_t wb = warp_global * per_warp; wb < a.dr.n_total; wb += nwarps * per_warp) {
+    const int64_t my_slot = static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    for (int64_t wb = my_slot * per_warp; wb < a.dr.n_total; wb += nwarps * per_warp) {
         Draw<D> my;
         make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
         if constexpr (PF) {
