@@ -18,8 +18,7 @@ import math
 
 import numpy as np
 
-from . import (SEMI_STRATIFIED, STRATIFIED, UNIFORM, adam_step, concat_factors, grad,
-               loss_estimate, sample, split_factors)
+from . import adam_step, concat_factors, grad, loss_estimate, sample, split_factors
 
 EST_STREAM = 0xFFFFFFFFFFFFFFFF  # the Philox stream word of the fixed estimate set
 

@@ -183,18 +183,6 @@ DrawArgs make_draw_args(const gcp_handle* h, const gcp_sampling* S, const gcp_sa
     return a;
 }
 
-template <typename T>
-gcp_status grow(T** ptr, int64_t* cap, int64_t need)
-{
-    if (*cap >= need) return GCP_OK;
-    if (*ptr) cudaFree(*ptr);
-    *ptr = nullptr;
-    *cap = 0;
-    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(ptr), static_cast<size_t>(need) * sizeof(T)));
-    *cap = need;
-    return GCP_OK;
-}
-
 gcp_status ensure_hash(gcp_handle* h, cudaStream_t s)
 {
     if (h->table) return GCP_OK;

@@ -12,7 +12,6 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
-#include <type_traits>
 #include <vector>
 
 #include "gcp_device.cuh"
