@@ -490,15 +490,16 @@ gcp_status gcp_set_tuning(gcp_handle *h, const gcp_tuning *t);
 gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, gcp_launch_info *out);
 
 /* Kernel timing for benchmarks.  With enable = 1 the handle creates
-   capacity pairs of CUDA events (at most 65536; allocation, so call it
+   2 x capacity pairs of CUDA events (at most 65536; allocation, so call it
    outside stream capture) and records one pair on the launching stream
    around every fused-gradient kernel launch that follows (gcp_grad,
-   gcp_iteration), until the pairs are used up; enable = 0 destroys them.
-   gcp_profile_read synchronises those events and returns the summed device
-   time of the recorded launches in milliseconds and their count, then
-   starts a new count.  host outputs. */
+   gcp_iteration; set 0) and around every Adam kernel launch of
+   gcp_iteration (set 1), until the pairs are used up; enable = 0 destroys
+   them.  gcp_profile_read synchronises the events of set `which` and returns
+   the summed device time of its recorded launches in milliseconds and their
+   count, then starts a new count.  host outputs. */
 gcp_status gcp_profile(gcp_handle *h, int32_t enable, int32_t capacity);
-gcp_status gcp_profile_read(gcp_handle *h, double *total_ms, int64_t *launches);
+gcp_status gcp_profile_read(gcp_handle *h, int32_t which, double *total_ms, int64_t *launches);
 
 /* A static string naming a status code. */
 const char *gcp_status_string(gcp_status s);

@@ -54,10 +54,13 @@ struct gcp_handle {
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
-    // optional CUDA-event timing of the fused-gradient kernel
+    // optional CUDA-event timing of the fused-gradient kernel (set 0) and of
+    // gcp_iteration's Adam kernel (set 1)
     cudaEvent_t* prof_ev = nullptr;
     int32_t prof_cap = 0;
     int32_t prof_used = 0;
+    cudaEvent_t* prof_ev2 = nullptr;
+    int32_t prof_used2 = 0;
 };
 
 namespace {
@@ -543,10 +546,14 @@ gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream
 static void profile_free(gcp_handle* h)
 {
     if (!h->prof_ev) return;
-    for (int i = 0; i < 2 * h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
+    for (int i = 0; i < 2 * h->prof_cap; ++i) {
+        cudaEventDestroy(h->prof_ev[i]);
+        cudaEventDestroy(h->prof_ev2[i]);
+    }
     delete[] h->prof_ev;
-    h->prof_ev = nullptr;
-    h->prof_cap = h->prof_used = 0;
+    delete[] h->prof_ev2;
+    h->prof_ev = h->prof_ev2 = nullptr;
+    h->prof_cap = h->prof_used = h->prof_used2 = 0;
 }
 
 gcp_status gcp_profile(gcp_handle* h, int32_t enable, int32_t capacity)
@@ -555,34 +562,40 @@ gcp_status gcp_profile(gcp_handle* h, int32_t enable, int32_t capacity)
     GCP_CUDA_TRY(cudaDeviceSynchronize());
     profile_free(h);
     if (!enable) return GCP_OK;
-    h->prof_ev = new (std::nothrow) cudaEvent_t[2 * static_cast<size_t>(capacity)];
-    if (!h->prof_ev) return GCP_ERR_NO_MEMORY;
+    h->prof_ev = new (std::nothrow) cudaEvent_t[2 * static_cast<size_t>(capacity)]();
+    h->prof_ev2 = new (std::nothrow) cudaEvent_t[2 * static_cast<size_t>(capacity)]();
+    if (!h->prof_ev || !h->prof_ev2) {
+        delete[] h->prof_ev;
+        delete[] h->prof_ev2;
+        h->prof_ev = h->prof_ev2 = nullptr;
+        return GCP_ERR_NO_MEMORY;
+    }
+    h->prof_cap = capacity;
     for (int i = 0; i < 2 * capacity; ++i) {
-        if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) {
-            h->prof_cap = i / 2;
+        if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess || cudaEventCreate(&h->prof_ev2[i]) != cudaSuccess) {
             profile_free(h);
             return GCP_ERR_CUDA;
         }
-        h->prof_cap = (i + 1) / 2;
     }
-    h->prof_cap = capacity;
-    h->prof_used = 0;
+    h->prof_used = h->prof_used2 = 0;
     return GCP_OK;
 }
 
-gcp_status gcp_profile_read(gcp_handle* h, double* total_ms, int64_t* launches)
+gcp_status gcp_profile_read(gcp_handle* h, int32_t which, double* total_ms, int64_t* launches)
 {
-    if (!h || !total_ms || !launches) return GCP_ERR_INVALID_ARG;
+    if (!h || !total_ms || !launches || which < 0 || which > 1) return GCP_ERR_INVALID_ARG;
+    cudaEvent_t* ev = which == 0 ? h->prof_ev : h->prof_ev2;
+    int32_t* used = which == 0 ? &h->prof_used : &h->prof_used2;
     double sum = 0.0;
-    for (int i = 0; i < h->prof_used; ++i) {
-        GCP_CUDA_TRY(cudaEventSynchronize(h->prof_ev[2 * i + 1]));
+    for (int i = 0; i < *used; ++i) {
+        GCP_CUDA_TRY(cudaEventSynchronize(ev[2 * i + 1]));
         float ms = 0.f;
-        GCP_CUDA_TRY(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+        GCP_CUDA_TRY(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
         sum += ms;
     }
     *total_ms = sum;
-    *launches = h->prof_used;
-    h->prof_used = 0;
+    *launches = *used;
+    *used = 0;
     return GCP_OK;
 }
 
@@ -964,7 +977,13 @@ gcp_status gcp_iteration(gcp_handle* h, const gcp_factors* F, gcp_loss loss, con
     a.lower = prm->lower;
     a.eps_inside_sqrt = prm->eps_inside_sqrt;
     a.st = state;
+    const bool timed = h->prof_ev2 && h->prof_used2 < h->prof_cap;
+    if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev2[2 * h->prof_used2], s));
     GCP_CUDA_TRY(launch_adam(a, elementwise_grid(a.mt), s));
+    if (timed) {
+        GCP_CUDA_TRY(cudaEventRecord(h->prof_ev2[2 * h->prof_used2 + 1], s));
+        h->prof_used2++;
+    }
     return GCP_OK;
 }
 

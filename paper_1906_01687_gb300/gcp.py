@@ -103,7 +103,7 @@ _SIGS = {
     "gcp_set_tuning": ([_vp, _P(gcp_tuning)], ctypes.c_int),
     "gcp_get_launch": ([_vp, _P(gcp_factors), _i64, _P(gcp_launch_info)], ctypes.c_int),
     "gcp_profile": ([_vp, _i32, _i32], ctypes.c_int),
-    "gcp_profile_read": ([_vp, _P(ctypes.c_double), _P(_i64)], ctypes.c_int),
+    "gcp_profile_read": ([_vp, _i32, _P(ctypes.c_double), _P(_i64)], ctypes.c_int),
     "gcp_sample": ([_vp, _P(gcp_sampling), _P(gcp_samples), _vp], ctypes.c_int),
     "gcp_reserve": ([_vp, _P(gcp_sampling), _vp], ctypes.c_int),
     "gcp_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _P(gcp_samples), _vp, _P8, _vp], ctypes.c_int),
@@ -388,10 +388,11 @@ def gcp_profile(h: Handle, enable: bool, capacity: int = 1024):
     _check(_lib.gcp_profile(h.ptr, int(bool(enable)), int(capacity)), "gcp_profile")
 
 
-def gcp_profile_read(h: Handle):
-    """(total device milliseconds, launches) of the recorded gradient kernels."""
+def gcp_profile_read(h: Handle, which: int = 0):
+    """(total device milliseconds, launches) of the recorded gradient kernels
+    (which = 0) or of gcp_iteration's Adam kernels (which = 1)."""
     ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
-    _check(_lib.gcp_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(n)), "gcp_profile_read")
+    _check(_lib.gcp_profile_read(h.ptr, int(which), ctypes.byref(ms), ctypes.byref(n)), "gcp_profile_read")
     return ms.value, n.value
 
 

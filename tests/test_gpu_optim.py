@@ -282,6 +282,12 @@ def test_profile_events_count_gradient_kernels():
     assert n == 4 and ms > 0
     ms, n = g.gcp_profile_read(h)
     assert n == 0
+    B, C, st = F.like(), F.like(), g.new_state()
+    g.gcp_state_init(st, 0.01)
+    for x in G:
+        x.zero_()
+    g.gcp_iteration(h, F, 0, g.Sampling(g.SAMPLER_UNIFORM, 0, 5000, seed=1, stream=9), G, B, C, st)
+    assert g.gcp_profile_read(h, 0)[1] == 1 and g.gcp_profile_read(h, 1)[1] == 1
     g.gcp_profile(h, False)
 
 
