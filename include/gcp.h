@@ -454,6 +454,18 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    prefetch = 1 (one chunk per lane, 2 or 4 lanes, at most 4 modes): a group
    issues the row loads of all its draws before consuming any (one round
    trip to L2 per group walk instead of one per draw; more registers).
+   early_draws = 1: where the draws read nothing but the data tensor (uniform
+   sampling, semi-stratified sampling, or uniform over a sparse tensor whose
+   nonzero table was built by an earlier call), the kernel makes each warp's
+   first batch of draws (Philox, value gather) before it waits for the
+   kernel launched just before it on the stream (programmatic dependent
+   launch), so that work overlaps the previous kernel's tail.  Contract: the
+   data tensor's values and weights are not written by the kernel launched
+   immediately before the call (copies and anything further back are
+   ordered as usual).  With stream_dev, the kernel starts from a prediction
+   (the previous such launch's stream + 1), checks it against *stream_dev
+   after the wait and redoes the batch when it differs, so the draws are
+   always those of *stream_dev.  Default 0 (wait first).
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -466,6 +478,7 @@ typedef struct gcp_tuning {
     int32_t replica_target;
     int32_t group_draws;
     int32_t prefetch;
+    int32_t early_draws;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */
@@ -479,6 +492,7 @@ typedef struct gcp_launch_info {
     int32_t replicas[GCP_MAX_MODES];
     int32_t group_draws;
     int32_t prefetch;
+    int32_t early_draws;
 } gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch

@@ -7,6 +7,12 @@ read by the gradient kernel from the device state (``iter``), so an epoch's
 launches are identical every time and can be captured once in a CUDA graph
 and replayed; the host reads the 64-byte state only to decide when to stop.
 
+The gradient kernel of each iteration makes its first draws while the
+previous iteration's Adam step is still running (the handle's early_draws
+tuning, on by default here): the draws read only the data tensor, and the
+kernel checks its predicted stream word against the device counter after
+waiting, so the draws are the same as with the wait first.
+
 Readings of Alg. 4 (shared with the oracle's driver): the bias correction of
 step t uses t + 1; an equal estimate is accepted; a non-finite one fails; the
 draws' stream word counts every iteration ever run and is never wound back.
@@ -27,10 +33,13 @@ class GcpAdam:
                  beta2: float = 0.999, eps: float = 1e-8, tau: int = 1000, kappa: int = 1, nu: float = 0.1,
                  lower: float = -math.inf, bf16: bool = False, problem: int = 0, oversample: float = 1.1,
                  handle: Optional[gcp.Handle] = None, eps_inside_sqrt: bool = True, stream=None,
-                 autotune: bool = False):
+                 autotune: bool = False, early_draws: bool = True):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.stream.wait_stream(torch.cuda.current_stream())  # X and A0 may come from the current stream
         self.h = handle if handle is not None else gcp.Handle(X, stream=self.stream)
+        self.early_draws = bool(early_draws)
+        if self.early_draws:  # every other field of the handle's launch shape automatic
+            gcp.gcp_set_tuning(self.h, early_draws=1)
         self.loss = loss
         self.tau, self.kappa, self.nu = int(tau), int(kappa), float(nu)
         self.adam = dict(beta1=beta1, beta2=beta2, eps=eps, lower=lower, eps_inside_sqrt=eps_inside_sqrt)
@@ -87,7 +96,7 @@ class GcpAdam:
     def autotune(self, launches: int = 20):
         """Chooses the gradient's launch shape by timing whole iterations
         (gradient + Adam with the replica fold) on throwaway copies."""
-        from .autotune import autotune as _autotune
+        from .autotune import autotune as _autotune, candidates
         with torch.cuda.stream(self.stream):
             F = gcp.Factors([a[:, : self.F.rank] for a in self.F.A], bf16=self.F.bf16, device=self.F.A[0].device)
             G, B, C = F.like(), F.like(), F.like()
@@ -95,8 +104,11 @@ class GcpAdam:
             gcp.gcp_state_init(st, 0.0, stream=self.stream)
 
         def call(spec, stream):
-            gcp.gcp_iteration(self.h, F, self.loss, spec, G, B, C, st, stream=stream, **self.adam)
-        return _autotune(self.h, F, self.loss, self.spec, launches=launches, stream=self.stream, call=call)
+            gcp.gcp_iteration(self.h, F, self.loss, spec, G, B, C, st, stream_dev=st[3:4], stream=stream,
+                              **self.adam)
+        configs = [dict(c, early_draws=int(self.early_draws)) for c in candidates(F.rank)]
+        return _autotune(self.h, F, self.loss, self.spec, configs=configs, launches=launches, stream=self.stream,
+                         call=call)
 
     def capture(self):
         """Captures one epoch's launches in a CUDA graph (replayed by run_epoch)."""

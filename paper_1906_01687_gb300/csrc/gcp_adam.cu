@@ -2,8 +2,9 @@
 // state (F-hat, F-hat_old, t, iteration, alpha, failed epochs) kept in device
 // memory so that whole epochs can be replayed from a CUDA graph.
 //
-// Scalars that every block reads at its start are changed only by the last
-// block to finish (a completion ticket), after all blocks have read them.
+// Scalars that every block reads at its start are changed only after all
+// blocks have read them: by block 0 after a cluster barrier (small grids) or
+// by the last block to finish (a completion ticket).
 #include <cuda_bf16.h>
 
 #include "gcp_device.cuh"
@@ -55,22 +56,27 @@ __device__ __forceinline__ float adam_one(float& a, float& b, float& c, float g,
     return a;
 }
 
+// One launch of the Adam step.  Every thread reads the step's scalars (t,
+// alpha, done) itself, then issues the loads of its element -- the gradient,
+// its replica slabs, A, B, C -- before using any, so an element costs one
+// round trip to L2.  t and iter advance once every block has read them: with
+// a grid of at most 8 blocks launched as one thread-block cluster, through the
+// cluster barrier (each thread arrives right after its reads; block 0 waits
+// and writes); with a larger grid, through the completion ticket.
+template <bool kCluster>
 __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ float s_alpha, s_c1, s_c2;
-    __shared__ int s_done;
-    if (threadIdx.x == 0) {
-        // 1 - beta^n = -expm1(n log1p(beta - 1)): accurate to a few FP32 ulps even
-        // for beta near 1 and small n, where 1 - powf(beta, n) would cancel
-        const float n = static_cast<float>(a.st->t + 1);
-        s_c1 = -expm1f(n * log1pf(a.beta1 - 1.0f));
-        s_c2 = -expm1f(n * log1pf(a.beta2 - 1.0f));
-        s_alpha = a.st->alpha;
-        s_done = a.st->done;
-    }
-    __syncthreads();
+    const int64_t t0 = a.st->t;
+    const float alpha = a.st->alpha;
+    const int done = a.st->done;
+    if constexpr (kCluster) cluster_arrive();
+    // 1 - beta^n = -expm1(n log1p(beta - 1)): accurate to a few FP32 ulps even
+    // for beta near 1 and small n, where 1 - powf(beta, n) would cancel
+    const float n = static_cast<float>(t0 + 1);
+    const float c1 = -expm1f(n * log1pf(a.beta1 - 1.0f));
+    const float c2 = -expm1f(n * log1pf(a.beta2 - 1.0f));
     const ModeTable& mt = a.mt;
     const int64_t total4 = mt.off4[mt.d];
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -80,19 +86,19 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
         const int64_t loc = i4 - mt.off4[k];
         const int col = static_cast<int>((loc * 4) % mt.ld);
         float4* g4 = reinterpret_cast<float4*>(mt.G[k]) + loc;
+        float4* a4p = reinterpret_cast<float4*>(mt.A[k]) + loc;
+        float4* b4p = reinterpret_cast<float4*>(mt.B[k]) + loc;
+        float4* c4p = reinterpret_cast<float4*>(mt.C[k]) + loc;
         float4 g = *g4;
+        float4 A4 = *a4p, B4 = *b4p, C4 = *c4p;
         if (a.reps[k] > 1)  // fold the replica slabs of this mode, leaving them zero
             g = add4(g, fold_replicas(reinterpret_cast<float4*>(a.R[k]) + loc, a.reps[k], a.rep_stride4[k]));
-        if (!s_done && col < mt.rank) {
-            float4* a4p = reinterpret_cast<float4*>(mt.A[k]) + loc;
-            float4* b4p = reinterpret_cast<float4*>(mt.B[k]) + loc;
-            float4* c4p = reinterpret_cast<float4*>(mt.C[k]) + loc;
-            float4 A4 = *a4p, B4 = *b4p, C4 = *c4p;
+        if (!done && col < mt.rank) {
             const int live = mt.rank - col;  // columns of this chunk below rank
-            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
-            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
-            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
-            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, s_c1, s_c2, a.eps, s_alpha, a.lower, inside);
+            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
+            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
+            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
+            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
             *a4p = A4;
             *b4p = B4;
             *c4p = C4;
@@ -100,7 +106,13 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
         }
         *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (last_block_done(&a.st->ticket)) {
+    if constexpr (kCluster) {
+        cluster_wait();
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (!done) a.st->t = t0 + 1;
+            a.st->iter += 1;
+        }
+    } else if (last_block_done(&a.st->ticket)) {
         if (!a.st->done) a.st->t += 1;
         a.st->iter += 1;
         a.st->ticket = 0u;
@@ -108,9 +120,27 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
     }
 }
 
+// Grids of up to 8 blocks run as one cluster (rounded up to 1, 2, 4 or 8 blocks).
 cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s)
 {
-    return launch_pdl(adam_kernel, dim3(grid), dim3(256), 0, s, a);
+    if (grid > 8) return launch_pdl(adam_kernel<false>, dim3(grid), dim3(256), 0, s, a);
+    int c = 1;
+    while (c < grid) c <<= 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = static_cast<unsigned>(c);
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, adam_kernel<true>, a);
 }
 
 // epoch_begin (snapshot) and epoch_end (accept or revert)

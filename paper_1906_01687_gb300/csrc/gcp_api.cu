@@ -20,8 +20,8 @@ static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
 static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
-static_assert(sizeof(gcp_tuning) == 40, "gcp_tuning layout");
-static_assert(sizeof(gcp_launch_info) == 64, "gcp_launch_info layout");
+static_assert(sizeof(gcp_tuning) == 44, "gcp_tuning layout");
+static_assert(sizeof(gcp_launch_info) == 68, "gcp_launch_info layout");
 
 struct gcp_handle {
     gcp_tensor X{};
@@ -30,7 +30,7 @@ struct gcp_handle {
     double omega = 0.0;
     int rec_int4 = 0;
     int4* recs = nullptr;
-    int32_t* d_status = nullptr;
+    int32_t* d_status = nullptr;     // 16 bytes: the status word, then the predicted stream (int64)
     cudaStream_t last_stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -50,7 +50,7 @@ struct gcp_handle {
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
     int partials_cap = 0;
-    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0};
+    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0};
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
@@ -289,6 +289,7 @@ struct Shape {
     int64_t rep_floats = 0;  // replica workspace the shape needs
     int group = 0;           // group_draws layout
     int pf = 0;              // prefetch layout
+    int early = 0;           // early descriptors (where the draw source allows)
 };
 
 int next_pow2(int v)
@@ -354,6 +355,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     sh->block = t.block > 0 ? t.block : 256;
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
     sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;
+    sh->early = t.early_draws == 1 ? 1 : 0;
     sh->pf = (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, true) &&
               h->X.d == sh->D) ? 1 : 0;
     const int64_t per_warp = sh->group ? 32 / sh->L : 32;
@@ -522,13 +524,13 @@ gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream
     if (e != cudaSuccess) return fail(cuda_status(e));
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (h->num_sms < 1) h->num_sms = 1;
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), sizeof(int32_t))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), 16)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMalloc(reinterpret_cast<void**>(&h->zcount), sizeof(int64_t))) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMalloc(reinterpret_cast<void**>(&h->partials), kLossMaxBlocks * sizeof(double))) != cudaSuccess)
         return fail(cuda_status(e));
     if ((e = cudaMalloc(reinterpret_cast<void**>(&h->ticket), sizeof(unsigned int))) != cudaSuccess) return fail(cuda_status(e));
     h->partials_cap = kLossMaxBlocks;
-    if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s)) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMemsetAsync(h->d_status, 0, 16, s)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMemsetAsync(h->zcount, 0, sizeof(int64_t), s)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(cuda_status(e));
     if (X->sparse) {
@@ -635,14 +637,14 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     if (!t) {
-        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0};
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0};
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, false)) return GCP_ERR_INVALID_ARG;
     if (t->prefetch < 0 || t->prefetch > 1) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
-        t->group_draws < 0 || t->group_draws > 1)
+        t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1)
         return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
@@ -665,6 +667,7 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     out->smem_mode_mask = sh.mask;
     out->group_draws = sh.group;
     out->prefetch = sh.pf;
+    out->early_draws = sh.early;
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
@@ -727,12 +730,17 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     st = S ? check_spec(h, S) : check_list(h, list);
     if (st != GCP_OK) return st;
     h->last_stream = s;
+    const bool table_ready = h->table != nullptr;
     if (S && S->kind == GCP_SAMPLER_UNIFORM && h->X.sparse) {
         st = ensure_hash(h, s);
         if (st != GCP_OK) return st;
     }
     GradArgs a{};
     a.dr = make_draw_args(h, S, list, stream_dev);
+    // early descriptors only for draws that read nothing but the data tensor and
+    // tables built before this call (not a list, not a stratified zero list)
+    const bool early_ok = a.dr.src == kSrcUniformDense || (a.dr.src == kSrcUniformSparse && table_ready) ||
+                          (a.dr.src == kSrcSparse && a.dr.semi);
     if (a.dr.n_total == 0) return GCP_OK;
     if (S && S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
         st = ensure_zero_list(h, S->q);
@@ -761,6 +769,8 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     a.smem_floats = static_cast<int32_t>(sh.smem / 4);
     a.smem_mask = sh.mask;
     a.group_draws = sh.group;
+    a.early = (sh.early && early_ok) ? 1 : 0;
+    a.stream_pred = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(h->d_status) + 8);
     FoldArgs fold{};
     int64_t ws_off = 0;
     for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
@@ -822,6 +832,8 @@ static gcp_status grad_from_args(gcp_handle* h, const gcp_factors* F, gcp_loss l
     a.smem_floats = 0;
     a.smem_mask = 0;
     a.group_draws = sh.group;
+    a.early = 0;
+    a.stream_pred = nullptr;
     for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
     for (int k = 0; k < h->X.d; ++k) {
         a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);

@@ -176,40 +176,45 @@ __device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4
 __device__ __forceinline__ float sum4(float4 a) { return (a.x + a.y) + (a.z + a.w); }
 __device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
-// Sum of reps replica chunks r[0], r[stride], ... (each then zeroed), with
-// four loads in flight; the summation order is fixed by reps and stride.
+// Sum of reps replica chunks r[0], r[stride], ... (each then zeroed), added
+// in replica order.  The first 16 loads are all issued before any store, so
+// a fold of up to 16 replicas costs one round trip to L2; further replicas
+// follow one at a time.
 __device__ __forceinline__ float4 fold_replicas(float4* r, uint32_t reps, uint64_t stride)
 {
-    float4 acc[4] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                     make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    constexpr int kWide = 16;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t q = 0;
-    for (; q + 4 <= reps; q += 4) {
-        const float4 v0 = r[(q + 0) * stride], v1 = r[(q + 1) * stride];
-        const float4 v2 = r[(q + 2) * stride], v3 = r[(q + 3) * stride];
-        r[(q + 0) * stride] = zero;
-        r[(q + 1) * stride] = zero;
-        r[(q + 2) * stride] = zero;
-        r[(q + 3) * stride] = zero;
-        acc[0] = add4(acc[0], v0);
-        acc[1] = add4(acc[1], v1);
-        acc[2] = add4(acc[2], v2);
-        acc[3] = add4(acc[3], v3);
-    }
-    for (; q < reps; ++q) {
-        acc[0] = add4(acc[0], r[q * stride]);
+    float4 v[kWide];
+#pragma unroll
+    for (int q = 0; q < kWide; ++q) v[q] = static_cast<uint32_t>(q) < reps ? r[q * stride] : zero;
+    float4 acc = zero;
+#pragma unroll
+    for (int q = 0; q < kWide; ++q) acc = add4(acc, v[q]);
+#pragma unroll
+    for (int q = 0; q < kWide; ++q)
+        if (static_cast<uint32_t>(q) < reps) r[q * stride] = zero;
+    for (uint32_t q = kWide; q < reps; ++q) {
+        acc = add4(acc, r[q * stride]);
         r[q * stride] = zero;
     }
-    return add4(add4(acc[0], acc[1]), add4(acc[2], acc[3]));
+    return acc;
 }
+
+// Cluster barrier halves (all threads of every block of the cluster): arrive
+// releases this thread's earlier memory accesses, wait acquires everyone's.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 // Programmatic dependent launch.  A kernel launched with the programmatic
 // stream-serialization attribute may begin while its predecessor in the
 // stream is still running; pdl_wait() blocks until that predecessor has
 // completed and its writes are visible (a no-op after a normal launch), and
 // pdl_trigger() lets the successor begin launching.  Every kernel of the path
-// calls pdl_wait() before its first global-memory access, so the overlap
-// covers launch and block scheduling only, never data.
+// calls pdl_wait() before pdl_trigger(), so when a kernel starts, the kernel
+// two launches before it has completed.  Every kernel calls pdl_wait() before
+// its first global-memory access, with one exception: the gradient kernel's
+// early descriptors read the data tensor and the handle's nonzero tables
+// (written, if ever, at least two launches back) before waiting.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

@@ -18,6 +18,15 @@
 // are hit many times per launch adds into one of several replica slabs
 // (CTA b into replica b % reps), which keeps same-address contention at L2
 // low; a fold kernel then sums the replicas into G_k.
+//
+// Early descriptors.  With a.early the first batch of each warp is drawn
+// before the dependency wait (griddepcontrol.wait), while the preceding
+// kernel (the previous iteration's Adam step) is still running: the draw
+// reads only the data tensor, which no kernel of the sequence writes.  The
+// updates, which need the preceding kernel's factors and zeroed
+// accumulators, come after the wait.  When the stream word is read from
+// device memory the kernel starts from a predicted stream and checks it
+// after the wait.
 #pragma once
 
 #include <type_traits>
@@ -29,8 +38,11 @@ namespace gcpk {
 template <int D, int L, int NC, bool BF16, bool PF>
 __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(const GradArgs a)
 {
-    pdl_wait();
-    pdl_trigger();
+    const bool early = a.early != 0;
+    if (!early) {
+        pdl_wait();
+        pdl_trigger();
+    }
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
@@ -38,7 +50,13 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
     __syncthreads();
 
     constexpr unsigned kFull = 0xFFFFFFFFu;
-    const uint64_t stream = read_stream(a.dr);
+    // the stream word: exact, or (early with a device stream word) predicted
+    uint64_t stream = early && a.dr.stream_dev
+                          ? static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.stream_pred))
+                          : read_stream(a.dr);
+    if (!early && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
+        *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(stream + 1);
+    bool waited = !early;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
@@ -64,6 +82,20 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
     for (int64_t wb = my_slot * per_warp; wb < a.dr.n_total; wb += nwarps * per_warp) {
         Draw<D> my;
         make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
+        if (!waited) {
+            pdl_wait();
+            pdl_trigger();
+            waited = true;
+            if (a.dr.stream_dev) {
+                const uint64_t actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
+                if (blockIdx.x == 0 && threadIdx.x == 0)
+                    *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
+                if (actual != stream) {  // warp-uniform: every lane read the same words
+                    stream = actual;
+                    make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
+                }
+            }
+        }
         if constexpr (PF) {
             // prefetch layout (one chunk per lane): the descriptors and row loads
             // of all L draws of the group are issued before any is consumed, so
@@ -231,6 +263,7 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
     }
 
     if (a.smem_mask == 0) return;
+    if (!waited) pdl_wait();  // a warp with no draws still waits before the block's flush
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < d; ++k) {

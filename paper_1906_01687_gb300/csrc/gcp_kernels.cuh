@@ -57,7 +57,8 @@ struct GradArgs {
     uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
     uint32_t smem_off[GCP_MAX_MODES];
     int32_t group_draws;           // 1: each group of L lanes takes its own draw (32/L draws per warp step)
-    int32_t pad2;
+    int32_t early;                 // 1: each warp's first descriptors are made before the dependency wait
+    int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
 };
 
 // Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).

@@ -28,9 +28,11 @@ def flat(mats, rank):
 
 @pytest.mark.parametrize("rank,lower,inside", [(10, -math.inf, True), (3, 0.0, True), (32, -math.inf, False),
                                                (7, -0.05, True)])
-def test_adam_steps_match_oracle(rank, lower, inside):
+@pytest.mark.parametrize("dims", [(37, 20, 9), (3001, 20, 9)], ids=["cluster", "ticket"])
+def test_adam_steps_match_oracle(rank, lower, inside, dims):
+    """Small factor sets take the one-cluster Adam launch (<= 8 blocks), large
+    ones the completion-ticket launch; both match the oracle's Alg. 4 step."""
     g = gcp()
-    dims = (37, 20, 9)
     rs = np.random.default_rng(rank)
     A = [rs.standard_normal((n, rank)).astype(np.float32) for n in dims]
     F = g.Factors(A)
@@ -233,13 +235,16 @@ def test_planted_recovery_on_gpu():
     assert cosine_score(true, run.factors()) >= 0.9
 
 
-@pytest.mark.parametrize("kind", ["uniform", "stratified"])
+@pytest.mark.parametrize("kind", ["uniform", "stratified", "uniform_large"])
 def test_fused_iteration_equals_grad_then_adam(kind):
     """gcp_iteration (gradient + Adam with the replica fold inside Adam) gives
-    the factors of gcp_grad followed by gcp_adam_step on the same draws."""
+    the factors of gcp_grad followed by gcp_adam_step on the same draws: with
+    more than 16 replicas per mode (the fold's tail), and with factor sets
+    small enough for the one-cluster Adam launch and large enough for the
+    ticket launch."""
     g = gcp()
-    if kind == "uniform":
-        dims = (60, 50, 40, 30)
+    if kind in ("uniform", "uniform_large"):
+        dims = (60, 50, 40, 30) if kind == "uniform" else (3000, 40, 30)
         X = np.random.default_rng(3).standard_normal(dims).astype(np.float32)
         h = g.Handle(g.DataTensor.dense(X))
         S = g.Sampling(g.SAMPLER_UNIFORM, 0, 50000, seed=3, stream=5)
@@ -265,7 +270,14 @@ def test_fused_iteration_equals_grad_then_adam(kind):
         assert all(torch.count_nonzero(x).item() == 0 for x in G)
         runs.append(flat(F.A, 10))
         assert g.read_state(st)["t"] == 3
-    np.testing.assert_allclose(runs[0], runs[1], rtol=1e-4, atol=1e-6)
+    # The two runs add the same terms in different orders.  An entry of G that
+    # nearly cancels (a row hit by few draws) keeps only rounding noise, and
+    # Adam's normalised step turns it into a move of up to alpha per step, so
+    # single entries may differ by up to steps * alpha while all others agree
+    # to FP32 noise.
+    diff = np.abs(runs[0] - runs[1])
+    assert diff.max() <= 3 * 0.01 * 1.01
+    assert np.count_nonzero(diff > 1e-5 * np.abs(runs[1]).max()) <= 1e-3 * diff.size
 
 
 def test_profile_events_count_gradient_kernels():
