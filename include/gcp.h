@@ -330,7 +330,9 @@ gcp_status gcp_state_init(gcp_adam_state *state, float alpha, gcp_stream_t strea
    (or sqrt(Ch) + eps); then G = 0, the BF16 copy (where non-NULL) is
    re-rounded from A, and state->t, state->iter advance by one.  alpha is
    read from state.  B, C, G: device FP32 with A's layout.  Does nothing
-   but zero G once state->done is set.  dims: host, d entries. */
+   but zero G once state->done is set.  dims: host, d entries.  Factor sets
+   of 2^31 or more float4 chunks (sum of n_k * ld / 4; 32 GB) are rejected
+   with GCP_ERR_INVALID_ARG. */
 gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
                          float *const G[GCP_MAX_MODES], float *const B[GCP_MAX_MODES],
                          float *const C[GCP_MAX_MODES], const gcp_adam_params *prm,
@@ -342,7 +344,10 @@ gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
    inside the Adam kernel (two kernel launches per iteration, three with a
    stratified spec's zero pass counted as one).  G must be zero on entry and
    is left zero; B, C, state as for gcp_adam_step.  Same results as
-   gcp_grad followed by gcp_adam_step up to the summation order. */
+   gcp_grad followed by gcp_adam_step up to the summation order.  Between
+   the two kernels state->t has already advanced (the gradient kernel does
+   it, so that the Adam kernel's blocks need not wait for one another); on
+   return both t and iter have advanced by one, as with gcp_adam_step. */
 gcp_status gcp_iteration(gcp_handle *h, const gcp_factors *F, gcp_loss loss, const gcp_sampling *S,
                          const int64_t *stream_dev, float *const G[GCP_MAX_MODES], float *const B[GCP_MAX_MODES],
                          float *const C[GCP_MAX_MODES], const gcp_adam_params *prm, gcp_adam_state *state,

@@ -95,7 +95,9 @@ class GcpAdam:
 
     def autotune(self, launches: int = 20):
         """Chooses the gradient's launch shape by timing whole iterations
-        (gradient + Adam with the replica fold) on throwaway copies."""
+        (gradient + Adam with the replica fold) on throwaway copies, captured
+        in a CUDA graph as an epoch is, so that the overlap between one
+        iteration's kernels and the next is part of the measurement."""
         from .autotune import autotune as _autotune, candidates
         with torch.cuda.stream(self.stream):
             F = gcp.Factors([a[:, : self.F.rank] for a in self.F.A], bf16=self.F.bf16, device=self.F.A[0].device)
@@ -108,7 +110,7 @@ class GcpAdam:
                               **self.adam)
         configs = [dict(c, early_draws=int(self.early_draws)) for c in candidates(F.rank)]
         return _autotune(self.h, F, self.loss, self.spec, configs=configs, launches=launches, stream=self.stream,
-                         call=call)
+                         call=call, graph=True)
 
     def capture(self):
         """Captures one epoch's launches in a CUDA graph (replayed by run_epoch)."""

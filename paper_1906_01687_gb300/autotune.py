@@ -49,15 +49,41 @@ def candidates(rank: int) -> list:
     return out
 
 
-def time_grad(h, F, loss, spec, launches=20, stream=None, call=None) -> float:
+def time_graph(call, spec, launches, stream) -> float:
+    """Device time (s) per call of `launches` back-to-back calls captured in a
+    CUDA graph: the calls overlap as they do in a captured epoch."""
+    with torch.cuda.stream(stream):
+        call(spec, stream)  # allocate any workspace outside the capture
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=stream.device)
+    with torch.cuda.graph(g, stream=cap):
+        for i in range(launches):
+            s = gcp.Sampling(spec.kind, spec.p, spec.q, spec.seed, (1 << 62) + i, spec.problem, spec.oversample)
+            call(s, cap)
+    with torch.cuda.stream(stream):
+        g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            g.replay()
+        b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) * 1e-3 / (3 * launches)
+
+
+def time_grad(h, F, loss, spec, launches=20, stream=None, call=None, graph=False) -> float:
     """Median device time (s) of one gcp_grad call (or of call(spec, stream))
-    for the current tuning."""
+    for the current tuning; with graph, the time per call of a captured
+    sequence of calls."""
     stream = stream or torch.cuda.current_stream()
     if call is None:
         G = F.like()
 
         def call(s, st):
             gcp.gcp_grad(h, F, loss, G, S=s, stream=st)
+    if graph:
+        return time_graph(call, spec, launches, stream)
     with torch.cuda.stream(stream):
         call(spec, stream)  # allocate any workspace outside the timing
         stream.synchronize()
@@ -73,10 +99,10 @@ def time_grad(h, F, loss, spec, launches=20, stream=None, call=None) -> float:
 
 
 def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launches=20, stream=None,
-             log=None, call=None) -> dict:
+             log=None, call=None, graph=False) -> dict:
     """Times every candidate (gcp_grad, or call(spec, stream) when given, e.g.
-    a whole GCP-Adam iteration), sets the fastest on the handle, returns it
-    with its time."""
+    a whole GCP-Adam iteration; with graph, as a captured sequence of calls),
+    sets the fastest on the handle, returns it with its time."""
     best, best_t = None, float("inf")
     results = []
     for cfg in configs if configs is not None else candidates(F.rank):
@@ -84,7 +110,7 @@ def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launche
             gcp.gcp_set_tuning(h, **cfg)
         except gcp.GcpError:
             continue
-        t = time_grad(h, F, loss, spec, launches, stream, call)
+        t = time_grad(h, F, loss, spec, launches, stream, call, graph)
         results.append((t, cfg))
         if log:
             log(dict(seconds=t, **cfg))

@@ -7,6 +7,8 @@
 // by the last block to finish (a completion ticket).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "gcp_device.cuh"
 #include "gcp_kernels.cuh"
 
@@ -44,26 +46,34 @@ __device__ __forceinline__ bool last_block_done(unsigned int* ticket)
     return is_last && threadIdx.x == 0;
 }
 
+// One entry of the Adam step with the bias corrections given as reciprocals
+// (ic1 = 1 / (1 - beta1^n), ic2 = 1 / (1 - beta2^n)).  The step bh / den is
+// taken with the hardware reciprocal square root (eps inside the root) or
+// the fast division (eps outside): a few FP32 ulps of the step, far below
+// the FP32 rounding of the factor itself for any alpha < 1.
 __device__ __forceinline__ float adam_one(float& a, float& b, float& c, float g, float beta1, float beta2,
-                                          float c1, float c2, float eps, float alpha, float lower, bool inside)
+                                          float ic1, float ic2, float eps, float alpha, float lower, bool inside)
 {
     b = beta1 * b + (1.0f - beta1) * g;
     c = beta2 * c + (1.0f - beta2) * (g * g);
-    const float bh = b / c1;
-    const float ch = c / c2;
-    const float den = inside ? sqrtf(ch + eps) : sqrtf(ch) + eps;
-    a = fmaxf(a - alpha * (bh / den), lower);
+    const float bh = b * ic1;
+    const float ch = c * ic2;
+    const float step = inside ? bh * rsqrtf(ch + eps) : __fdividef(bh, sqrtf(ch) + eps);
+    a = fmaxf(a - alpha * step, lower);
     return a;
 }
 
 // One launch of the Adam step.  Every thread reads the step's scalars (t,
 // alpha, done) itself, then issues the loads of its element -- the gradient,
 // its replica slabs, A, B, C -- before using any, so an element costs one
-// round trip to L2.  t and iter advance once every block has read them: with
-// a grid of at most 8 blocks launched as one thread-block cluster, through the
-// cluster barrier (each thread arrives right after its reads; block 0 waits
-// and writes); with a larger grid, through the completion ticket.
-template <bool kCluster>
+// round trip to L2.  kSync says how t and iter advance:
+//   kTicket:   after every block has read t, by the last block to finish;
+//   kCluster:  a grid of at most 8 blocks launched as one thread-block
+//              cluster; each thread arrives at the cluster barrier right after
+//              its reads, block 0 waits and writes.
+enum AdamSync { kTicket = 0, kCluster = 1 };
+
+template <int kSync>
 __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
 {
     pdl_wait();
@@ -71,20 +81,22 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
     const int64_t t0 = a.st->t;
     const float alpha = a.st->alpha;
     const int done = a.st->done;
-    if constexpr (kCluster) cluster_arrive();
+    if constexpr (kSync == kCluster) cluster_arrive();
     // 1 - beta^n = -expm1(n log1p(beta - 1)): accurate to a few FP32 ulps even
     // for beta near 1 and small n, where 1 - powf(beta, n) would cancel
     const float n = static_cast<float>(t0 + 1);
-    const float c1 = -expm1f(n * log1pf(a.beta1 - 1.0f));
-    const float c2 = -expm1f(n * log1pf(a.beta2 - 1.0f));
+    const float ic1 = 1.0f / -expm1f(n * log1pf(a.beta1 - 1.0f));
+    const float ic2 = 1.0f / -expm1f(n * log1pf(a.beta2 - 1.0f));
     const ModeTable& mt = a.mt;
-    const int64_t total4 = mt.off4[mt.d];
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    // 32-bit element indices: the host keeps the factor set below 2^31 float4 chunks
+    const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
+    const uint32_t ld4 = static_cast<uint32_t>(mt.ld) / 4;
+    const uint32_t stride = gridDim.x * blockDim.x;
     const bool inside = a.eps_inside_sqrt != 0;
-    for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
+    for (uint32_t i4 = blockIdx.x * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
         const int k = mode_of(mt, i4);
-        const int64_t loc = i4 - mt.off4[k];
-        const int col = static_cast<int>((loc * 4) % mt.ld);
+        const uint32_t loc = i4 - static_cast<uint32_t>(mt.off4[k]);
+        const int col = static_cast<int>((loc % ld4) * 4);
         float4* g4 = reinterpret_cast<float4*>(mt.G[k]) + loc;
         float4* a4p = reinterpret_cast<float4*>(mt.A[k]) + loc;
         float4* b4p = reinterpret_cast<float4*>(mt.B[k]) + loc;
@@ -95,18 +107,18 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
             g = add4(g, fold_replicas(reinterpret_cast<float4*>(a.R[k]) + loc, a.reps[k], a.rep_stride4[k]));
         if (!done && col < mt.rank) {
             const int live = mt.rank - col;  // columns of this chunk below rank
-            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
-            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
-            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
-            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, c1, c2, a.eps, alpha, a.lower, inside);
+            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
             *a4p = A4;
             *b4p = B4;
             *c4p = C4;
-            if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + loc * 4, A4);
+            if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + static_cast<size_t>(loc) * 4, A4);
         }
         *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if constexpr (kCluster) {
+    if constexpr (kSync == kCluster) {
         cluster_wait();
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             if (!done) a.st->t = t0 + 1;
@@ -123,7 +135,7 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
 // Grids of up to 8 blocks run as one cluster (rounded up to 1, 2, 4 or 8 blocks).
 cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s)
 {
-    if (grid > 8) return launch_pdl(adam_kernel<false>, dim3(grid), dim3(256), 0, s, a);
+    if (grid > 8) return launch_pdl(adam_kernel<kTicket>, dim3(grid), dim3(256), 0, s, a);
     int c = 1;
     while (c < grid) c <<= 1;
     cudaLaunchConfig_t cfg{};
@@ -140,7 +152,108 @@ cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s)
     attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, adam_kernel<true>, a);
+    return cudaLaunchKernelEx(&cfg, adam_kernel<kCluster>, a);
+}
+
+// The step after a gradient kernel that advanced t (gcp_iteration), with
+// the replica fold split over kParts lanes per float4 element: lane p of an
+// element's group adds replicas p, p + kParts, ... (all its loads in flight
+// at once) and zeroes them, the group sums its partials with shuffles in a
+// fixed order, and lane 0 applies the Adam update.  Each thread so has a few
+// loads outstanding instead of all of an element's replicas, and the work is
+// spread thinly (64 threads per block) over many SMs.  No block waits for
+// another: t was advanced by the gradient kernel; block 0 advances iter,
+// which no Adam block reads.
+constexpr int kParts = 4;
+
+__global__ void __launch_bounds__(64) adam_split_kernel(const AdamArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int64_t t0 = a.st->t;
+    const float alpha = a.st->alpha;
+    const int done = a.st->done;
+    const float n = static_cast<float>(t0);  // already advanced for this step
+    const float ic1 = 1.0f / -expm1f(n * log1pf(a.beta1 - 1.0f));
+    const float ic2 = 1.0f / -expm1f(n * log1pf(a.beta2 - 1.0f));
+    const ModeTable& mt = a.mt;
+    const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
+    const uint32_t ld4 = static_cast<uint32_t>(mt.ld) / 4;
+    const bool inside = a.eps_inside_sqrt != 0;
+    const uint32_t part = threadIdx.x % kParts;
+    const uint32_t stride = gridDim.x * blockDim.x / kParts;  // elements per grid step
+    // warp-uniform trip count: every lane of a warp takes part in the shuffles
+    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) / kParts;
+    const uint32_t warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / kParts;
+    for (uint32_t w4 = warp_first, i4 = first; w4 < total4; w4 += stride, i4 += stride) {
+        const bool live_elem = i4 < total4;
+        int k = 0;
+        uint32_t loc = 0;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 g = acc, A4 = acc, B4 = acc, C4 = acc;
+        if (live_elem) {
+            k = mode_of(mt, i4);
+            loc = i4 - static_cast<uint32_t>(mt.off4[k]);
+            if (part == 0) {
+                g = reinterpret_cast<const float4*>(mt.G[k])[loc];
+                A4 = reinterpret_cast<const float4*>(mt.A[k])[loc];
+                B4 = reinterpret_cast<const float4*>(mt.B[k])[loc];
+                C4 = reinterpret_cast<const float4*>(mt.C[k])[loc];
+            }
+            const uint32_t reps = a.reps[k] > 1 ? a.reps[k] : 0;
+            float4* r = reinterpret_cast<float4*>(a.R[k]) + loc;
+            const uint64_t rs = a.rep_stride4[k];
+            constexpr int kWide = 8;  // per lane: replicas part, part + kParts, ... (up to 32 in flight per group)
+            float4 v[kWide];
+#pragma unroll
+            for (int q = 0; q < kWide; ++q) {
+                const uint32_t rep = part + static_cast<uint32_t>(q) * kParts;
+                v[q] = rep < reps ? r[rep * rs] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < kWide; ++q) acc = add4(acc, v[q]);
+#pragma unroll
+            for (int q = 0; q < kWide; ++q) {
+                const uint32_t rep = part + static_cast<uint32_t>(q) * kParts;
+                if (rep < reps) r[rep * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            for (uint32_t rep = part + kWide * kParts; rep < reps; rep += kParts) {
+                acc = add4(acc, r[rep * rs]);
+                r[rep * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        // the group's partial sums: lane 0 ends with ((p0 + p1) + (p2 + p3))
+#pragma unroll
+        for (int off = 1; off < kParts; off <<= 1) {
+            acc.x += __shfl_xor_sync(0xFFFFFFFFu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xFFFFFFFFu, acc.y, off);
+            acc.z += __shfl_xor_sync(0xFFFFFFFFu, acc.z, off);
+            acc.w += __shfl_xor_sync(0xFFFFFFFFu, acc.w, off);
+        }
+        if (!live_elem || part != 0) continue;
+        g = add4(g, acc);
+        const int col = static_cast<int>((loc % ld4) * 4);
+        if (!done && col < mt.rank) {
+            const int live = mt.rank - col;  // columns of this chunk below rank
+            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+            reinterpret_cast<float4*>(mt.A[k])[loc] = A4;
+            reinterpret_cast<float4*>(mt.B[k])[loc] = B4;
+            reinterpret_cast<float4*>(mt.C[k])[loc] = C4;
+            if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + static_cast<size_t>(loc) * 4, A4);
+        }
+        reinterpret_cast<float4*>(mt.G[k])[loc] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->iter += 1;
+}
+
+cudaError_t launch_adam_advanced(const AdamArgs& a, int num_sms, cudaStream_t s)
+{
+    const int64_t threads = a.mt.off4[a.mt.d] * kParts;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((threads + 63) / 64, int64_t(num_sms) * 32));
+    return launch_pdl(adam_split_kernel, dim3(static_cast<unsigned>(grid)), dim3(64), 0, s, a);
 }
 
 // epoch_begin (snapshot) and epoch_end (accept or revert)

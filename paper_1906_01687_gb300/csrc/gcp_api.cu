@@ -290,6 +290,7 @@ struct Shape {
     int group = 0;           // group_draws layout
     int pf = 0;              // prefetch layout
     int early = 0;           // early descriptors (where the draw source allows)
+    int layout() const { return pf ? 1 : 0; }
 };
 
 int next_pow2(int v)
@@ -300,7 +301,7 @@ int next_pow2(int v)
 }
 
 struct OccKey {
-    int D, L, NC, bf16, pf, block;
+    int D, L, NC, bf16, layout, block;
     size_t smem;
     int device;
 };
@@ -312,18 +313,18 @@ std::mutex g_occ_mutex;
 OccEntry g_occ[256];
 int g_occ_n = 0;
 
-int occupancy(int D, int L, int NC, bool bf16, bool pf, int block, size_t smem, int device)
+int occupancy(int D, int L, int NC, bool bf16, int layout, int block, size_t smem, int device)
 {
     std::lock_guard<std::mutex> lock(g_occ_mutex);
     for (int i = 0; i < g_occ_n; ++i) {
         const OccKey& k = g_occ[i].key;
-        if (k.D == D && k.L == L && k.NC == NC && k.bf16 == int(bf16) && k.pf == int(pf) && k.block == block &&
+        if (k.D == D && k.L == L && k.NC == NC && k.bf16 == int(bf16) && k.layout == layout && k.block == block &&
             k.smem == smem && k.device == device)
             return g_occ[i].bps;
     }
     int bps = 0;
-    if (grad_occupancy(D, L, NC, bf16, pf, block, smem, &bps) != cudaSuccess || bps < 1) bps = 1;
-    if (g_occ_n < 256) g_occ[g_occ_n++] = OccEntry{OccKey{D, L, NC, int(bf16), int(pf), block, smem, device}, bps};
+    if (grad_occupancy(D, L, NC, bf16, layout, block, smem, &bps) != cudaSuccess || bps < 1) bps = 1;
+    if (g_occ_n < 256) g_occ[g_occ_n++] = OccEntry{OccKey{D, L, NC, int(bf16), layout, block, smem, device}, bps};
     return bps;
 }
 
@@ -336,7 +337,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     if (t.lanes > 0) {
         sh->L = t.lanes;
         sh->NC = t.chunks > 0 ? t.chunks : 1;
-        if (!grad_has_config(sh->D, sh->L, sh->NC, false) || sh->L * sh->NC < chunks) return GCP_ERR_INVALID_ARG;
+        if (!grad_has_config(sh->D, sh->L, sh->NC, 0) || sh->L * sh->NC < chunks) return GCP_ERR_INVALID_ARG;
     } else if (chunks <= 32) {  // one float4 chunk per lane: measured fastest across ranks
         sh->L = next_pow2(chunks);
         sh->NC = 1;
@@ -344,7 +345,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
         sh->L = 32;
         sh->NC = 2;
     }
-    if (!grad_has_config(sh->D, sh->L, sh->NC, false)) {  // automatic choices must be compiled pairs
+    if (!grad_has_config(sh->D, sh->L, sh->NC, 0)) {  // automatic choices must be compiled pairs
         sh->L = 32;
         sh->NC = chunks <= 32 ? 1 : 2;
         if (chunks <= 4) {
@@ -356,7 +357,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
     sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;
     sh->early = t.early_draws == 1 ? 1 : 0;
-    sh->pf = (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, true) &&
+    sh->pf = (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 1) &&
               h->X.d == sh->D) ? 1 : 0;
     const int64_t per_warp = sh->group ? 32 / sh->L : 32;
     const int64_t warps = (n_total + per_warp - 1) / per_warp;
@@ -380,7 +381,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     }
     sh->smem = static_cast<size_t>(used);
     if (sh->pf && sh->smem > 0) sh->pf = 0;  // the prefetch layout accumulates through L2 only
-    const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->pf != 0, sh->block, sh->smem, h->device);
+    const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->layout(), sh->block, sh->smem, h->device);
     const int64_t resident = static_cast<int64_t>(h->num_sms) * bps;
     // one resident wave; the kernel deals batches across all of its blocks
     // evenly, so a launch that fills at least half the wave takes all of it
@@ -640,7 +641,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
         h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0};
         return GCP_OK;
     }
-    if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, false)) return GCP_ERR_INVALID_ARG;
+    if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, 0)) return GCP_ERR_INVALID_ARG;
     if (t->prefetch < 0 || t->prefetch > 1) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
@@ -718,10 +719,14 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
     return GCP_OK;
 }
 
+// advance_t (gcp_iteration): the gradient kernel advances advance_t->t for the
+// Adam step that follows; *launched reports whether a gradient kernel ran.
 static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
                             const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
-                            cudaStream_t s, FoldArgs* deferred_fold)
+                            cudaStream_t s, FoldArgs* deferred_fold, gcp_adam_state* advance_t = nullptr,
+                            bool* launched = nullptr)
 {
+    if (launched) *launched = false;
     if (!h || (S == nullptr) == (list == nullptr)) return GCP_ERR_INVALID_ARG;
     if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     gcp_status st = check_factors(h, F);
@@ -771,6 +776,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     a.group_draws = sh.group;
     a.early = (sh.early && early_ok) ? 1 : 0;
     a.stream_pred = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(h->d_status) + 8);
+    a.st_advance = advance_t;
     FoldArgs fold{};
     int64_t ws_off = 0;
     for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
@@ -806,7 +812,8 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     }
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));
-    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.pf != 0, sh.grid, sh.block, sh.smem, s));
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.layout(), sh.grid, sh.block, sh.smem, s));
+    if (launched) *launched = true;
     if (timed) {
         GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s));
         h->prof_used++;
@@ -834,13 +841,14 @@ static gcp_status grad_from_args(gcp_handle* h, const gcp_factors* F, gcp_loss l
     a.group_draws = sh.group;
     a.early = 0;
     a.stream_pred = nullptr;
+    a.st_advance = nullptr;
     for (int k = 0; k < GCP_MAX_MODES; ++k) a.reps[k] = 1;
     for (int k = 0; k < h->X.d; ++k) {
         a.A[k] = F->bf16 ? static_cast<const void*>(F->A_bf16[k]) : static_cast<const void*>(F->A[k]);
         a.G[k] = G[k];
         a.rep_stride[k] = 0;
     }
-    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, false, sh.grid, sh.block, 0, s));
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, 0, sh.grid, sh.block, 0, s));
     return GCP_OK;
 }
 
@@ -942,6 +950,7 @@ gcp_status gcp_adam_step(const gcp_factors* F, int32_t d, const int64_t* dims, f
         return GCP_ERR_INVALID_ARG;
     AdamArgs a{};
     a.mt = mode_table(F, d, dims);
+    if (a.mt.off4[a.mt.d] >= (int64_t(1) << 31)) return GCP_ERR_INVALID_ARG;  // 32-bit element indices
     for (int k = 0; k < d; ++k) {
         a.mt.G[k] = G[k];
         a.mt.B[k] = B[k];
@@ -969,9 +978,12 @@ gcp_status gcp_iteration(gcp_handle* h, const gcp_factors* F, gcp_loss loss, con
     if (!prm || !state || !aligned(state, 8) || !modes_ok(B, h->X.d) || !modes_ok(C, h->X.d)) return GCP_ERR_INVALID_ARG;
     if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
         return GCP_ERR_INVALID_ARG;
+    if (mode_table(F, h->X.d, h->X.dims).off4[h->X.d] >= (int64_t(1) << 31))  // 32-bit element indices
+        return GCP_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     FoldArgs fold{};
-    st = grad_impl(h, F, loss, S, nullptr, stream_dev, G, s, &fold);
+    bool advanced = false;
+    st = grad_impl(h, F, loss, S, nullptr, stream_dev, G, s, &fold, state, &advanced);
     if (st != GCP_OK) return st;
     AdamArgs a{};
     a.mt = mode_table(F, h->X.d, h->X.dims);
@@ -989,9 +1001,13 @@ gcp_status gcp_iteration(gcp_handle* h, const gcp_factors* F, gcp_loss loss, con
     a.lower = prm->lower;
     a.eps_inside_sqrt = prm->eps_inside_sqrt;
     a.st = state;
+    a.t_advanced = advanced ? 1 : 0;
     const bool timed = h->prof_ev2 && h->prof_used2 < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev2[2 * h->prof_used2], s));
-    GCP_CUDA_TRY(launch_adam(a, elementwise_grid(a.mt), s));
+    if (advanced)
+        GCP_CUDA_TRY(launch_adam_advanced(a, h->num_sms, s));
+    else
+        GCP_CUDA_TRY(launch_adam(a, elementwise_grid(a.mt), s));
     if (timed) {
         GCP_CUDA_TRY(cudaEventRecord(h->prof_ev2[2 * h->prof_used2 + 1], s));
         h->prof_used2++;

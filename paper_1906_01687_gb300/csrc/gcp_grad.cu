@@ -4,25 +4,25 @@
 
 namespace gcpk {
 
-const void* grad_kernel_ptr_d3(int L, int NC, bool bf16, bool pf);
-const void* grad_kernel_ptr_d4(int L, int NC, bool bf16, bool pf);
-const void* grad_kernel_ptr_d8(int L, int NC, bool bf16, bool pf);
+const void* grad_kernel_ptr_d3(int L, int NC, bool bf16, int layout);
+const void* grad_kernel_ptr_d4(int L, int NC, bool bf16, int layout);
+const void* grad_kernel_ptr_d8(int L, int NC, bool bf16, int layout);
 
-static const void* grad_ptr(int D, int L, int NC, bool bf16, bool pf)
+static const void* grad_ptr(int D, int L, int NC, bool bf16, int layout)
 {
     switch (D) {
-    case 3: return grad_kernel_ptr_d3(L, NC, bf16, pf);
-    case 4: return grad_kernel_ptr_d4(L, NC, bf16, pf);
-    case 8: return grad_kernel_ptr_d8(L, NC, bf16, pf);
+    case 3: return grad_kernel_ptr_d3(L, NC, bf16, layout);
+    case 4: return grad_kernel_ptr_d4(L, NC, bf16, layout);
+    case 8: return grad_kernel_ptr_d8(L, NC, bf16, layout);
     default: return nullptr;
     }
 }
 
-bool grad_has_config(int D, int L, int NC, bool pf) { return grad_ptr(D, L, NC, false, pf) != nullptr; }
+bool grad_has_config(int D, int L, int NC, int layout) { return grad_ptr(D, L, NC, false, layout) != nullptr; }
 
-cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, bool pf, int block, size_t smem, int* blocks_per_sm)
+cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int layout, int block, size_t smem, int* blocks_per_sm)
 {
-    const void* f = grad_ptr(D, L, NC, bf16, pf);
+    const void* f = grad_ptr(D, L, NC, bf16, layout);
     if (!f) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -31,10 +31,10 @@ cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, bool pf, int block, 
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
 }
 
-cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, bool pf, int grid, int block,
+cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int layout, int grid, int block,
                         size_t smem, cudaStream_t s)
 {
-    const void* f = grad_ptr(D, L, NC, bf16, pf);
+    const void* f = grad_ptr(D, L, NC, bf16, layout);
     if (!f) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

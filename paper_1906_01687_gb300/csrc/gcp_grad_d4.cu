@@ -2,8 +2,8 @@
 #include "gcp_grad_impl.cuh"
 
 namespace gcpk {
-const void* grad_kernel_ptr_d4(int L, int NC, bool bf16, bool pf)
+const void* grad_kernel_ptr_d4(int L, int NC, bool bf16, int layout)
 {
-    return bf16 ? grad_kernel_ptr<4, true>(L, NC, pf) : grad_kernel_ptr<4, false>(L, NC, pf);
+    return bf16 ? grad_kernel_ptr<4, true>(L, NC, layout) : grad_kernel_ptr<4, false>(L, NC, layout);
 }
 }  // namespace gcpk

@@ -35,67 +35,76 @@
 
 namespace gcpk {
 
-template <int D, int L, int NC, bool BF16, bool PF>
-__global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(const GradArgs a)
+// LAYOUT 0: the group walk; 1: the prefetch layout.
+template <int D, int L, int NC, bool BF16, int LAYOUT>
+__global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_kernel(const GradArgs a)
 {
-    const bool early = a.early != 0;
-    if (!early) {
-        pdl_wait();
-        pdl_trigger();
-    }
+    constexpr bool PF = LAYOUT == 1;
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
     for (int i = threadIdx.x; i < a.smem_floats; i += blockDim.x) sG[i] = 0.0f;
-    __syncthreads();
 
     constexpr unsigned kFull = 0xFFFFFFFFu;
-    // the stream word: exact, or (early with a device stream word) predicted
-    uint64_t stream = early && a.dr.stream_dev
-                          ? static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.stream_pred))
-                          : read_stream(a.dr);
-    if (!early && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
-        *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(stream + 1);
-    bool waited = !early;
+    const bool early = a.early != 0;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int d = D <= 4 ? D : a.dr.d;
     const int ld = a.ld, rank = a.rank;
+
+    // Batches are dealt to warps interleaved across blocks (batch i of a
+    // round goes to block i % gridDim.x), so that every SM of a resident
+    // wave receives the same share even when the draws fill only part of it.
+    // A warp takes 32 draws per batch (each lane makes one descriptor, each
+    // group walks its L draws), or with group_draws 32 / L (each group makes
+    // its own draw's descriptor in all its lanes and takes it at once: more
+    // warps, shorter chains).
+    const int per_warp = a.group_draws ? 32 / L : 32;
+    const int steps = a.group_draws ? 1 : L;
+    const int sub = a.group_draws ? lane / L : lane;
+    const int64_t wb0 = (static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * per_warp;
+
+    // The first batch's descriptors: before the dependency wait when early
+    // (from the predicted stream word when it lives in device memory).
+    uint64_t stream = 0;
+    Draw<D> my;
+    if (early) {
+        stream = a.dr.stream_dev ? static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.stream_pred))
+                                 : a.dr.stream;
+        make_draw<D>(a.dr, wb0 + sub, stream, my);
+    }
+    pdl_wait();
+    pdl_trigger();
+
+    // gcp_iteration: this iteration's Adam step count, advanced here so that the
+    // Adam kernel that follows needs no grid-wide ordering of its own
+    if (a.st_advance && blockIdx.x == 0 && threadIdx.x == 0 && !a.st_advance->done) a.st_advance->t += 1;
+    if (a.dr.stream_dev) {
+        const uint64_t actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
+        if (a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
+            *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
+        if (early && actual != stream) make_draw<D>(a.dr, wb0 + sub, actual, my);  // mispredicted: redraw
+        stream = actual;
+    } else if (!early) {
+        stream = a.dr.stream;
+    }
+    if (!early) make_draw<D>(a.dr, wb0 + sub, stream, my);
+    if (a.smem_floats > 0) __syncthreads();  // the shared accumulators are zero
+    auto row4 = [&](int k, uint32_t i, int col) -> float4 {
+        return load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(i) * ld + col);
+    };
+
     // this CTA's destination of each mode (its replica slab, or G_k itself)
     float* gdst[D];
 #pragma unroll
     for (int k = 0; k < D; ++k)
         gdst[k] = k < d ? a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k] : nullptr;
 
-    // warp-uniform loop over batches of draws: 32 per warp step (each lane
-    // makes one descriptor, each group walks its L draws), or with
-    // group_draws 32 / L per step (each group makes its own draw's descriptor
-    // in all its lanes and takes it at once: more warps, shorter chains)
-    // Batches are dealt to warps interleaved across blocks (batch i of a
-    // round goes to block i % gridDim.x), so that every SM of a resident
-    // wave receives the same share even when the draws fill only part of it.
-    const int per_warp = a.group_draws ? 32 / L : 32;
-    const int steps = a.group_draws ? 1 : L;
-    const int64_t my_slot = static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    for (int64_t wb = my_slot * per_warp; wb < a.dr.n_total; wb += nwarps * per_warp) {
-        Draw<D> my;
-        make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
-        if (!waited) {
-            pdl_wait();
-            pdl_trigger();
-            waited = true;
-            if (a.dr.stream_dev) {
-                const uint64_t actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
-                if (blockIdx.x == 0 && threadIdx.x == 0)
-                    *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
-                if (actual != stream) {  // warp-uniform: every lane read the same words
-                    stream = actual;
-                    make_draw<D>(a.dr, wb + (a.group_draws ? lane / L : lane), stream, my);
-                }
-            }
-        }
+    // warp-uniform loop over this warp's batches
+    for (int64_t wb = wb0; wb < a.dr.n_total; wb += nwarps * per_warp) {
+        if (wb != wb0) make_draw<D>(a.dr, wb + sub, stream, my);
         if constexpr (PF) {
             // prefetch layout (one chunk per lane): the descriptors and row loads
             // of all L draws of the group are issued before any is consumed, so
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
                     if (k >= d) {
                         v[k] = make_float4(1.f, 1.f, 1.f, 1.f);
                     } else if (valid && col < rank) {
-                        v[k] = load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col);
+                        v[k] = row4(k, ix[k], col);
                     } else {
                         v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
@@ -231,8 +240,7 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
                         if (kKeep) rc[k] = r[k];
-                        else rc[k] = k < d ? load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col)
-                                           : make_float4(1.f, 1.f, 1.f, 1.f);
+                        else rc[k] = k < d ? row4(k, ix[k], col) : make_float4(1.f, 1.f, 1.f, 1.f);
                     }
                     // prefix and suffix products
                     float4 pre[D], suf[D];
@@ -263,7 +271,6 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
     }
 
     if (a.smem_mask == 0) return;
-    if (!waited) pdl_wait();  // a warp with no draws still waits before the block's flush
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < d; ++k) {
@@ -283,17 +290,18 @@ __global__ void __launch_bounds__(256, (D <= 4 && !PF ? 3 : 2)) grad_kernel(cons
 
 // The prefetch layout exists for one chunk per lane with 2 or 4 lanes (3 or 4 modes).
 template <int D, bool BF16>
-const void* grad_kernel_ptr(int L, int NC, bool pf)
+const void* grad_kernel_ptr(int L, int NC, int layout)
 {
-    if (pf) {
+    if (layout == 1) {
         if constexpr (D <= 4) {
-            if (NC == 1 && L == 2) return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, true>);
-            if (NC == 1 && L == 4) return reinterpret_cast<const void*>(&grad_kernel<D, 4, 1, BF16, true>);
+            if (NC == 1 && L == 2) return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, 1>);
+            if (NC == 1 && L == 4) return reinterpret_cast<const void*>(&grad_kernel<D, 4, 1, BF16, 1>);
         }
         return nullptr;
     }
+    if (layout != 0) return nullptr;
 #define GCP_CASE(LL, CC) \
-    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, false>);
+    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, 0>);
     GCP_GRAD_CONFIGS(GCP_CASE)
 #undef GCP_CASE
     return nullptr;

@@ -59,6 +59,7 @@ struct GradArgs {
     int32_t group_draws;           // 1: each group of L lanes takes its own draw (32/L draws per warp step)
     int32_t early;                 // 1: each warp's first descriptors are made before the dependency wait
     int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
+    gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
 };
 
 // Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).
@@ -104,6 +105,9 @@ struct AdamArgs {
     uint32_t reps[GCP_MAX_MODES];
     uint64_t rep_stride4[GCP_MAX_MODES];
     float* R[GCP_MAX_MODES];
+    // 1 (gcp_iteration): the gradient kernel of the same iteration has already
+    // advanced st->t, so no block of this launch has to wait for the others
+    int32_t t_advanced;
 };
 
 struct EpochArgs {
@@ -174,10 +178,11 @@ inline cudaError_t launch_pdl_ptr(const void* kernel, dim3 grid, dim3 block, siz
 }
 
 // Launchers (defined in the kernel translation units).
-cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, bool pf, int grid, int block,
+// layout: 0 the group walk, 1 the prefetch layout
+cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int layout, int grid, int block,
                         size_t smem, cudaStream_t s);
-cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, bool pf, int block, size_t smem, int* blocks_per_sm);
-bool grad_has_config(int D, int L, int NC, bool pf);
+cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int layout, int block, size_t smem, int* blocks_per_sm);
+bool grad_has_config(int D, int L, int NC, int layout);
 
 cudaError_t launch_fold(const FoldArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_loss(const LossArgs& a, bool bf16, int grid, int block, cudaStream_t s);
@@ -189,6 +194,7 @@ cudaError_t launch_hash_build(const int4* recs, int rec_int4, int d, const uint6
                               cudaStream_t s);
 cudaError_t launch_pack_records(const gcp_tensor& X, int4* recs, int rec_int4, cudaStream_t s);
 cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adam_advanced(const AdamArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_epoch(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_state_init(gcp_adam_state* st, float alpha, cudaStream_t s);
 cudaError_t launch_to_bf16(const ModeTable& mt, int grid, cudaStream_t s);

@@ -122,3 +122,4 @@ def test_iterations_with_early_draws_follow_waiting_run(sampler):
     a1, s1 = out[1]
     assert s0["iter"] == s1["iter"] == 30 and s0["t"] == s1["t"] == 30
     assert np.linalg.norm(a1 - a0) <= 1e-5 * np.linalg.norm(a0)
+
