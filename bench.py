@@ -54,8 +54,10 @@ def kernel_source_hash():
 
 def recorded_traffic(launch):
     """DRAM bytes per launch of grad_kernel from the committed ncu summary, if
-    the kernel sources and the launch shape are those the counters were taken
-    with; otherwise None."""
+    the kernel sources and the kernel instance (lanes x chunks, draw layout,
+    early draws) are those the counters were taken with; otherwise None.
+    The block size is not compared: it changes neither the kernel's code nor
+    its DRAM traffic, which is the random gathers of X."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
@@ -63,8 +65,8 @@ def recorded_traffic(launch):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
-    shape = {k: launch.get(k) for k in ("lanes", "chunks", "block", "group_draws", "prefetch")}
-    if rec.get("launch_shape") != shape:
+    keys = ("lanes", "chunks", "group_draws", "prefetch", "early_draws")
+    if any(rec.get("launch_shape", {}).get(k) != launch.get(k) for k in keys):
         return None
     return rec.get("dram_bytes_per_launch")
 

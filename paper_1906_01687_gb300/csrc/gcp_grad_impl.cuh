@@ -81,12 +81,19 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     // gcp_iteration: this iteration's Adam step count, advanced here so that the
     // Adam kernel that follows needs no grid-wide ordering of its own
     if (a.st_advance && blockIdx.x == 0 && threadIdx.x == 0 && !a.st_advance->done) a.st_advance->t += 1;
+    // The true stream word.  With early draws in the group walk, its check
+    // against the prediction is deferred to just before the first update of
+    // the first batch, so that the load overlaps that batch's row gathers.
+    uint64_t actual = stream;
+    bool verify = false;
     if (a.dr.stream_dev) {
-        const uint64_t actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
-        if (a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
-            *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
-        if (early && actual != stream) make_draw<D>(a.dr, wb0 + sub, actual, my);  // mispredicted: redraw
-        stream = actual;
+        actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
+        if (early && !PF) {
+            verify = true;
+        } else {
+            if (early && actual != stream) make_draw<D>(a.dr, wb0 + sub, actual, my);  // mispredicted: redraw
+            stream = actual;
+        }
     } else if (!early) {
         stream = a.dr.stream;
     }
@@ -213,6 +220,15 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
             }
 #pragma unroll
             for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+            if (verify) {  // warp-uniform; first batch only
+                verify = false;
+                if (actual != stream) {  // mispredicted: redraw the batch and start it again
+                    stream = actual;
+                    make_draw<D>(a.dr, wb + sub, stream, my);
+                    b = -1;
+                    continue;
+                }
+            }
             if (!valid) continue;  // no shuffles below this point
             const float y = entry_y(a.loss, cls, x, part, w);
 
@@ -270,6 +286,9 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
         }
     }
 
+    // the prediction for the next launch that reads its stream word from memory
+    if (a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
+        *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
     if (a.smem_mask == 0) return;
     __syncthreads();
 #pragma unroll 1
