@@ -257,6 +257,11 @@ def ours_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
+    # the end-to-end section's copy stream, taken now: torch hands out streams
+    # round-robin from a small pool, and one taken after the autotuner's
+    # captures can be the compute stream itself
+    copy_stream = torch.cuda.Stream(device=dev)
+    assert copy_stream.cuda_stream != stream.cuda_stream
 
     X32, _ = synth.dense_100_4()
     init_seed, seed = replica_seeds(rank)
@@ -316,7 +321,6 @@ def ours_arm(args):
     handles.append(h2)
     graphs.append(run.graph)
     run.h, run.graph = handles[0], graphs[0]
-    copy_stream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     step_done = [torch.cuda.Event(), torch.cuda.Event()]
     factors_in = torch.cuda.Event()

@@ -117,7 +117,8 @@ class GcpAdam:
         self._warm()
         self.stream.synchronize()
         g = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream(device=self.stream.device)
+        from .autotune import side_stream
+        cap = side_stream(self.stream)
         with torch.cuda.graph(g, stream=cap):
             saved, self.stream = self.stream, torch.cuda.current_stream()
             try:

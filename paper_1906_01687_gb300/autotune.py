@@ -49,14 +49,24 @@ def candidates(rank: int) -> list:
     return out
 
 
-def time_graph(call, spec, launches, stream) -> float:
+def side_stream(stream):
+    """A stream other than `stream` (torch hands streams out round-robin from
+    a small pool, so a new one can be `stream` itself)."""
+    for _ in range(64):
+        s = torch.cuda.Stream(device=stream.device)
+        if s.cuda_stream != stream.cuda_stream:
+            return s
+    raise RuntimeError("no CUDA stream other than the working stream")
+
+
+def time_graph(call, spec, launches, stream, cap=None) -> float:
     """Device time (s) per call of `launches` back-to-back calls captured in a
     CUDA graph: the calls overlap as they do in a captured epoch."""
     with torch.cuda.stream(stream):
         call(spec, stream)  # allocate any workspace outside the capture
     stream.synchronize()
     g = torch.cuda.CUDAGraph()
-    cap = torch.cuda.Stream(device=stream.device)
+    cap = cap if cap is not None else side_stream(stream)
     with torch.cuda.graph(g, stream=cap):
         for i in range(launches):
             s = gcp.Sampling(spec.kind, spec.p, spec.q, spec.seed, (1 << 62) + i, spec.problem, spec.oversample)
@@ -72,7 +82,7 @@ def time_graph(call, spec, launches, stream) -> float:
     return a.elapsed_time(b) * 1e-3 / (3 * launches)
 
 
-def time_grad(h, F, loss, spec, launches=20, stream=None, call=None, graph=False) -> float:
+def time_grad(h, F, loss, spec, launches=20, stream=None, call=None, graph=False, cap=None) -> float:
     """Median device time (s) of one gcp_grad call (or of call(spec, stream))
     for the current tuning; with graph, the time per call of a captured
     sequence of calls."""
@@ -83,7 +93,7 @@ def time_grad(h, F, loss, spec, launches=20, stream=None, call=None, graph=False
         def call(s, st):
             gcp.gcp_grad(h, F, loss, G, S=s, stream=st)
     if graph:
-        return time_graph(call, spec, launches, stream)
+        return time_graph(call, spec, launches, stream, cap)
     with torch.cuda.stream(stream):
         call(spec, stream)  # allocate any workspace outside the timing
         stream.synchronize()
@@ -105,12 +115,14 @@ def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launche
     sets the fastest on the handle, returns it with its time."""
     best, best_t = None, float("inf")
     results = []
+    stream = stream or torch.cuda.current_stream()
+    cap = side_stream(stream) if graph else None
     for cfg in configs if configs is not None else candidates(F.rank):
         try:
             gcp.gcp_set_tuning(h, **cfg)
         except gcp.GcpError:
             continue
-        t = time_grad(h, F, loss, spec, launches, stream, call, graph)
+        t = time_grad(h, F, loss, spec, launches, stream, call, graph, cap)
         results.append((t, cfg))
         if log:
             log(dict(seconds=t, **cfg))

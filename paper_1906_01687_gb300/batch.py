@@ -69,7 +69,8 @@ class GcpAdamBatch:
     def capture(self):
         self.stream.synchronize()
         g = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream(device=self.stream.device)
+        from .autotune import side_stream
+        cap = side_stream(self.stream)
         with torch.cuda.graph(g, stream=cap):
             saved, self.stream = self.stream, torch.cuda.current_stream()
             try:
