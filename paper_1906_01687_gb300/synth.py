@@ -311,12 +311,10 @@ def gamma_problem(dims=(200, 150, 100, 50), rank=5, seed=1912):
     return X.astype(np.float32), factors
 
 
-def binary_odds_problem(dims=(200, 150, 100, 50), rank=5, delta=0.15, p_high=0.9, p_low=0.0025, seed=1913):
-    """App. D: factors 1..r-1 sparse (density delta, nonzero entries
-    N(root_d(p_high / (1 - p_high)), 0.5^2)), factor r dense with entries
-    root_d(p_low / (1 - p_low)); x_i ~ Bernoulli(m_i / (1 + m_i)) with m the
-    odds.  Dense generation (for moderate sizes).  Returns (X float32, factors)."""
-    rng = np.random.default_rng(seed)
+def app_d_factors(rng, dims, rank, delta=0.15, p_high=0.9, p_low=0.0025):
+    """App. D's planted odds model: components 1..r-1 sparse (density delta,
+    nonzero entries |N(root_d(p_high / (1 - p_high)), 0.5^2)|), component r
+    dense with entries root_d(p_low / (1 - p_low))."""
     d = len(dims)
     hi = (p_high / (1 - p_high)) ** (1.0 / d)
     lo = (p_low / (1 - p_low)) ** (1.0 / d)
@@ -327,6 +325,50 @@ def binary_odds_problem(dims=(200, 150, 100, 50), rank=5, delta=0.15, p_high=0.9
         a[:, : rank - 1] = np.where(mask, np.abs(rng.normal(hi, 0.5, (n, rank - 1))), 0.0)
         a[:, rank - 1] = lo
         factors.append(a)
+    return factors
+
+
+def binary_odds_problem(dims=(200, 150, 100, 50), rank=5, delta=0.15, p_high=0.9, p_low=0.0025, seed=1913):
+    """App. D: x_i ~ Bernoulli(m_i / (1 + m_i)) with m the odds of the planted
+    model of app_d_factors.  Dense generation on the host (moderate sizes).
+    Returns (X float32, factors)."""
+    rng = np.random.default_rng(seed)
+    factors = app_d_factors(rng, dims, rank, delta, p_high, p_low)
     M = dense_from_factors(factors)
     X = (rng.random(M.shape) < M / (1.0 + M)).astype(np.float32)
     return X, factors
+
+
+def binary_odds_coo(dims=(400, 300, 200, 100), rank=5, delta=0.15, p_high=0.9, p_low=0.0025, seed=1913,
+                    device="cuda", slab=8):
+    """App. D at the size of the paper's sampler comparison (Section 5.2:
+    400 x 300 x 200 x 100, rank 5, about 0.38% nonzeros), generated on the
+    device a few mode-1 slices at a time (torch's seeded generator draws the
+    Bernoulli variables).  Returns (COO indices as one int32 tensor per mode,
+    sorted row-major, and the factors)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    factors = app_d_factors(rng, dims, rank, delta, p_high, p_low)
+    A = [torch.as_tensor(a, device=device, dtype=torch.float64) for a in factors]
+    rest = A[1]
+    for a in A[2:]:  # Khatri-Rao-like outer product of modes 2..d, kept per component
+        rest = (rest.unsqueeze(-2) * a.reshape((1,) * (rest.dim() - 1) + a.shape)).reshape(-1, rank)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    parts = []
+    for i0 in range(0, dims[0], slab):
+        i1 = min(dims[0], i0 + slab)
+        M = A[0][i0:i1] @ rest.T  # (slab, prod(dims[1:])) odds
+        u = torch.rand(M.shape, generator=gen, device=device, dtype=torch.float64)
+        nz = torch.nonzero(u < M / (1.0 + M))
+        nz[:, 0] += i0
+        parts.append(nz)
+    nz = torch.cat(parts)
+    idx = [nz[:, 0].to(torch.int32)]
+    rem = nz[:, 1]
+    tail = []
+    for n in reversed(dims[1:]):
+        tail.append((rem % n).to(torch.int32))
+        rem = rem // n
+    idx += list(reversed(tail))
+    return idx, factors

@@ -1,4 +1,5 @@
 """Checks of the seeded input generators (they feed both the CUDA path and the oracle)."""
+import pytest
 import numpy as np
 
 from paper_1906_01687_gb300 import synth
@@ -41,3 +42,23 @@ def test_app_c_and_d_generators():
     assert (X >= 0).all() and X.shape == (10, 8, 6)
     X, f = synth.binary_odds_problem(dims=(20, 15, 10, 5), rank=4, seed=5)
     assert set(np.unique(X)) <= {0.0, 1.0} and 0 < X.mean() < 0.5
+
+
+def test_binary_odds_coo_draws_app_d_model():
+    """The device generator of App. D's sparse binary tensor: indices valid,
+    unique and row-major sorted; the number of ones matches the model's
+    expected count sum_i m_i / (1 + m_i) within 5 binomial sigma."""
+    torch = pytest.importorskip("torch")
+    dims = (40, 30, 20, 10)
+    idx, factors = synth.binary_odds_coo(dims, rank=5, seed=4, device="cpu", slab=7)
+    assert all(i.dtype == torch.int32 for i in idx)
+    for i, n in zip(idx, dims):
+        assert int(i.min()) >= 0 and int(i.max()) < n
+    lin = idx[0].long()
+    for i, n in zip(idx[1:], dims[1:]):
+        lin = lin * n + i.long()
+    assert bool((lin[1:] > lin[:-1]).all())
+    M = synth.dense_from_factors(factors)
+    p = M / (1.0 + M)
+    mean, sd = p.sum(), np.sqrt((p * (1 - p)).sum())
+    assert abs(idx[0].numel() - mean) < 5 * sd
