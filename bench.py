@@ -386,6 +386,8 @@ def ours_arm(args):
             "final_state": {k: st[k] for k in ("F", "t", "iter", "alpha", "bad")}}
     clocks = clk.summary()
     line["clocks"] = clocks
+    if not args.no_sweep:
+        line["sweep"] = sweep_draws(torch, gcp, run, stream, peak)
     if not args.no_forms:
         line["forms"] = {"bf16": forms_bf16(torch, gcp, synth, stream),
                          "batched": forms_batched(torch, gcp, synth, stream)}
@@ -413,6 +415,49 @@ def _time_calls(torch, fn, stream, reps):
             b.record(stream)
     stream.synchronize()
     return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
+
+
+def sweep_draws(torch, gcp, run, stream, peak, sizes=(100_000, 1_000_000, 10_000_000)):
+    """Whole GCP-Adam iterations (gradient + Adam) on the benchmark tensor at
+    larger draw counts per iteration, each size captured as a CUDA graph of
+    back-to-back iterations on throwaway copies of the factors: the
+    bandwidth-bound reading of the same kernels."""
+    out = []
+    with torch.cuda.stream(stream):
+        F = gcp.Factors([a[:, :RANK] for a in run.F.A])
+        G, B, C = F.like(), F.like(), F.like()
+        st = gcp.new_state()
+        gcp.gcp_state_init(st, 1e-4, stream=stream)
+    from paper_1906_01687_gb300.autotune import side_stream
+    cap = side_stream(stream)
+    for s in sizes:
+        spec = gcp.Sampling(gcp.SAMPLER_UNIFORM, 0, s, 99, 0)
+        iters = max(3, min(50, 5_000_000 // s))
+
+        def one(strm):
+            gcp.gcp_iteration(run.h, F, gcp.LOSS_GAUSSIAN, spec, G, B, C, st, stream_dev=st[3:4], stream=strm)
+        with torch.cuda.stream(stream):
+            one(stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(iters):
+                one(cap)
+        with torch.cuda.stream(stream):
+            g.replay()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                g.replay()
+            b.record(stream)
+        stream.synchronize()
+        us = a.elapsed_time(b) * 1e3 / (3 * iters)
+        gbs = BYTES_PER_DRAW * s / us / 1e3
+        out.append({"draws_per_iteration": s, "us_per_iteration": us, "entries_per_s": s / us * 1e6,
+                    "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peak})
+        del g
+    return {"what": "whole iterations (gradient + Adam), CUDA graph, dense 100^4 rank 10, Gaussian, uniform",
+            "points": out}
 
 
 def forms_bf16(torch, gcp, synth, stream):
@@ -527,6 +572,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form comparisons")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the draws-per-iteration sweep")
     ap.add_argument("--tuning", default=None, help="JSON gcp_tuning fields to use instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
