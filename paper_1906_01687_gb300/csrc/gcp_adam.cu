@@ -168,14 +168,6 @@ constexpr int kParts = 4;
 
 __global__ void __launch_bounds__(64) adam_split_kernel(const AdamArgs a)
 {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t t0 = a.st->t;
-    const float alpha = a.st->alpha;
-    const int done = a.st->done;
-    const float n = static_cast<float>(t0);  // already advanced for this step
-    const float ic1 = 1.0f / -expm1f(n * log1pf(a.beta1 - 1.0f));
-    const float ic2 = 1.0f / -expm1f(n * log1pf(a.beta2 - 1.0f));
     const ModeTable& mt = a.mt;
     const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
     const uint32_t ld4 = static_cast<uint32_t>(mt.ld) / 4;
@@ -185,21 +177,42 @@ __global__ void __launch_bounds__(64) adam_split_kernel(const AdamArgs a)
     // warp-uniform trip count: every lane of a warp takes part in the shuffles
     const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) / kParts;
     const uint32_t warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / kParts;
+
+    // An element's mode, addresses and A, B, C.  A, B, C were last written by
+    // the previous iteration's Adam step (or earlier), which had completed
+    // before this iteration's gradient kernel passed its wait, so the first
+    // element is prepared before this kernel's wait, together with the
+    // kernel-parameter reads; G and the replicas come from the gradient kernel
+    // and are read after it.
+    int k = 0;
+    uint32_t loc = 0;
+    float4 A4 = make_float4(0.f, 0.f, 0.f, 0.f), B4 = A4, C4 = A4;
+    auto prepare = [&](uint32_t i4) {
+        if (i4 >= total4) return;
+        k = mode_of(mt, i4);
+        loc = i4 - static_cast<uint32_t>(mt.off4[k]);
+        if (part == 0) {
+            A4 = reinterpret_cast<const float4*>(mt.A[k])[loc];
+            B4 = reinterpret_cast<const float4*>(mt.B[k])[loc];
+            C4 = reinterpret_cast<const float4*>(mt.C[k])[loc];
+        }
+    };
+    prepare(first);
+    const float alpha = a.st->alpha;  // written by epoch kernels only
+    const int done = a.st->done;
+    pdl_wait();
+    pdl_trigger();
+    const int64_t t0 = a.st->t;  // advanced by this iteration's gradient kernel
+    const float n = static_cast<float>(t0);
+    const float ic1 = 1.0f / -expm1f(n * log1pf(a.beta1 - 1.0f));
+    const float ic2 = 1.0f / -expm1f(n * log1pf(a.beta2 - 1.0f));
     for (uint32_t w4 = warp_first, i4 = first; w4 < total4; w4 += stride, i4 += stride) {
+        if (i4 != first) prepare(i4);
         const bool live_elem = i4 < total4;
-        int k = 0;
-        uint32_t loc = 0;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 g = acc, A4 = acc, B4 = acc, C4 = acc;
+        float4 g = acc;
         if (live_elem) {
-            k = mode_of(mt, i4);
-            loc = i4 - static_cast<uint32_t>(mt.off4[k]);
-            if (part == 0) {
-                g = reinterpret_cast<const float4*>(mt.G[k])[loc];
-                A4 = reinterpret_cast<const float4*>(mt.A[k])[loc];
-                B4 = reinterpret_cast<const float4*>(mt.B[k])[loc];
-                C4 = reinterpret_cast<const float4*>(mt.C[k])[loc];
-            }
+            if (part == 0) g = reinterpret_cast<const float4*>(mt.G[k])[loc];
             const uint32_t reps = a.reps[k] > 1 ? a.reps[k] : 0;
             float4* r = reinterpret_cast<float4*>(a.R[k]) + loc;
             const uint64_t rs = a.rep_stride4[k];

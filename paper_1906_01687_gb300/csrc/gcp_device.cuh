@@ -212,9 +212,10 @@ __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.w
 // pdl_trigger() lets the successor begin launching.  Every kernel of the path
 // calls pdl_wait() before pdl_trigger(), so when a kernel starts, the kernel
 // two launches before it has completed.  Every kernel calls pdl_wait() before
-// its first global-memory access, with one exception: the gradient kernel's
-// early descriptors read the data tensor and the handle's nonzero tables
-// (written, if ever, at least two launches back) before waiting.
+// its first global-memory access, with two exceptions, both reading only
+// data written at least two launches back: the gradient kernel's early
+// descriptors (the data tensor, the handle's nonzero tables) and the fused
+// Adam step's first element (A, B, C, alpha and the done flag).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
