@@ -465,7 +465,7 @@ def forms_bf16(torch, gcp, synth, stream):
     nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): gradient
     throughput and error against the FP64 oracle on the same draws."""
     import oracle
-    from paper_1906_01687_gb300.autotune import autotune
+    from paper_1906_01687_gb300.autotune import autotune, candidates
     dims = (6186, 24, 77, 32)
     idx, vals, _ = synth.count_tensor()
     h = gcp.Handle(gcp.DataTensor.coo(dims, idx, vals))
@@ -478,7 +478,8 @@ def forms_bf16(torch, gcp, synth, stream):
            "metric": "entries/s of gcp_grad (zero pass + gradient)"}
     for name, bf16 in (("fp32", False), ("bf16", True)):
         F = gcp.Factors(A, bf16=bf16)
-        autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream)
+        autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream,
+                 configs=[dict(c, early_draws=1) for c in candidates(10)])
         G = F.like()
         t = _time_calls(torch, lambda: gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream), stream, 50)
         for x in G:
@@ -574,12 +575,25 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form comparisons")
     ap.add_argument("--no-sweep", action="store_true", help="skip the draws-per-iteration sweep")
     ap.add_argument("--tuning", default=None, help="JSON gcp_tuning fields to use instead of autotuning")
+    ap.add_argument("--only-forms", action="store_true",
+                    help="run only the BF16 and batched form comparisons (one JSON object; for profiling them)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only_forms:
+        return forms_only()
     return ours_arm(args)
+
+
+def forms_only():
+    import torch
+    from paper_1906_01687_gb300 import gcp, synth
+    stream = torch.cuda.Stream()
+    print(json.dumps({"forms": {"bf16": forms_bf16(torch, gcp, synth, stream),
+                                "batched": forms_batched(torch, gcp, synth, stream)}}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

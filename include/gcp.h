@@ -460,11 +460,12 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    issues the row loads of all its draws before consuming any (one round
    trip to L2 per group walk instead of one per draw; more registers).
    early_draws = 1: where the draws read nothing but the data tensor (uniform
-   sampling, semi-stratified sampling, or uniform over a sparse tensor whose
-   nonzero table was built by an earlier call), the kernel makes each warp's
-   first batch of draws (Philox, value gather) before it waits for the
-   kernel launched just before it on the stream (programmatic dependent
-   launch), so that work overlaps the previous kernel's tail.  Contract: the
+   sampling, semi-stratified sampling, the nonzero draws of stratified
+   sampling, or uniform over a sparse tensor whose nonzero table was built by
+   an earlier call), the kernel makes each warp's first batch of draws
+   (Philox, value gather) before it waits for the kernel launched just
+   before it on the stream (programmatic dependent launch), so that work
+   overlaps the previous kernel's tail.  Contract: the
    data tensor's values and weights are not written by the kernel launched
    immediately before the call (copies and anything further back are
    ordered as usual).  With stream_dev, the kernel starts from a prediction

@@ -743,9 +743,10 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     GradArgs a{};
     a.dr = make_draw_args(h, S, list, stream_dev);
     // early descriptors only for draws that read nothing but the data tensor and
-    // tables built before this call (not a list, not a stratified zero list)
+    // tables built before this call (not a list; with stratified sampling the
+    // kernel keeps them to warps whose first batch holds nonzero draws only)
     const bool early_ok = a.dr.src == kSrcUniformDense || (a.dr.src == kSrcUniformSparse && table_ready) ||
-                          (a.dr.src == kSrcSparse && a.dr.semi);
+                          a.dr.src == kSrcSparse;
     if (a.dr.n_total == 0) return GCP_OK;
     if (S && S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
         st = ensure_zero_list(h, S->q);

@@ -46,7 +46,6 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     for (int i = threadIdx.x; i < a.smem_floats; i += blockDim.x) sG[i] = 0.0f;
 
     constexpr unsigned kFull = 0xFFFFFFFFu;
-    const bool early = a.early != 0;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
@@ -65,6 +64,12 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     const int steps = a.group_draws ? 1 : L;
     const int sub = a.group_draws ? lane / L : lane;
     const int64_t wb0 = (static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * per_warp;
+    // early descriptors for this warp: every draw of its first batch reads only
+    // data written before the preceding kernel (with stratified sampling, the
+    // nonzero draws j < p; the zeros come from the zero pass just before)
+    // (a warp vote, so that the condition is warp-uniform by construction)
+    const bool early =
+        a.early != 0 && __all_sync(0xFFFFFFFFu, a.dr.src != kSrcSparse || a.dr.semi || wb0 + per_warp <= a.dr.p);
 
     // The first batch's descriptors: before the dependency wait when early
     // (from the predicted stream word when it lives in device memory).

@@ -175,7 +175,7 @@ cudaError_t launch_materialise(const DrawArgs& dr, int32_t* const idx[GCP_MAX_MO
 //   scatter -- each tile writes its accepted candidates' slots below q.
 // ---------------------------------------------------------------------------
 constexpr int kZeroTile = 1024;
-constexpr int kZeroBlock = 256;
+constexpr int kZeroBlock = 1024;  // one candidate per thread: every hash probe of a tile in flight at once
 
 template <int D>
 __device__ __forceinline__ bool zero_candidate(const ZeroArgs& a, uint64_t stream, int64_t c, uint32_t (&ix)[D])

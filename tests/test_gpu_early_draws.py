@@ -89,11 +89,12 @@ def test_device_stream_word_prediction_hits_and_misses():
                               oracle.grad(dims, f64(A), 0, SO), oracle.grad_abs(dims, f64(A), 0, SO))
 
 
-@pytest.mark.parametrize("sampler", ["uniform", "semi_stratified"])
+@pytest.mark.parametrize("sampler", ["uniform", "semi_stratified", "stratified"])
 def test_iterations_with_early_draws_follow_waiting_run(sampler):
     """Thirty GCP-Adam iterations drawing from the device iteration counter:
-    early and waiting kernels take the same draws, so the factors agree to
-    FP32 summation-order noise and the counters match."""
+    early and waiting kernels take the same draws (with stratified sampling
+    only the warps whose first batch is all nonzero draws start early), so
+    the factors agree to FP32 summation-order noise and the counters match."""
     g = gcp()
     dims, rank = (40, 35, 30), 6
     if sampler == "uniform":
@@ -103,7 +104,7 @@ def test_iterations_with_early_draws_follow_waiting_run(sampler):
     else:
         idx, vals = sparse_random(dims, 4000, 9)
         T = g.DataTensor.coo(dims, idx, vals)
-        S = g.Sampling(g.SAMPLER_SEMI_STRATIFIED, 6000, 6000, seed=3)
+        S = g.Sampling(g.SAMPLERS[sampler], 6000, 6000, seed=3)
     A0 = rng_factors(dims, rank, 10, scale=0.5)
     out = {}
     for early in (0, 1):
