@@ -388,6 +388,8 @@ def ours_arm(args):
     line["clocks"] = clocks
     if not args.no_sweep:
         line["sweep"] = sweep_draws(torch, gcp, run, stream, peak)
+    if not args.no_large:
+        line["large_sparse"] = large_sparse(torch, gcp, synth, stream, peak)
     if not args.no_forms:
         line["forms"] = {"bf16": forms_bf16(torch, gcp, synth, stream),
                          "batched": forms_batched(torch, gcp, synth, stream)}
@@ -458,6 +460,64 @@ def sweep_draws(torch, gcp, run, stream, peak, sizes=(100_000, 1_000_000, 10_000
         del g
     return {"what": "whole iterations (gradient + Adam), CUDA graph, dense 100^4 rank 10, Gaussian, uniform",
             "points": out}
+
+
+def large_sparse(torch, gcp, synth, stream, peak, iters=10):
+    """The largest sparse workload: the 1e5 x 1e5 x 1e4 binary tensor with 1e8
+    nonzeros, rank 32, Bernoulli-logit, semi-stratified 1e6 + 1e6 draws per
+    iteration, whole GCP-Adam iterations (gradient + Adam over all 2.1e5 x 32
+    factor entries) captured in a CUDA graph; FP32 and BF16 factor storage.
+    Algorithmic bytes per iteration: nonzero draws 16 B (packed record) +
+    d r b_f B rows + d r 4 B updates (784 B in FP32, 592 B with BF16 rows),
+    "zero" draws the same without the record (no value read), plus the Adam
+    pass (32 B per factor entry, + 2 B for the BF16 copy)."""
+    t0 = time.time()
+    dims, rank, p, q = (100_000, 100_000, 10_000), 32, 1_000_000, 1_000_000
+    idx, _, _ = synth.binary_tensor(device=stream.device)
+    h = gcp.Handle(gcp.DataTensor.coo(dims, idx, None, device=stream.device), stream=stream)
+    gen_s = time.time() - t0
+    A = [(a / math.sqrt(rank) ** (1 / 3)).astype(np.float32) for a in synth.initial_guess(dims, rank, 5)]
+    entries = sum(dims) * rank
+    out = {"workload": "coo-1e5x1e5x1e4-nnz1e8-r32-bernoullilogit-semistratified-1e6+1e6",
+           "what": "whole iterations (gradient + Adam), CUDA graph", "generation_s": gen_s}
+    from paper_1906_01687_gb300.autotune import side_stream
+    cap = side_stream(stream)
+    for name, bf16 in (("fp32", False), ("bf16", True)):
+        b_f = 2 if bf16 else 4
+        grad_bytes = p * (16 + len(dims) * rank * (b_f + 4)) + q * (len(dims) * rank * (b_f + 4))
+        adam_bytes = entries * (32 + (2 if bf16 else 0))
+        with torch.cuda.stream(stream):
+            F = gcp.Factors(A, bf16=bf16)
+            G, B, C = F.like(), F.like(), F.like()
+            st = gcp.new_state()
+            gcp.gcp_state_init(st, 1e-4, stream=stream)
+        spec = gcp.Sampling(gcp.SAMPLER_SEMI_STRATIFIED, p, q, 1687, 0)
+        gcp.gcp_set_tuning(h, early_draws=1)
+
+        def one(strm):
+            gcp.gcp_iteration(h, F, gcp.LOSS_BERNOULLI_LOGIT, spec, G, B, C, st, stream_dev=st[3:4], stream=strm)
+        with torch.cuda.stream(stream):
+            one(stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(iters):
+                one(cap)
+        with torch.cuda.stream(stream):
+            g.replay()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                g.replay()
+            b.record(stream)
+        stream.synchronize()
+        us = a.elapsed_time(b) * 1e3 / (3 * iters)
+        gbs = (grad_bytes + adam_bytes) / us / 1e3
+        out[name] = {"us_per_iteration": us, "entries_per_s": (p + q) / us * 1e6,
+                     "algorithmic_bytes_per_iteration": grad_bytes + adam_bytes, "algorithmic_gbs": gbs,
+                     "frac_of_measured_hbm": gbs / peak}
+        del g
+    return out
 
 
 def forms_bf16(torch, gcp, synth, stream):
@@ -574,6 +634,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form comparisons")
     ap.add_argument("--no-sweep", action="store_true", help="skip the draws-per-iteration sweep")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1e8-nonzero sparse workload")
     ap.add_argument("--tuning", default=None, help="JSON gcp_tuning fields to use instead of autotuning")
     ap.add_argument("--only-forms", action="store_true",
                     help="run only the BF16 and batched form comparisons (one JSON object; for profiling them)")
