@@ -344,3 +344,17 @@ def test_checkpoint_resume_reproduces_run(tmp_path):
     assert num <= 1e-4 * math.sqrt(sum(np.linalg.norm(y) ** 2 for y in a))
     s1, s2 = straight.status(), resumed.status()
     assert (s1["t"], s1["iter"], s1["bad"]) == (s2["t"], s2["iter"], s2["bad"])
+
+
+def test_readme_example_runs():
+    """The README's fitting example, as written, runs and lowers the estimated loss."""
+    from paper_1906_01687_gb300 import gcp as G, synth
+    from paper_1906_01687_gb300.adam import GcpAdam
+    X = synth.dense_small()[0]
+    A0 = synth.initial_guess(X.shape, 3, seed=1, target_norm=float(np.linalg.norm(X)))
+    run = GcpAdam(G.DataTensor.dense(X), A0, G.LOSS_GAUSSIAN, G.SAMPLER_UNIFORM, p=0, q=1000,
+                  est_p=0, est_q=500, seed=1, est_seed=2, tau=100)
+    state = run.fit(max_epochs=50)
+    A = run.factors()
+    assert len(A) == 3 and all(a.shape == (n, 3) for a, n in zip(A, X.shape))
+    assert state["status"] == 0 and math.isfinite(state["F"]) and state["F"] < run.history[0]
