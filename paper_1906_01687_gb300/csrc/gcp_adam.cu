@@ -9,29 +9,11 @@
 
 #include <algorithm>
 
+#include "gcp_adam_phase.cuh"
 #include "gcp_device.cuh"
 #include "gcp_kernels.cuh"
 
 namespace gcpk {
-
-__device__ __forceinline__ int mode_of(const ModeTable& mt, int64_t i4)
-{
-    int k = 0;
-#pragma unroll
-    for (int l = 1; l < GCP_MAX_MODES; ++l)
-        if (l < mt.d && i4 >= mt.off4[l]) k = l;
-    return k;
-}
-
-__device__ __forceinline__ void store_bf16x4(uint16_t* dst, float4 v)
-{
-    const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y);
-    const __nv_bfloat16 b2 = __float2bfloat16_rn(v.z), b3 = __float2bfloat16_rn(v.w);
-    uint2 packed;
-    packed.x = static_cast<uint32_t>(__bfloat16_as_ushort(b0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b1)) << 16);
-    packed.y = static_cast<uint32_t>(__bfloat16_as_ushort(b2)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b3)) << 16);
-    *reinterpret_cast<uint2*>(dst) = packed;
-}
 
 // Completion ticket: returns true in exactly one thread of the last block.
 __device__ __forceinline__ bool last_block_done(unsigned int* ticket)
@@ -44,23 +26,6 @@ __device__ __forceinline__ bool last_block_done(unsigned int* ticket)
     }
     __syncthreads();
     return is_last && threadIdx.x == 0;
-}
-
-// One entry of the Adam step with the bias corrections given as reciprocals
-// (ic1 = 1 / (1 - beta1^n), ic2 = 1 / (1 - beta2^n)).  The step bh / den is
-// taken with the hardware reciprocal square root (eps inside the root) or
-// the fast division (eps outside): a few FP32 ulps of the step, far below
-// the FP32 rounding of the factor itself for any alpha < 1.
-__device__ __forceinline__ float adam_one(float& a, float& b, float& c, float g, float beta1, float beta2,
-                                          float ic1, float ic2, float eps, float alpha, float lower, bool inside)
-{
-    b = beta1 * b + (1.0f - beta1) * g;
-    c = beta2 * c + (1.0f - beta2) * (g * g);
-    const float bh = b * ic1;
-    const float ch = c * ic2;
-    const float step = inside ? bh * rsqrtf(ch + eps) : __fdividef(bh, sqrtf(ch) + eps);
-    a = fmaxf(a - alpha * step, lower);
-    return a;
 }
 
 // One launch of the Adam step.  Every thread reads the step's scalars (t,
@@ -82,11 +47,9 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
     const float alpha = a.st->alpha;
     const int done = a.st->done;
     if constexpr (kSync == kCluster) cluster_arrive();
-    // 1 - beta^n = -expm1(n log1p(beta - 1)): accurate to a few FP32 ulps even
-    // for beta near 1 and small n, where 1 - powf(beta, n) would cancel
     const float n = static_cast<float>(t0 + 1);
-    const float ic1 = 1.0f / -expm1f(n * log1pf(a.beta1 - 1.0f));
-    const float ic2 = 1.0f / -expm1f(n * log1pf(a.beta2 - 1.0f));
+    const float ic1 = inv_bias_correction(a.beta1, n);
+    const float ic2 = inv_bias_correction(a.beta2, n);
     const ModeTable& mt = a.mt;
     // 32-bit element indices: the host keeps the factor set below 2^31 float4 chunks
     const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
@@ -156,109 +119,28 @@ cudaError_t launch_adam(const AdamArgs& a, int grid, cudaStream_t s)
 }
 
 // The step after a gradient kernel that advanced t (gcp_iteration), with
-// the replica fold split over kParts lanes per float4 element: lane p of an
-// element's group adds replicas p, p + kParts, ... (all its loads in flight
-// at once) and zeroes them, the group sums its partials with shuffles in a
-// fixed order, and lane 0 applies the Adam update.  Each thread so has a few
-// loads outstanding instead of all of an element's replicas, and the work is
-// spread thinly (64 threads per block) over many SMs.  No block waits for
-// another: t was advanced by the gradient kernel; block 0 advances iter,
-// which no Adam block reads.
-constexpr int kParts = 4;
-
+// the replica fold split over kParts lanes per float4 element (the layout of
+// adam_elements), spread thinly (64 threads per block) over many SMs.  No
+// block waits for another: t was advanced by the gradient kernel; block 0
+// advances iter, which no Adam block reads.
+//
+// The first element's mode, addresses and A, B, C, and the scalars alpha and
+// done, were last written two launches back or earlier (the previous
+// iteration's Adam step, an epoch kernel), which had completed before this
+// iteration's gradient kernel passed its wait; they are read before this
+// kernel's wait, with the kernel parameters.  G and the replicas come from the
+// gradient kernel and are read after it.
 __global__ void __launch_bounds__(64) adam_split_kernel(const AdamArgs a)
 {
-    const ModeTable& mt = a.mt;
-    const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
-    const uint32_t ld4 = static_cast<uint32_t>(mt.ld) / 4;
-    const bool inside = a.eps_inside_sqrt != 0;
-    const uint32_t part = threadIdx.x % kParts;
-    const uint32_t stride = gridDim.x * blockDim.x / kParts;  // elements per grid step
-    // warp-uniform trip count: every lane of a warp takes part in the shuffles
-    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) / kParts;
-    const uint32_t warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / kParts;
-
-    // An element's mode, addresses and A, B, C.  A, B, C were last written by
-    // the previous iteration's Adam step (or earlier), which had completed
-    // before this iteration's gradient kernel passed its wait, so the first
-    // element is prepared before this kernel's wait, together with the
-    // kernel-parameter reads; G and the replicas come from the gradient kernel
-    // and are read after it.
-    int k = 0;
-    uint32_t loc = 0;
-    float4 A4 = make_float4(0.f, 0.f, 0.f, 0.f), B4 = A4, C4 = A4;
-    auto prepare = [&](uint32_t i4) {
-        if (i4 >= total4) return;
-        k = mode_of(mt, i4);
-        loc = i4 - static_cast<uint32_t>(mt.off4[k]);
-        if (part == 0) {
-            A4 = reinterpret_cast<const float4*>(mt.A[k])[loc];
-            B4 = reinterpret_cast<const float4*>(mt.B[k])[loc];
-            C4 = reinterpret_cast<const float4*>(mt.C[k])[loc];
-        }
-    };
-    prepare(first);
-    const float alpha = a.st->alpha;  // written by epoch kernels only
+    const uint32_t total4 = static_cast<uint32_t>(a.mt.off4[a.mt.d]);
+    const uint32_t gthread = blockIdx.x * blockDim.x + threadIdx.x;
+    AdamElem e;
+    adam_prepare(a, gthread / kParts, total4, gthread % kParts, e);
+    const float alpha = a.st->alpha;
     const int done = a.st->done;
     pdl_wait();
     pdl_trigger();
-    const int64_t t0 = a.st->t;  // advanced by this iteration's gradient kernel
-    const float n = static_cast<float>(t0);
-    const float ic1 = 1.0f / -expm1f(n * log1pf(a.beta1 - 1.0f));
-    const float ic2 = 1.0f / -expm1f(n * log1pf(a.beta2 - 1.0f));
-    for (uint32_t w4 = warp_first, i4 = first; w4 < total4; w4 += stride, i4 += stride) {
-        if (i4 != first) prepare(i4);
-        const bool live_elem = i4 < total4;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 g = acc;
-        if (live_elem) {
-            if (part == 0) g = reinterpret_cast<const float4*>(mt.G[k])[loc];
-            const uint32_t reps = a.reps[k] > 1 ? a.reps[k] : 0;
-            float4* r = reinterpret_cast<float4*>(a.R[k]) + loc;
-            const uint64_t rs = a.rep_stride4[k];
-            constexpr int kWide = 8;  // per lane: replicas part, part + kParts, ... (up to 32 in flight per group)
-            float4 v[kWide];
-#pragma unroll
-            for (int q = 0; q < kWide; ++q) {
-                const uint32_t rep = part + static_cast<uint32_t>(q) * kParts;
-                v[q] = rep < reps ? r[rep * rs] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < kWide; ++q) acc = add4(acc, v[q]);
-#pragma unroll
-            for (int q = 0; q < kWide; ++q) {
-                const uint32_t rep = part + static_cast<uint32_t>(q) * kParts;
-                if (rep < reps) r[rep * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            for (uint32_t rep = part + kWide * kParts; rep < reps; rep += kParts) {
-                acc = add4(acc, r[rep * rs]);
-                r[rep * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        // the group's partial sums: lane 0 ends with ((p0 + p1) + (p2 + p3))
-#pragma unroll
-        for (int off = 1; off < kParts; off <<= 1) {
-            acc.x += __shfl_xor_sync(0xFFFFFFFFu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xFFFFFFFFu, acc.y, off);
-            acc.z += __shfl_xor_sync(0xFFFFFFFFu, acc.z, off);
-            acc.w += __shfl_xor_sync(0xFFFFFFFFu, acc.w, off);
-        }
-        if (!live_elem || part != 0) continue;
-        g = add4(g, acc);
-        const int col = static_cast<int>((loc % ld4) * 4);
-        if (!done && col < mt.rank) {
-            const int live = mt.rank - col;  // columns of this chunk below rank
-            adam_one(A4.x, B4.x, C4.x, g.x, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
-            if (live > 1) adam_one(A4.y, B4.y, C4.y, g.y, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
-            if (live > 2) adam_one(A4.z, B4.z, C4.z, g.z, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
-            if (live > 3) adam_one(A4.w, B4.w, C4.w, g.w, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
-            reinterpret_cast<float4*>(mt.A[k])[loc] = A4;
-            reinterpret_cast<float4*>(mt.B[k])[loc] = B4;
-            reinterpret_cast<float4*>(mt.C[k])[loc] = C4;
-            if (mt.Abf[k]) store_bf16x4(mt.Abf[k] + static_cast<size_t>(loc) * 4, A4);
-        }
-        reinterpret_cast<float4*>(mt.G[k])[loc] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    adam_elements(a, gthread, gridDim.x * blockDim.x, e, a.st->t, alpha, done);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.st->iter += 1;
 }
 
