@@ -2,7 +2,8 @@
 // form subtracts f(0, m) at the nonzeros like Alg. 3's gradient).  Each term
 // is computed in FP32; terms are summed in FP64: per thread in a fixed
 // grid-stride order, then per block, then the last block to finish adds the
-// block partials in block order.  The result is therefore the same on every
+// block partials (thread i the partials i, i + blockDim, ... in order, then a
+// fixed shuffle and warp tree).  The result is therefore the same on every
 // launch with the same list and grid.
 #include <type_traits>
 
@@ -47,11 +48,19 @@ __global__ void __launch_bounds__(256) loss_kernel(const LossArgs a)
         is_last = prev == gridDim.x - 1;
     }
     __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        __threadfence();
-        const volatile double* p = a.partials;
+    if (!is_last) return;  // block-uniform
+    __threadfence();
+    const volatile double* p = a.partials;
+    double part = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) part += p[b];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, off);
+    __syncthreads();  // warp_sums is reused
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double total = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) total += p[b];
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) total += warp_sums[w];
         *a.out = total;
         *a.ticket = 0u;
     }
