@@ -418,12 +418,16 @@ gcp_status gcp_batch_destroy(gcp_batch *b);
    <= 256; 0 = 256) and blocks (0 = one resident wave). */
 gcp_status gcp_batch_set_tuning(gcp_batch *b, int32_t block, int32_t grid_blocks);
 
-/* The sampled gradients of every problem (Eq. (4.3), Alg. 1), one launch:
-   warps take 32 consecutive draws of one problem at a time from a table of
-   all problems' draws. */
+/* The sampled gradients of every problem (Eq. (4.3), Alg. 1) into G: warps
+   take 32 consecutive draws of one problem at a time from a table of all
+   problems' draws; a mode whose rows receive many updates adds them into
+   replica slabs, folded into G by a second launch. */
 gcp_status gcp_batch_grad(gcp_batch *b, gcp_stream_t stream);
 
-/* The Adam step of every problem (as gcp_adam_step), one launch. */
+/* The Adam step of every problem (as gcp_adam_step), one launch.  It also
+   folds (and clears) the replica slabs into which gcp_batch_iteration's
+   gradient kernel spreads the updates of heavily hit rows; after a plain
+   gcp_batch_grad those slabs are already folded and zero. */
 gcp_status gcp_batch_adam_step(gcp_batch *b, gcp_stream_t stream);
 
 /* gcp_batch_grad then gcp_batch_adam_step. */

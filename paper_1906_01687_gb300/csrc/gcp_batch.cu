@@ -9,11 +9,15 @@
 //   batch_epoch_kernel -- every problem's epoch accept / revert.
 // The per-problem arithmetic is that of the single-problem kernels; lanes per
 // draw and chunks per lane are chosen per problem from its rank at run time.
+// A mode whose rows each receive many updates per iteration spreads them over
+// replica slabs (warp u adds into replica u mod R), which the Adam kernel
+// folds into G and clears, as the single-problem gcp_iteration does.
 #include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
 
+#include "gcp_adam_phase.cuh"
 #include "gcp_device.cuh"
 #include "gcp_kernels.cuh"
 
@@ -36,6 +40,9 @@ struct BatchDesc {
     float* SA[kBatchMaxD];
     float* SB[kBatchMaxD];
     float* SC[kBatchMaxD];
+    float* R[kBatchMaxD];          // replica slabs of mode k (reps[k] > 1), kept zero between iterations
+    uint32_t reps[kBatchMaxD];
+    uint64_t rep_stride[kBatchMaxD];  // floats between replicas: n_k * ld
     int64_t off4[kBatchMaxD + 1];  // float4 prefix of the problem's modes
     uint64_t seed, problem;
     int64_t s;
@@ -129,6 +136,13 @@ __global__ void __launch_bounds__(256) batch_grad_kernel(const BatchArgs a)
             x = __ldg(P.X + lin);
         }
         const int gl = lane & (L - 1), gbase = lane & ~(L - 1);
+        // this batch's destination of each mode: G_k, or replica u mod R of its slabs
+        float* dst[kBatchMaxD];
+#pragma unroll
+        for (int k = 0; k < kBatchMaxD; ++k)
+            dst[k] = (k < d && P.reps[k] > 1)
+                         ? P.R[k] + static_cast<size_t>(static_cast<uint32_t>(u) % P.reps[k]) * P.rep_stride[k]
+                         : P.G[k];
         for (int b = 0; b < L; ++b) {
             const int src = gbase + b;
             uint32_t jx[kBatchMaxD];
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(256) batch_grad_kernel(const BatchArgs a)
 #pragma unroll
                 for (int k = 0; k < kBatchMaxD; ++k) {
                     if (k >= d) continue;
-                    atomicAdd(reinterpret_cast<float4*>(P.G[k] + static_cast<size_t>(jx[k]) * ld + col),
+                    atomicAdd(reinterpret_cast<float4*>(dst[k] + static_cast<size_t>(jx[k]) * ld + col),
                               mul4(pre[k], suf[k]));
                 }
             }
@@ -205,8 +219,8 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
     for (int b = threadIdx.x; b < a.count; b += blockDim.x) {
         const BatchDesc& P = a.desc[b];
         const float n = static_cast<float>(P.st->t + 1);
-        s_prob[4 * b + 0] = -expm1f(n * log1pf(P.beta1 - 1.0f));
-        s_prob[4 * b + 1] = -expm1f(n * log1pf(P.beta2 - 1.0f));
+        s_prob[4 * b + 0] = inv_bias_correction(P.beta1, n);
+        s_prob[4 * b + 1] = inv_bias_correction(P.beta2, n);
         s_prob[4 * b + 2] = P.st->alpha;
         s_prob[4 * b + 3] = P.st->done ? 1.0f : 0.0f;
     }
@@ -221,43 +235,62 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
         const int64_t loc = p4 - P.off4[k];
         const int col = static_cast<int>((loc * 4) % P.ld);
         float4* g4 = reinterpret_cast<float4*>(P.G[k]) + loc;
+        float4 g = *g4;
+        if (P.reps[k] > 1)  // fold the replica slabs of this mode, leaving them zero
+            g = add4(g, fold_replicas(reinterpret_cast<float4*>(P.R[k]) + loc, P.reps[k], P.rep_stride[k] / 4));
         if (s_prob[4 * pb + 3] == 0.0f && col < P.rank) {
-            const float c1 = s_prob[4 * pb], c2 = s_prob[4 * pb + 1], alpha = s_prob[4 * pb + 2];
-            const float4 g = *g4;
+            const float ic1 = s_prob[4 * pb], ic2 = s_prob[4 * pb + 1], alpha = s_prob[4 * pb + 2];
             float4* a4p = reinterpret_cast<float4*>(P.A[k]) + loc;
             float4* b4p = reinterpret_cast<float4*>(P.B[k]) + loc;
             float4* c4p = reinterpret_cast<float4*>(P.C[k]) + loc;
-            float av[4], bv[4], cv[4];
-            const float gv[4] = {g.x, g.y, g.z, g.w};
             float4 A4 = *a4p, B4 = *b4p, C4 = *c4p;
-            av[0] = A4.x; av[1] = A4.y; av[2] = A4.z; av[3] = A4.w;
-            bv[0] = B4.x; bv[1] = B4.y; bv[2] = B4.z; bv[3] = B4.w;
-            cv[0] = C4.x; cv[1] = C4.y; cv[2] = C4.z; cv[3] = C4.w;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (col + e >= P.rank) continue;
-                bv[e] = P.beta1 * bv[e] + (1.0f - P.beta1) * gv[e];
-                cv[e] = P.beta2 * cv[e] + (1.0f - P.beta2) * (gv[e] * gv[e]);
-                const float bh = bv[e] / c1, ch = cv[e] / c2;
-                const float den = P.eps_inside ? sqrtf(ch + P.eps) : sqrtf(ch) + P.eps;
-                av[e] = fmaxf(av[e] - alpha * (bh / den), P.lower);
-            }
-            A4 = make_float4(av[0], av[1], av[2], av[3]);
+            const bool inside = P.eps_inside != 0;
+            const int ncol = P.rank - col;
+            adam_one(A4.x, B4.x, C4.x, g.x, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+            if (ncol > 1) adam_one(A4.y, B4.y, C4.y, g.y, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+            if (ncol > 2) adam_one(A4.z, B4.z, C4.z, g.z, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+            if (ncol > 3) adam_one(A4.w, B4.w, C4.w, g.w, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
             *a4p = A4;
-            *b4p = make_float4(bv[0], bv[1], bv[2], bv[3]);
-            *c4p = make_float4(cv[0], cv[1], cv[2], cv[3]);
+            *b4p = B4;
+            *c4p = C4;
             if (P.Abf[k]) bstore_bf16x4(P.Abf[k] + loc * 4, A4);
         }
         *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (batch_last_block(a.ticket) && threadIdx.x == 0) {
-        for (int b = 0; b < a.count; ++b) {
+    if (batch_last_block(a.ticket)) {  // every problem's step count, one thread per problem
+        for (int b = threadIdx.x; b < a.count; b += blockDim.x) {
             gcp_adam_state* st = a.desc[b].st;
             if (!st->done) st->t += 1;
             st->iter += 1;
         }
-        *a.ticket = 0u;
-        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *a.ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// gcp_batch_grad on its own: every problem's replica slabs folded into G (and
+// cleared); gcp_batch_iteration folds them inside the Adam kernel instead.
+__global__ void __launch_bounds__(256) batch_fold_kernel(const BatchArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ int64_t s_param[];
+    for (int i = threadIdx.x; i <= a.count; i += blockDim.x) s_param[i] = a.param_begin4[i];
+    __syncthreads();
+    const int64_t total4 = s_param[a.count];
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
+        const int pb = find_problem(s_param, a.count, i4);
+        const BatchDesc& P = a.desc[pb];
+        const int64_t p4 = i4 - s_param[pb];
+        const int k = mode_in_problem(P, p4);
+        if (P.reps[k] <= 1) continue;
+        const int64_t loc = p4 - P.off4[k];
+        float4* g4 = reinterpret_cast<float4*>(P.G[k]) + loc;
+        *g4 = add4(*g4, fold_replicas(reinterpret_cast<float4*>(P.R[k]) + loc, P.reps[k], P.rep_stride[k] / 4));
     }
 }
 
@@ -390,6 +423,7 @@ struct gcp_batch {
     int64_t* d_est = nullptr;
     double* d_partials = nullptr;
     unsigned int* d_ticket = nullptr;
+    float* d_rep = nullptr;  // every problem's replica slabs
     int64_t total_work = 0, total_param4 = 0, est_blocks = 0;
     int num_sms = 1;
     int block = 0, grid = 0;
@@ -399,6 +433,11 @@ namespace {
 
 constexpr int kBatchMaxProblems = 1024;
 constexpr int kBatchEstBlocksPerProblem = 32;
+// replica slabs: a mode whose rows receive more than kBatchRepTarget updates
+// per iteration on average gets ceil(updates / kBatchRepTarget) slabs, at most
+// kBatchMaxReps (the single-problem defaults)
+constexpr double kBatchRepTarget = 64.0;
+constexpr int64_t kBatchMaxReps = 32;
 
 bool al(const void* p, size_t a) { return p && (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -517,6 +556,22 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
         const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((desc[i].n_est + 255) / 256, kBatchEstBlocksPerProblem));
         est[i + 1] = est[i] + nb;
     }
+    // replica slabs per problem and mode, one workspace for all (offsets filled after allocation)
+    std::vector<int64_t> rep_off(static_cast<size_t>(count) * kBatchMaxD, -1);
+    int64_t rep_floats = 0;
+    for (int i = 0; i < count; ++i) {
+        for (int k = 0; k < desc[i].d; ++k) {
+            const double hits = static_cast<double>(desc[i].s) / static_cast<double>(desc[i].dims[k]);
+            const int64_t r = std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(std::ceil(hits / kBatchRepTarget)),
+                                                                      kBatchMaxReps));
+            desc[i].reps[k] = static_cast<uint32_t>(r);
+            desc[i].rep_stride[k] = static_cast<uint64_t>(desc[i].dims[k]) * desc[i].ld;
+            if (r > 1) {
+                rep_off[static_cast<size_t>(i) * kBatchMaxD + k] = rep_floats;
+                rep_floats += r * static_cast<int64_t>(desc[i].rep_stride[k]);
+            }
+        }
+    }
     gcp_batch* b = new (std::nothrow) gcp_batch();
     if (!b) return GCP_ERR_NO_MEMORY;
     b->count = count;
@@ -539,6 +594,15 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_est), sizeof(int64_t) * (count + 1))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_partials), sizeof(double) * b->est_blocks)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_ticket), sizeof(unsigned int))) != cudaSuccess) return fail(e);
+    if (rep_floats > 0) {
+        if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_rep), sizeof(float) * rep_floats)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(b->d_rep, 0, sizeof(float) * rep_floats, s)) != cudaSuccess) return fail(e);
+    }
+    for (int i = 0; i < count; ++i)
+        for (int k = 0; k < desc[i].d; ++k) {
+            const int64_t off = rep_off[static_cast<size_t>(i) * kBatchMaxD + k];
+            desc[i].R[k] = off >= 0 ? b->d_rep + off : nullptr;
+        }
     if ((e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(e);
     if ((e = cudaMemcpyAsync(b->d_work, work.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -563,6 +627,7 @@ gcp_status gcp_batch_destroy(gcp_batch* b)
     cudaFree(b->d_est);
     cudaFree(b->d_partials);
     cudaFree(b->d_ticket);
+    cudaFree(b->d_rep);
     delete b;
     return GCP_OK;
 }
@@ -575,7 +640,8 @@ gcp_status gcp_batch_set_tuning(gcp_batch* b, int32_t block, int32_t grid_blocks
     return GCP_OK;
 }
 
-gcp_status gcp_batch_grad(gcp_batch* b, gcp_stream_t stream)
+// The gradient kernel alone: replicated modes are left in their slabs.
+static gcp_status batch_grad_launch(gcp_batch* b, gcp_stream_t stream)
 {
     if (!b) return GCP_ERR_INVALID_ARG;
     if (b->total_work == 0) return GCP_OK;
@@ -591,6 +657,15 @@ gcp_status gcp_batch_grad(gcp_batch* b, gcp_stream_t stream)
                                 batch_args(b, 0)));
 }
 
+gcp_status gcp_batch_grad(gcp_batch* b, gcp_stream_t stream)
+{
+    gcp_status st = batch_grad_launch(b, stream);
+    if (st != GCP_OK || !b->d_rep) return st;
+    const size_t smem = sizeof(int64_t) * (b->count + 1);
+    return to_status(launch_pdl(batch_fold_kernel, dim3(elementwise_blocks(b)), dim3(256), smem,
+                                reinterpret_cast<cudaStream_t>(stream), batch_args(b, 0)));
+}
+
 gcp_status gcp_batch_adam_step(gcp_batch* b, gcp_stream_t stream)
 {
     if (!b) return GCP_ERR_INVALID_ARG;
@@ -601,7 +676,7 @@ gcp_status gcp_batch_adam_step(gcp_batch* b, gcp_stream_t stream)
 
 gcp_status gcp_batch_iteration(gcp_batch* b, gcp_stream_t stream)
 {
-    gcp_status st = gcp_batch_grad(b, stream);
+    gcp_status st = batch_grad_launch(b, stream);  // the Adam kernel folds the replica slabs
     if (st != GCP_OK) return st;
     return gcp_batch_adam_step(b, stream);
 }
