@@ -538,8 +538,8 @@ def forms_bf16(torch, gcp, synth, stream):
            "metric": "entries/s of gcp_grad (zero pass + gradient)"}
     for name, bf16 in (("fp32", False), ("bf16", True)):
         F = gcp.Factors(A, bf16=bf16)
-        autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream,
-                 configs=[dict(c, early_draws=1) for c in candidates(10)])
+        tuned = autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream,
+                         configs=[dict(c, early_draws=1) for c in candidates(10)])
         G = F.like()
         t = _time_calls(torch, lambda: gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream), stream, 50)
         for x in G:
@@ -549,7 +549,8 @@ def forms_bf16(torch, gcp, synth, stream):
         got = [x[:, :10].double().cpu().numpy() for x in G]
         err = math.sqrt(sum(np.linalg.norm(a - b) ** 2 for a, b in zip(got, ref)) /
                         sum(np.linalg.norm(b) ** 2 for b in ref))
-        out[name] = {"value": 200_000 / t, "us_per_call": t * 1e6, "grad_rel_err_vs_fp64_oracle": err}
+        out[name] = {"value": 200_000 / t, "us_per_call": t * 1e6, "grad_rel_err_vs_fp64_oracle": err,
+                     "launch": gcp.gcp_get_launch(h, F, 200_000), "tuning": tuned["best"]}
     out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
     return out
 
