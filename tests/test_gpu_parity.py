@@ -61,8 +61,11 @@ def test_uniform_sample_list_bit_exact(dims, stream):
 
 @pytest.mark.parametrize("kind", ["stratified", "semi_stratified"])
 @pytest.mark.parametrize("dims,nnz,binary", [((40, 30, 20), 1200, False), ((30, 20, 10, 8), 2400, True),
-                                             ((9, 8, 7, 6, 5), 700, False), ((200, 3), 30, False)])
+                                             ((9, 8, 7, 6, 5), 700, False), ((200, 3), 30, False),
+                                             ((70000, 70000, 2), 3000, False)])
 def test_sparse_sample_list_bit_exact(kind, dims, nnz, binary):
+    """Sample lists equal the oracle's bit for bit, also on a tensor whose
+    linear keys exceed 32 bits (the last one, 9.8e9 entries)."""
     g = gcp()
     idx, vals = sparse_random(dims, nnz, 2, binary)
     h = g.Handle(g.DataTensor.coo(dims, idx, vals))
