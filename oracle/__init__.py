@@ -25,12 +25,12 @@ _lock = threading.Lock()
 _lib = None
 
 # classes, losses and samplers: the same numbering the C file defines
-UNIFORM, STRATIFIED, SEMI_STRATIFIED = 0, 1, 2
+UNIFORM, STRATIFIED, SEMI_STRATIFIED, OBSERVED = 0, 1, 2, 3
 GAUSSIAN, BERNOULLI_LOGIT, POISSON_LOG = 0, 1, 2
 BERNOULLI_ODDS, POISSON_IDENTITY, GAMMA, BETA_HALF = 3, 4, 5, 6
 M_EPS = 1e-10  # odds/identity-link losses are evaluated at m + M_EPS
 CLS_UNIFORM, CLS_STRAT_NZ, CLS_STRAT_ZERO, CLS_SEMI_NZ, CLS_SEMI_ZERO = 0, 1, 2, 3, 4
-TAG_UNIFORM, TAG_NONZERO, TAG_ZERO_CANDIDATE, TAG_SEMI_ZERO = 0, 1, 2, 3
+TAG_UNIFORM, TAG_NONZERO, TAG_ZERO_CANDIDATE, TAG_SEMI_ZERO, TAG_OBSERVED = 0, 1, 2, 3, 4
 OK, ERR_ARG, ERR_SHORTFALL = 0, 1, 4
 
 
@@ -254,10 +254,12 @@ class Samples:
 
 def sample(X: Tensor, kind: int, p: int, q: int, seed: int, stream: int,
            problem: int = 0, rho: float = 1.1) -> Samples:
-    """Draw the sample list of Alg. 1 (kind 0), Alg. 2 (kind 1) or Alg. 3 (kind 2).
+    """Draw the sample list of Alg. 1 (kind 0), Alg. 2 (kind 1), Alg. 3 (kind 2),
+    or uniform draws over the entries of nonzero weight (kind 3, Section 4.4;
+    a dense tensor with weights).
 
-    Raises RuntimeError on a stratified shortfall (fewer than q zeros after
-    64 batches of ceil(rho q omega / zeta) candidates).
+    Raises RuntimeError on a shortfall (fewer than q accepted after 64 batches
+    of candidates).
     """
     lib = _load()
     n = int(lib.orc_sample_count(kind, p, q))
@@ -274,7 +276,7 @@ def sample(X: Tensor, kind: int, p: int, q: int, seed: int, stream: int,
                         _p(keys), _p(svals), kind, p, q, seed, problem, stream, rho,
                         _p(idx), _p(x), _p(w), _p(cls), ctypes.byref(used))
     if st == ERR_SHORTFALL:
-        raise RuntimeError(f"stratified zero sampling fell short after {used.value} candidates")
+        raise RuntimeError(f"rejection sampling fell short after {used.value} candidates")
     if st != OK:
         raise ValueError(f"oracle sample: invalid arguments (status {st})")
     return Samples(idx, x, w, cls, used.value)

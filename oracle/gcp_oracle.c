@@ -34,11 +34,13 @@
 #define ORC_TAG_NONZERO 1u
 #define ORC_TAG_ZERO_CANDIDATE 2u
 #define ORC_TAG_SEMI_ZERO 3u
+#define ORC_TAG_OBSERVED 4u
 
 /* sampler kinds */
 #define ORC_UNIFORM 0
 #define ORC_STRATIFIED 1
 #define ORC_SEMI_STRATIFIED 2
+#define ORC_OBSERVED 3
 
 /* classes of a drawn entry; they decide which form of y_i applies */
 #define ORC_CLS_UNIFORM 0     /* Alg. 1: weight omega/s, g(x,m)            */
@@ -303,7 +305,17 @@ int orc_is_nonzero(int64_t nnz, const uint64_t *sorted_keys, uint64_t key)
 
 int64_t orc_sample_count(int kind, int64_t p, int64_t q)
 {
-    return kind == ORC_UNIFORM ? q : p + q;
+    return (kind == ORC_UNIFORM || kind == ORC_OBSERVED) ? q : p + q;
+}
+
+/* Number of entries of nonzero weight (the observed entries of weighted GCP
+   for missing data, Section 4.4). */
+int64_t orc_count_observed(int64_t n, const double *weights)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (weights[i] != 0.0) c++;
+    return c;
 }
 
 int orc_sample(int d, const int64_t *dims, int sparse,
@@ -337,6 +349,43 @@ int orc_sample(int d, const int64_t *dims, int sparse,
             }
             cls_out[j] = ORC_CLS_UNIFORM;
         }
+        return ORC_OK;
+    }
+
+    if (kind == ORC_OBSERVED) {
+        /* Section 4.4: with missing entries given weight 0, sample only the
+           entries of nonzero weight.  Reading taken: uniform draws over the
+           observed set Omega_obs by rejection, candidates c = 0, 1, ... from
+           their own stream, the first q accepted in candidate order (in
+           batches of ceil(rho q omega / |Omega_obs|), at most 64), each with
+           weight (|Omega_obs| / q) v_i: unbiased for the weighted objective,
+           as entries of weight 0 contribute nothing to it. */
+        if (sparse || !dense_weights) return ORC_ERR_ARG;
+        int64_t n_all = 1;
+        for (int k = 0; k < d; ++k) n_all *= dims[k];
+        double observed = (double)orc_count_observed(n_all, dense_weights);
+        if (q > 0 && observed <= 0) return ORC_ERR_ARG;
+        if (rho <= 0) rho = 1.1;
+        int64_t batch = q > 0 ? (int64_t)ceil(rho * (double)q * omega / observed) : 0;
+        int64_t cap = 64 * batch;
+        int64_t accepted = 0, c = 0;
+        int64_t ix[ORC_MAX_D];
+        while (accepted < q) {
+            if (c >= cap) {
+                if (candidates_used) *candidates_used = c;
+                return ORC_ERR_SHORTFALL;
+            }
+            orc_draw_multi_index(d, dims, seed, problem, stream, ORC_TAG_OBSERVED, (uint64_t)c, ix);
+            c++;
+            uint64_t key = orc_linear_key(d, dims, ix);
+            if (dense_weights[key] == 0.0) continue; /* missing: reject */
+            for (int k = 0; k < d; ++k) idx_out[accepted * d + k] = ix[k];
+            x_out[accepted] = dense_vals[key];
+            w_out[accepted] = (observed / (double)q) * dense_weights[key];
+            cls_out[accepted] = ORC_CLS_UNIFORM;
+            accepted++;
+        }
+        if (candidates_used) *candidates_used = c;
         return ORC_OK;
     }
 

@@ -349,3 +349,22 @@ def test_uniform_over_sparse_enumeration_identity():
     G, _ = oracle.full_grad(dims, A, oracle.POISSON_LOG, X)
     for k in range(3):
         np.testing.assert_allclose(Gs[k], G[k], rtol=1e-12, atol=1e-12)
+
+
+def test_observed_sampling_unbiased():
+    """Drawing only the entries of nonzero weight (Section 4.4, missing data
+    as weight 0) keeps the gradient unbiased for the weighted full gradient,
+    with 40% of the entries missing."""
+    dims = (3, 4, 5)
+    X, A = problem(dims, 2, oracle.POISSON_LOG, 73)
+    rng = np.random.default_rng(74)
+    v = (0.5 + rng.random(dims)) * (rng.random(dims) >= 0.4)
+    G_full, _ = oracle.full_grad(dims, A, oracle.POISSON_LOG, X, weights=v)
+    T = oracle.Tensor(dims, dense=X, weights=v)
+    N = 3000
+    gs = np.array([np.concatenate([g.reshape(-1) for g in
+                                   oracle.grad(dims, A, oracle.POISSON_LOG, oracle.sample(T, oracle.OBSERVED, 0, 30, 5, t))])
+                   for t in range(N)])
+    full = np.concatenate([g.reshape(-1) for g in G_full])
+    se = gs.std(axis=0, ddof=1) / np.sqrt(N)
+    assert np.all(np.abs(gs.mean(axis=0) - full) <= 5 * se + 1e-12)

@@ -172,3 +172,45 @@ def test_uniform_with_entry_weights_matches_twin():
     twin = twin_sample(dims, X, None, None, oracle.UNIFORM, 0, 300, 4, 1)
     twin = [(ix, x, w * v[tuple(ix)], c) for ix, x, w, c in twin]
     compare(S, twin)
+
+
+def twin_observed(dims, X, v, q, seed, stream, rho=1.1):
+    """Uniform draws over the entries of nonzero weight (Section 4.4): candidates
+    from their own stream, the first q with v != 0 kept in candidate order."""
+    observed = int(np.count_nonzero(v))
+    out, c = [], 0
+    cap = 64 * math.ceil(rho * q * math.prod(dims) / observed)
+    while len(out) < q:
+        assert c < cap
+        ix = twin_index(dims, seed, stream, oracle.TAG_OBSERVED, c)
+        c += 1
+        if v[tuple(ix)] == 0:
+            continue
+        out.append((ix, X[tuple(ix)], observed / q * v[tuple(ix)], oracle.CLS_UNIFORM))
+    return out
+
+
+@pytest.mark.parametrize("missing", [0.0, 0.3, 0.9])
+def test_observed_sampler_matches_twin(missing):
+    dims = (6, 7, 8)
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal(dims)
+    v = rng.random(dims) * (rng.random(dims) >= missing)
+    if missing == 0.0:
+        v = np.ones(dims)
+    S = oracle.sample(oracle.Tensor(dims, dense=X, weights=v), oracle.OBSERVED, 0, 400, 11, 6)
+    compare(S, twin_observed(dims, X, v, 400, 11, 6))
+    assert all(v[tuple(ix)] != 0 for ix in S.idx.tolist())  # missing entries are never drawn
+
+
+def test_observed_sampler_shortfall_and_arguments():
+    dims = (4, 4, 4)
+    X = np.ones(dims)
+    v = np.zeros(dims)
+    v[1, 2, 3] = 1.0
+    with pytest.raises(RuntimeError, match="short"):
+        oracle.sample(oracle.Tensor(dims, dense=X, weights=v), oracle.OBSERVED, 0, 50, 1, 0, rho=0.01)
+    with pytest.raises(ValueError):  # no weights: nothing defines the observed set
+        oracle.sample(oracle.Tensor(dims, dense=X), oracle.OBSERVED, 0, 5, 1, 0)
+    with pytest.raises(ValueError):  # every entry missing
+        oracle.sample(oracle.Tensor(dims, dense=X, weights=np.zeros(dims)), oracle.OBSERVED, 0, 5, 1, 0)
