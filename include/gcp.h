@@ -71,11 +71,16 @@ typedef enum gcp_loss {
 } gcp_loss;
 
 /* Samplers: Alg. 1 (uniform, Section 4.1), Alg. 2 (stratified, Section 4.2),
-   Alg. 3 (semi-stratified, Section 4.3). */
+   Alg. 3 (semi-stratified, Section 4.3), and uniform draws over the entries
+   of nonzero weight (Section 4.4: missing data as weight 0, avoided when
+   sampling; dense tensors with weights): candidates from their own stream,
+   the first q of nonzero weight kept in candidate order (batches of
+   ceil(rho q omega / |Omega_obs|), at most 64), weight (|Omega_obs| / q) v_i. */
 typedef enum gcp_sampler {
     GCP_SAMPLER_UNIFORM = 0,
     GCP_SAMPLER_STRATIFIED = 1,
-    GCP_SAMPLER_SEMI_STRATIFIED = 2
+    GCP_SAMPLER_SEMI_STRATIFIED = 2,
+    GCP_SAMPLER_OBSERVED = 3
 } gcp_sampler;
 
 /* Class of a drawn entry; it selects the form of y_i and of the F-hat term:

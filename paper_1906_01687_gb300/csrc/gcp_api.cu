@@ -9,6 +9,7 @@
 #include <new>
 
 #include "../../include/gcp.h"
+#include "gcp_device.cuh"
 #include "gcp_kernels.cuh"
 
 using namespace gcpk;
@@ -38,6 +39,8 @@ struct gcp_handle {
     unsigned long long* table = nullptr;
     float* table_vals = nullptr;
     uint64_t table_mask = 0;
+    // entries of nonzero weight (observed-entry sampling), counted on first use
+    int64_t n_observed = -1;
     // stratified zero list and its pass scratch
     int64_t zq_cap = 0;
     int32_t* zidx_base = nullptr;
@@ -132,6 +135,10 @@ gcp_status check_spec(const gcp_handle* h, const gcp_sampling* S)
     case GCP_SAMPLER_SEMI_STRATIFIED:
         if (!h->X.sparse) return GCP_ERR_INVALID_ARG;
         return GCP_OK;
+    case GCP_SAMPLER_OBSERVED:
+        // dense tensors with entry weights: the observed set is {i : v_i != 0}
+        if (h->X.sparse || !h->X.weights || S->p != 0) return GCP_ERR_INVALID_ARG;
+        return GCP_OK;
     default:
         return GCP_ERR_INVALID_ARG;
     }
@@ -169,6 +176,13 @@ DrawArgs make_draw_args(const gcp_handle* h, const gcp_sampling* S, const gcp_sa
     a.problem = S->problem;
     a.stream = S->stream;
     const double omega = h->omega, eta = static_cast<double>(h->X.nnz);
+    if (S->kind == GCP_SAMPLER_OBSERVED) {  // reads the list of the observed-entry pass
+        a.src = kSrcObserved;
+        a.p = 0;
+        a.n_total = S->q;
+        a.w_first = S->q > 0 ? static_cast<float>(static_cast<double>(h->n_observed) / static_cast<double>(S->q)) : 0.0f;
+        return a;
+    }
     if (S->kind == GCP_SAMPLER_UNIFORM) {
         a.src = h->X.sparse ? kSrcUniformSparse : kSrcUniformDense;
         a.p = 0;
@@ -232,8 +246,23 @@ gcp_status ensure_zero_scratch(gcp_handle* h, int64_t tiles)
 int64_t zero_batch(const gcp_handle* h, const gcp_sampling* S)
 {
     const double rho = S->oversample > 0.0 ? S->oversample : 1.1;
-    const double zeta = h->omega - static_cast<double>(h->X.nnz);
-    return static_cast<int64_t>(std::ceil(rho * static_cast<double>(S->q) * h->omega / zeta));
+    const double accept = S->kind == GCP_SAMPLER_OBSERVED ? static_cast<double>(h->n_observed)
+                                                          : h->omega - static_cast<double>(h->X.nnz);
+    return static_cast<int64_t>(std::ceil(rho * static_cast<double>(S->q) * h->omega / accept));
+}
+
+// Counts the entries of nonzero weight once (a host read: call gcp_reserve
+// before capturing a graph).  Errors: no entry of nonzero weight.
+gcp_status ensure_observed(gcp_handle* h, cudaStream_t s)
+{
+    if (h->n_observed >= 0) return h->n_observed > 0 ? GCP_OK : GCP_ERR_INVALID_ARG;
+    const int64_t n = static_cast<int64_t>(h->omega);
+    GCP_CUDA_TRY(launch_count_nonzero(h->X.weights, n, h->zcount, s));
+    int64_t c = 0;
+    GCP_CUDA_TRY(cudaMemcpyAsync(&c, h->zcount, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GCP_CUDA_TRY(cudaStreamSynchronize(s));
+    h->n_observed = c;
+    return c > 0 ? GCP_OK : GCP_ERR_INVALID_ARG;
 }
 
 // Runs the ordered rejection pass; the accepted zeros go to the given destination.
@@ -241,7 +270,8 @@ gcp_status run_zero_pass(gcp_handle* h, const gcp_sampling* S, const int64_t* st
                          int32_t* const out_idx[GCP_MAX_MODES], float* out_x, float* out_w, int8_t* out_cls,
                          float w_zero, cudaStream_t s)
 {
-    gcp_status st = ensure_hash(h, s);
+    const bool observed = S->kind == GCP_SAMPLER_OBSERVED;
+    gcp_status st = observed ? ensure_observed(h, s) : ensure_hash(h, s);
     if (st != GCP_OK) return st;
     const int64_t batch = zero_batch(h, S);
     const int64_t tiles = (batch + 1023) / 1024;
@@ -263,6 +293,12 @@ gcp_status run_zero_pass(gcp_handle* h, const gcp_sampling* S, const int64_t* st
     z.cap = 64 * batch;
     z.table = h->table;
     z.table_mask = h->table_mask;
+    z.tag = static_cast<uint32_t>(observed ? kTagObserved : kTagZeroCandidate);
+    if (observed) {
+        z.obs_w = h->X.weights;
+        z.obs_x = h->X.vals;
+        z.w_obs = static_cast<double>(h->n_observed) / static_cast<double>(S->q);
+    }
     z.mask_words = h->mask_words;
     z.tile_counts = h->tile_counts;
     z.tile_offsets = h->tile_offsets;
@@ -473,7 +509,7 @@ const char* gcp_status_string(gcp_status s)
 int64_t gcp_sample_count(const gcp_sampling* S)
 {
     if (!S || S->p < 0 || S->q < 0) return -1;
-    if (S->kind == GCP_SAMPLER_UNIFORM) return S->q;
+    if (S->kind == GCP_SAMPLER_UNIFORM || S->kind == GCP_SAMPLER_OBSERVED) return S->q;
     if (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_SEMI_STRATIFIED) return S->p + S->q;
     return -1;
 }
@@ -688,6 +724,12 @@ gcp_status gcp_sample(gcp_handle* h, const gcp_sampling* S, const gcp_samples* o
         st = ensure_hash(h, s);
         if (st != GCP_OK) return st;
     }
+    if (S->kind == GCP_SAMPLER_OBSERVED) {  // the whole list comes from the observed-entry pass
+        if ((st = ensure_observed(h, s)) != GCP_OK) return st;
+        int32_t* odst[GCP_MAX_MODES] = {};
+        for (int k = 0; k < h->X.d; ++k) odst[k] = out->idx[k];
+        return run_zero_pass(h, S, nullptr, odst, out->x, out->w, out->cls, 0.0f, s);
+    }
     DrawArgs dr = make_draw_args(h, S, nullptr, nullptr);
     if (S->kind != GCP_SAMPLER_STRATIFIED) {
         GCP_CUDA_TRY(launch_materialise(dr, out->idx, out->x, out->w, out->cls, 0, dr.n_total, h->d_status, s));
@@ -710,8 +752,9 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
     if (S->kind == GCP_SAMPLER_UNIFORM && h->X.sparse) {
         if ((st = ensure_hash(h, s)) != GCP_OK) return st;
     }
-    if (S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
-        if ((st = ensure_hash(h, s)) != GCP_OK) return st;
+    if ((S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
+        st = S->kind == GCP_SAMPLER_OBSERVED ? ensure_observed(h, s) : ensure_hash(h, s);
+        if (st != GCP_OK) return st;
         if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 1023) / 1024)) != GCP_OK) return st;
         if ((st = ensure_zero_list(h, S->q)) != GCP_OK) return st;
     }
@@ -740,6 +783,10 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
         st = ensure_hash(h, s);
         if (st != GCP_OK) return st;
     }
+    if (S && S->kind == GCP_SAMPLER_OBSERVED && S->q > 0) {
+        st = ensure_observed(h, s);
+        if (st != GCP_OK) return st;
+    }
     GradArgs a{};
     a.dr = make_draw_args(h, S, list, stream_dev);
     // early descriptors only for draws that read nothing but the data tensor and
@@ -748,7 +795,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     const bool early_ok = a.dr.src == kSrcUniformDense || (a.dr.src == kSrcUniformSparse && table_ready) ||
                           a.dr.src == kSrcSparse;
     if (a.dr.n_total == 0) return GCP_OK;
-    if (S && S->kind == GCP_SAMPLER_STRATIFIED && S->q > 0) {
+    if (S && (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
         st = ensure_zero_list(h, S->q);
         if (st != GCP_OK) return st;
         int32_t* zdst[GCP_MAX_MODES] = {};

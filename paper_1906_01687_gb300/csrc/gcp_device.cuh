@@ -16,7 +16,7 @@ namespace gcpk {
 constexpr int kMaxModes = GCP_MAX_MODES;
 
 // Philox tags (the third counter word)
-constexpr uint64_t kTagUniform = 0, kTagNonzero = 1, kTagZeroCandidate = 2, kTagSemiZero = 3;
+constexpr uint64_t kTagUniform = 0, kTagNonzero = 1, kTagZeroCandidate = 2, kTagSemiZero = 3, kTagObserved = 4;
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy

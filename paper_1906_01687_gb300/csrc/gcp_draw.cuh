@@ -77,6 +77,27 @@ __device__ __forceinline__ void make_draw(const DrawArgs& a, int64_t j, uint64_t
         return;
     }
 
+    if (a.src == kSrcObserved) {
+        // Section 4.4: draw j is the j-th accepted entry of nonzero weight; its
+        // value and weight (|Omega_obs| / s) v_i are read at its linear key
+        uint64_t lin = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < a.d) {
+                o.ix[k] = static_cast<uint32_t>(__ldg(a.zidx[k] + j));
+                lin += static_cast<uint64_t>(o.ix[k]) * a.strides[k];
+            }
+        }
+        o.cls = GCP_CLS_UNIFORM;
+        if (j >= *a.zcount) {  // shortfall slot: contributes nothing
+            o.valid = false;
+            return;
+        }
+        o.x = __ldg(a.X + lin);
+        o.w = a.w_first * __ldg(a.W + lin);
+        return;
+    }
+
     if (a.src == kSrcEnumerate) {
         // draw j is the index with row-major linear index j (Eqs. (1.2), (4.2) over all of Omega)
         uint64_t rem = static_cast<uint64_t>(j);

@@ -16,7 +16,8 @@ enum Source : int32_t {
     kSrcSparse = 1,        // Algs. 2/3: nonzeros generated in-kernel, zeros generated (semi) or listed (stratified)
     kSrcList = 2,          // a materialised list
     kSrcUniformSparse = 3, // Alg. 1 over a sparse tensor: values looked up in the nonzero hash
-    kSrcEnumerate = 4      // every index of a dense tensor once, weight 1 (or v_i): the full gradient
+    kSrcEnumerate = 4,     // every index of a dense tensor once, weight 1 (or v_i): the full gradient
+    kSrcObserved = 5       // Section 4.4: the listed entries of nonzero weight (from the rejection pass)
 };
 
 struct DrawArgs {
@@ -132,6 +133,10 @@ struct ZeroArgs {
     int64_t cap;              // candidates allowed in total (64 batches)
     const unsigned long long* table;  // nonzero key hash (open addressing)
     uint64_t table_mask;
+    uint32_t tag;             // candidate stream: zero candidates, or observed-entry candidates
+    const float* obs_w;       // observed-entry pass (Section 4.4): accept v_i != 0 (else: not a nonzero)
+    const float* obs_x;       //   and list x = X(i), w = w_obs v_i
+    double w_obs;             //   |Omega_obs| / q (the list weight is rounded once, from FP64)
     uint32_t* mask_words;     // accept bits of the parallel pass
     int32_t* tile_counts;
     int64_t* tile_offsets;
@@ -189,6 +194,8 @@ cudaError_t launch_loss(const LossArgs& a, bool bf16, int grid, int block, cudaS
 cudaError_t launch_materialise(const DrawArgs& a, int32_t* const idx[GCP_MAX_MODES], float* x, float* w,
                                int8_t* cls, int64_t first, int64_t count, int32_t* status, cudaStream_t s);
 cudaError_t launch_zero_sampling(const ZeroArgs& a, cudaStream_t s);
+// Number of nonzero entries of w[0..n) into *out (device), stream-ordered.
+cudaError_t launch_count_nonzero(const float* w, int64_t n, int64_t* out, cudaStream_t s);
 cudaError_t launch_hash_build(const int4* recs, int rec_int4, int d, const uint64_t* strides, int64_t nnz,
                               unsigned long long* table, float* table_vals, uint64_t mask, int32_t* status,
                               cudaStream_t s);

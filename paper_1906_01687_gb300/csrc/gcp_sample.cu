@@ -1,6 +1,8 @@
 // Sampling kernels: packed nonzero records, the nonzero-key hash table,
 // materialised draws (Algs. 1-3) and the ordered rejection pass that picks
 // stratified zeros (Alg. 2 with the oversampling of Section 4.2).
+#include <algorithm>
+
 #include "gcp_draw.cuh"
 
 namespace gcpk {
@@ -180,21 +182,35 @@ constexpr int kZeroBlock = 1024;  // one candidate per thread: every hash probe 
 template <int D>
 __device__ __forceinline__ bool zero_candidate(const ZeroArgs& a, uint64_t stream, int64_t c, uint32_t (&ix)[D])
 {
-    draw_index<D>(a.dims, a.seed, a.problem, stream, kTagZeroCandidate, static_cast<uint64_t>(c), a.d, ix);
+    draw_index<D>(a.dims, a.seed, a.problem, stream, a.tag, static_cast<uint64_t>(c), a.d, ix);
     if (c >= a.cap) return false;
     uint64_t key = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k)
         if (k < a.d) key += static_cast<uint64_t>(ix[k]) * a.strides[k];
+    if (a.obs_w) return __ldg(a.obs_w + key) != 0.0f;  // an observed entry (Section 4.4)
     return !hash_contains(a.table, a.table_mask, key);
 }
 
+// Writes accepted candidate `slot` of the destination list: a zero of Alg. 2
+// (x = 0, w = zeta / q), or an observed entry (x = X(i), w = w_obs v_i).
 template <int D>
 __device__ __forceinline__ void write_zero(const ZeroArgs& a, int64_t slot, const uint32_t (&ix)[D])
 {
+    uint64_t key = 0;
 #pragma unroll
-    for (int k = 0; k < D; ++k)
-        if (k < a.d) a.out_idx[k][slot] = static_cast<int32_t>(ix[k]);
+    for (int k = 0; k < D; ++k) {
+        if (k < a.d) {
+            a.out_idx[k][slot] = static_cast<int32_t>(ix[k]);
+            key += static_cast<uint64_t>(ix[k]) * a.strides[k];
+        }
+    }
+    if (a.obs_w) {
+        if (a.out_x) a.out_x[slot] = __ldg(a.obs_x + key);
+        if (a.out_w) a.out_w[slot] = static_cast<float>(a.w_obs * static_cast<double>(__ldg(a.obs_w + key)));
+        if (a.out_cls) a.out_cls[slot] = static_cast<int8_t>(GCP_CLS_UNIFORM);
+        return;
+    }
     if (a.out_x) a.out_x[slot] = 0.0f;
     if (a.out_w) a.out_w[slot] = a.w_zero;
     if (a.out_cls) a.out_cls[slot] = static_cast<int8_t>(GCP_CLS_STRAT_ZERO);
@@ -308,6 +324,7 @@ __global__ void __launch_bounds__(1024) zero_scan_kernel(const ZeroArgs a)
             for (int k = 0; k < D; ++k) ix[k] = 0u;
             write_zero<D>(a, s, ix);
             a.out_w[s] = 0.0f;
+            if (a.out_x) a.out_x[s] = 0.0f;
         }
     }
 }
@@ -346,7 +363,7 @@ __global__ void __launch_bounds__(kZeroBlock) zero_scatter_kernel(const ZeroArgs
         if (slot >= a.q) continue;
         const int64_t c = tile * kZeroTile + r * kZeroBlock + threadIdx.x;
         uint32_t ix[D];
-        draw_index<D>(a.dims, a.seed, a.problem, stream, kTagZeroCandidate, static_cast<uint64_t>(c), a.d, ix);
+        draw_index<D>(a.dims, a.seed, a.problem, stream, a.tag, static_cast<uint64_t>(c), a.d, ix);
         write_zero<D>(a, slot, ix);
     }
 }
@@ -359,6 +376,26 @@ static cudaError_t zero_launch(const ZeroArgs& a, cudaStream_t s)
     if (e == cudaSuccess) e = launch_pdl(zero_scan_kernel<D>, dim3(1), dim3(1024), 0, s, a);
     if (e == cudaSuccess) e = launch_pdl(zero_scatter_kernel<D>, tiles, dim3(kZeroBlock), 0, s, a);
     return e;
+}
+
+__global__ void __launch_bounds__(256) count_nonzero_kernel(const float* w, int64_t n, int64_t* out)
+{
+    int64_t local = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        local += w[i] != 0.0f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, off);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(reinterpret_cast<unsigned long long*>(out), static_cast<unsigned long long>(local));
+}
+
+cudaError_t launch_count_nonzero(const float* w, int64_t n, int64_t* out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    count_nonzero_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(w, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_zero_sampling(const ZeroArgs& a, cudaStream_t s)

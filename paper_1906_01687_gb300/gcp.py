@@ -30,12 +30,13 @@ STREAM_EST = 0xFFFFFFFFFFFFFFFF
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NO_MEMORY, ERR_SAMPLE_SHORTFALL, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = range(8)
 LOSS_GAUSSIAN, LOSS_BERNOULLI_LOGIT, LOSS_POISSON_LOG = 0, 1, 2
 LOSS_BERNOULLI_ODDS, LOSS_POISSON_IDENTITY, LOSS_GAMMA, LOSS_BETA_HALF = 3, 4, 5, 6
-SAMPLER_UNIFORM, SAMPLER_STRATIFIED, SAMPLER_SEMI_STRATIFIED = 0, 1, 2
+SAMPLER_UNIFORM, SAMPLER_STRATIFIED, SAMPLER_SEMI_STRATIFIED, SAMPLER_OBSERVED = 0, 1, 2, 3
 CLS_UNIFORM, CLS_STRAT_NZ, CLS_STRAT_ZERO, CLS_SEMI_NZ, CLS_SEMI_ZERO = range(5)
 LOSSES = {"gaussian": LOSS_GAUSSIAN, "bernoulli_logit": LOSS_BERNOULLI_LOGIT, "poisson_log": LOSS_POISSON_LOG,
           "bernoulli_odds": LOSS_BERNOULLI_ODDS, "poisson_identity": LOSS_POISSON_IDENTITY, "gamma": LOSS_GAMMA,
           "beta_half": LOSS_BETA_HALF}
-SAMPLERS = {"uniform": SAMPLER_UNIFORM, "stratified": SAMPLER_STRATIFIED, "semi_stratified": SAMPLER_SEMI_STRATIFIED}
+SAMPLERS = {"uniform": SAMPLER_UNIFORM, "stratified": SAMPLER_STRATIFIED, "semi_stratified": SAMPLER_SEMI_STRATIFIED,
+            "observed": SAMPLER_OBSERVED}
 
 _vp = ctypes.c_void_p
 _P8 = _vp * MAX_MODES

@@ -422,3 +422,76 @@ def test_full_gradient_and_objective(loss, weighted):
                                   weights=None if v is None else v.astype(np.float64))
     assert_grad_close(grad_to_numpy(G, 6), Gref)
     assert out.item() == pytest.approx(Fref, rel=2e-6)
+
+
+# ---------------------------------------------------------------------------
+# uniform draws over the entries of nonzero weight (Section 4.4)
+# ---------------------------------------------------------------------------
+
+def weighted_dense(dims, seed, missing):
+    r = np.random.default_rng(seed)
+    X = r.standard_normal(dims).astype(np.float32)
+    v = ((0.5 + r.random(dims)) * (r.random(dims) >= missing)).astype(np.float32)
+    return X, v
+
+
+@pytest.mark.parametrize("dims,missing", [((20, 30, 40), 0.3), ((12, 10, 9, 11), 0.9), ((7, 6, 5, 4, 3), 0.5),
+                                          ((50, 60), 0.0)])
+def test_observed_sample_list_bit_exact(dims, missing):
+    g = gcp()
+    X, v = weighted_dense(dims, 31, missing)
+    h = g.Handle(g.DataTensor.dense(X, weights=v))
+    XO = oracle.Tensor(dims, dense=X.astype(np.float64), weights=v.astype(np.float64))
+    for stream, q in [(3, 3001), (4, 1), (5, 20000)]:
+        S = g.Sampling(g.SAMPLER_OBSERVED, 0, q, seed=77, stream=stream)
+        L = g.gcp_sample(h, S)
+        torch.cuda.synchronize()
+        assert g.gcp_get_device_status(h) == 0
+        SO = oracle.sample(XO, oracle.OBSERVED, 0, q, 77, stream)
+        assert_lists_equal(L, SO)
+        assert np.all(v[tuple(L.idx[k].cpu().numpy() for k in range(len(dims)))] != 0)
+
+
+@pytest.mark.parametrize("loss", [0, 1, 2], ids=LOSS_IDS.get)
+def test_observed_gradient(loss):
+    g = gcp()
+    dims, rank = (30, 25, 20), 8
+    X, v = weighted_dense(dims, 32, 0.4)
+    if loss == 1:
+        X = (X > 0.5).astype(np.float32)
+    elif loss == 2:
+        X = np.floor(np.abs(X) * 2).astype(np.float32)
+    h = g.Handle(g.DataTensor.dense(X, weights=v))
+    XO = oracle.Tensor(dims, dense=X.astype(np.float64), weights=v.astype(np.float64))
+    A = rng_factors(dims, rank, 33, scale=(0.5 / rank) ** (1 / 3))
+    F = g.Factors(A)
+    for stream in (0, 9):
+        S = g.Sampling(g.SAMPLER_OBSERVED, 0, 5003, seed=19, stream=stream)
+        G = run_grad(h, F, loss, S=S)
+        SO = oracle.sample(XO, oracle.OBSERVED, 0, 5003, 19, stream)
+        assert_grad_close(grad_to_numpy(G, rank), oracle.grad(dims, f64(A), loss, SO),
+                          oracle.grad_abs(dims, f64(A), loss, SO))
+
+
+def test_observed_sampler_rejections():
+    """Arguments: observed sampling needs a dense tensor with weights and p = 0;
+    a tensor with every entry missing is rejected; an almost empty observed
+    set with a tiny oversampling rate reports the shortfall."""
+    g = gcp()
+    dims = (8, 8, 8)
+    X = np.ones(dims, np.float32)
+    with pytest.raises(g.GcpError):
+        g.gcp_sample(g.Handle(g.DataTensor.dense(X)), g.Sampling(g.SAMPLER_OBSERVED, 0, 10, seed=1))
+    v = np.zeros(dims, np.float32)
+    h = g.Handle(g.DataTensor.dense(X, weights=v))
+    with pytest.raises(g.GcpError):
+        g.gcp_sample(h, g.Sampling(g.SAMPLER_OBSERVED, 0, 10, seed=1))
+    v[1, 2, 3] = 1.0
+    h = g.Handle(g.DataTensor.dense(X, weights=v))
+    with pytest.raises(g.GcpError):
+        g.gcp_sample(h, g.Sampling(g.SAMPLER_OBSERVED, 3, 10, seed=1))
+    L = g.gcp_sample(h, g.Sampling(g.SAMPLER_OBSERVED, 0, 50, seed=1, oversample=0.01))
+    torch.cuda.synchronize()
+    assert g.gcp_get_device_status(h) == g.ERR_SAMPLE_SHORTFALL
+    w = L.w.cpu().numpy()
+    assert np.count_nonzero(w) >= 1 and np.all((w == 0) | (w == np.float32(1 / 50)))
