@@ -228,26 +228,32 @@ int64_t gcp_sample_count(const gcp_sampling *S);
 
 /* Materialises the drawn entries of Alg. 1 (uniform over a dense X),
    Alg. 2 (stratified: p nonzeros with xi = randi(nnz), then q zeros by
-   rejection against the nonzero keys) or Alg. 3 (semi-stratified: p
-   nonzeros, then q indices from all of Omega without rejection) into out,
-   nonzero draws first.  Each entry gets its value x (0 for zeros), its
+   rejection against the nonzero keys), Alg. 3 (semi-stratified: p
+   nonzeros, then q indices from all of Omega without rejection) or the
+   observed-entry draw of Section 4.4 (q uniform draws over the entries of
+   nonzero weight, by rejection of the rest) into out, nonzero draws first.  Each entry gets its value x (0 for zeros), its
    weight w (omega/s, eta/p, zeta/q or omega/q, computed in FP64 on the host
    and rounded once) and its class.  out->n must equal gcp_sample_count(S).
    stratified needs a sparse X with prod(dims) < 2^64 (else
    GCP_ERR_UNSUPPORTED); uniform over a sparse X looks each drawn index up
    among the nonzeros (value or 0; also prod(dims) < 2^64); uniform over a
    dense X with entry weights gives the draw weight (omega/s) v_i.  May allocate library
-   scratch on the first stratified call (cudaMalloc): make that first call
-   before any stream capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
+   scratch on the first stratified or observed call (cudaMalloc), and the
+   first observed call reads the count of entries of nonzero weight back to
+   the host: make that first call (or gcp_reserve) before any stream
+   capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
    the device status; the unfilled zero slots then hold weight 0. */
 gcp_status gcp_sample(gcp_handle *h, const gcp_sampling *S, const gcp_samples *out,
                       gcp_stream_t stream);
 
-/* Performs every library-owned allocation that gcp_sample and gcp_grad would
-   make for this spec (the stratified sampler's nonzero-key hash, candidate
-   scratch and zero list), so that later calls with the same or a smaller
-   spec allocate nothing and can be captured in a CUDA graph.  Waits for the
-   stream.  Errors: as gcp_sample. */
+/* Performs every library-owned allocation and host read that gcp_sample and
+   gcp_grad would make for this spec (the stratified sampler's nonzero-key
+   hash, candidate scratch and zero list; for the observed-entry sampler the
+   count of entries of nonzero weight, read back to the host once), so that
+   later calls with the same or a smaller spec allocate nothing, wait for
+   nothing and can be captured in a CUDA graph.  Waits for the stream.
+   Errors: as gcp_sample; GCP_ERR_INVALID_ARG when no entry has a nonzero
+   weight. */
 gcp_status gcp_reserve(gcp_handle *h, const gcp_sampling *S, gcp_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
