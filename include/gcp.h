@@ -101,7 +101,8 @@ typedef enum gcp_class {
                         an all-ones (binary) tensor.  Positions must be
                         unique for the stratified sampler's rejection test. */
 typedef struct gcp_tensor {
-    int32_t d;                        /* modes, 1..8 */
+    int32_t d;                        /* modes, 2..8 (one mode has no leave-one-out
+                                         product in Eq. (4.3): rejected) */
     int32_t sparse;
     int64_t dims[GCP_MAX_MODES];      /* n_k, each in [1, 2^31) */
     int64_t nnz;                      /* sparse only */
@@ -120,7 +121,7 @@ typedef struct gcp_tensor {
    that gcp_adam_step updates and re-rounds into A_bf16 whenever A_bf16[k]
    is non-NULL. */
 typedef struct gcp_factors {
-    int32_t rank;
+    int32_t rank;                     /* r, 1..256 */
     int32_t ld;
     int32_t bf16;
     int32_t reserved;
@@ -202,11 +203,11 @@ typedef struct gcp_handle gcp_handle; /* opaque: a prepared tensor */
    Copies the descriptor (the caller keeps X's device arrays alive and
    unchanged for the handle's lifetime) and, for a sparse X, builds in
    library-owned device memory a packed nonzero record per entry (indices and
-   value in one 16- or 32-byte record, so that a nonzero draw reads one
+   value in one 16-, 32- or 48-byte record, so that a nonzero draw reads one
    aligned segment).  The nonzero-key hash table of the stratified sampler is
    built on first stratified use.  Allocates with cudaMalloc and waits for
    the stream; call it before any stream capture.
-   Errors: GCP_ERR_INVALID_ARG (d outside 1..8, a dimension outside
+   Errors: GCP_ERR_INVALID_ARG (d outside 2..8, a dimension outside
    [1, 2^31), nnz < 1 for sparse, NULL arrays), GCP_ERR_NO_MEMORY,
    GCP_ERR_CUDA. */
 gcp_status gcp_create(gcp_handle **out, const gcp_tensor *X, gcp_stream_t stream);
@@ -391,7 +392,7 @@ gcp_status gcp_epoch_end(const gcp_factors *F, int32_t d, const int64_t *dims,
 /* for all of them.  Alg. 4 run per problem; no data crosses problems.      */
 /* ------------------------------------------------------------------------ */
 
-/* One problem of a batch.  X dense (uniform sampling, Alg. 1) with d <= 4;
+/* One problem of a batch.  X dense (uniform sampling, Alg. 1) with 2 <= d <= 4;
    F as for gcp_grad (bf16 allowed); S a uniform spec whose q draws are taken
    per iteration and whose seed and problem words key the Philox draws (the
    stream word is read from state->iter on the device); est the problem's

@@ -518,7 +518,7 @@ gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream
 {
     if (!out || !X) return GCP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (X->d < 1 || X->d > GCP_MAX_MODES) return GCP_ERR_INVALID_ARG;
+    if (X->d < 2 || X->d > GCP_MAX_MODES) return GCP_ERR_INVALID_ARG;
     for (int k = 0; k < X->d; ++k)
         if (X->dims[k] < 1 || X->dims[k] >= (int64_t(1) << 31)) return GCP_ERR_INVALID_ARG;
     if (X->sparse) {

@@ -451,7 +451,7 @@ gcp_status fill_desc(const gcp_batch_problem& p, BatchDesc* o)
 {
     const gcp_tensor& X = p.X;
     const gcp_factors& F = p.F;
-    if (X.sparse || X.d < 1 || X.d > kBatchMaxD || !X.vals || X.weights) return GCP_ERR_INVALID_ARG;
+    if (X.sparse || X.d < 2 || X.d > kBatchMaxD || !X.vals || X.weights) return GCP_ERR_INVALID_ARG;
     if (F.rank < 1 || F.rank > 256 || F.ld < F.rank || F.ld % 4 != 0) return GCP_ERR_INVALID_ARG;
     if (p.loss < GCP_LOSS_GAUSSIAN || p.loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     if (p.S.kind != GCP_SAMPLER_UNIFORM || p.S.q < 0 || p.S.q > (int64_t(1) << 40)) return GCP_ERR_INVALID_ARG;

@@ -58,6 +58,10 @@ def test_host_side_validation_without_gpu(lib_path):
     assert gcp._lib.gcp_create(ctypes.byref(h), ctypes.byref(t), None) == gcp.ERR_INVALID_ARG
     t.d = 9
     assert gcp._lib.gcp_create(ctypes.byref(h), ctypes.byref(t), None) == gcp.ERR_INVALID_ARG
+    # one mode: rejected (Eq. (4.3) has no leave-one-out product), even with a valid-looking descriptor
+    buf = (ctypes.c_float * 50)()
+    t.d, t.dims[0], t.vals = 1, 50, ctypes.addressof(buf)
+    assert gcp._lib.gcp_create(ctypes.byref(h), ctypes.byref(t), None) == gcp.ERR_INVALID_ARG
     assert gcp._lib.gcp_state_init(None, ctypes.c_float(0.1), None) == gcp.ERR_INVALID_ARG
 
 
