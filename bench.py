@@ -362,6 +362,7 @@ def ours_arm(args):
     launch = gcp.gcp_get_launch(run.h, run.F, S_DRAWS)
 
     if rank != 0:
+        torch.distributed.destroy_process_group()
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -386,14 +387,17 @@ def ours_arm(args):
             "final_state": {k: st[k] for k in ("F", "t", "iter", "alpha", "bad")}}
     clocks = clk.summary()
     line["clocks"] = clocks
-    if not args.no_sweep:
+    # the single-GPU characterisations and the CPU baseline belong to the
+    # one-GPU line; with N replicas they would only hold the N GPUs longer
+    single = world == 1
+    if single and not args.no_sweep:
         line["sweep"] = sweep_draws(torch, gcp, run, stream, peak)
-    if not args.no_large:
+    if single and not args.no_large:
         line["large_sparse"] = large_sparse(torch, gcp, synth, stream, peak)
-    if not args.no_forms:
+    if single and not args.no_forms:
         line["forms"] = {"bf16": forms_bf16(torch, gcp, synth, stream),
                          "batched": forms_batched(torch, gcp, synth, stream)}
-    if not args.no_cpu_baseline:
+    if single and not args.no_cpu_baseline:
         rate, sample = oracle_epoch_rate(oracle_tensor(X32), A0, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
