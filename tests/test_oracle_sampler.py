@@ -27,30 +27,30 @@ def twin_key(dims, ix):
     return key
 
 
-def twin_sample(dims, dense, coo, vals, kind, p, q, seed, stream, rho=1.1):
+def twin_sample(dims, dense, coo, vals, kind, p, q, seed, stream, rho=1.1, problem=0):
     omega = math.prod(dims)
     out = []  # (idx, x, w, cls)
     if kind == oracle.UNIFORM:
         for j in range(q):
-            ix = twin_index(dims, seed, stream, oracle.TAG_UNIFORM, j)
+            ix = twin_index(dims, seed, stream, oracle.TAG_UNIFORM, j, problem)
             out.append((ix, dense[tuple(ix)], omega / q, oracle.CLS_UNIFORM))
         return out
     eta = len(coo)
     for j in range(p):
-        w0 = numpy_philox_block([j, stream, oracle.TAG_NONZERO, 0], [seed, 0])[0]
+        w0 = numpy_philox_block([j, stream, oracle.TAG_NONZERO, 0], [seed, problem])[0]
         xi = (w0 * eta) >> 64
         out.append((list(coo[xi]), 1.0 if vals is None else vals[xi], eta / p,
                     oracle.CLS_STRAT_NZ if kind == oracle.STRATIFIED else oracle.CLS_SEMI_NZ))
     if kind == oracle.SEMI_STRATIFIED:
         for j in range(q):
-            ix = twin_index(dims, seed, stream, oracle.TAG_SEMI_ZERO, j)
+            ix = twin_index(dims, seed, stream, oracle.TAG_SEMI_ZERO, j, problem)
             out.append((ix, 0.0, omega / q, oracle.CLS_SEMI_ZERO))
         return out
     nzset = {twin_key(dims, c) for c in coo}
     zeta = omega - eta
     c = 0
     while len(out) < p + q:
-        ix = twin_index(dims, seed, stream, oracle.TAG_ZERO_CANDIDATE, c)
+        ix = twin_index(dims, seed, stream, oracle.TAG_ZERO_CANDIDATE, c, problem)
         c += 1
         if twin_key(dims, ix) in nzset:
             continue
@@ -174,7 +174,7 @@ def test_uniform_with_entry_weights_matches_twin():
     compare(S, twin)
 
 
-def twin_observed(dims, X, v, q, seed, stream, rho=1.1):
+def twin_observed(dims, X, v, q, seed, stream, rho=1.1, problem=0):
     """Uniform draws over the entries of nonzero weight (Section 4.4): candidates
     from their own stream, the first q with v != 0 kept in candidate order."""
     observed = int(np.count_nonzero(v))
@@ -182,7 +182,7 @@ def twin_observed(dims, X, v, q, seed, stream, rho=1.1):
     cap = 64 * math.ceil(rho * q * math.prod(dims) / observed)
     while len(out) < q:
         assert c < cap
-        ix = twin_index(dims, seed, stream, oracle.TAG_OBSERVED, c)
+        ix = twin_index(dims, seed, stream, oracle.TAG_OBSERVED, c, problem)
         c += 1
         if v[tuple(ix)] == 0:
             continue
@@ -214,3 +214,40 @@ def test_observed_sampler_shortfall_and_arguments():
         oracle.sample(oracle.Tensor(dims, dense=X), oracle.OBSERVED, 0, 5, 1, 0)
     with pytest.raises(ValueError):  # every entry missing
         oracle.sample(oracle.Tensor(dims, dense=X, weights=np.zeros(dims)), oracle.OBSERVED, 0, 5, 1, 0)
+
+
+def test_random_configurations_match_twin():
+    """Forty seeded random configurations: 2 to 8 modes (modes 4-7 come from
+    the second Philox block), extent-1 modes, densities from sparse to
+    mostly full, random 64-bit seeds, streams (including the estimate stream
+    2^64 - 1) and problem words, every sampler kind, p or q of 0."""
+    rng = np.random.default_rng(2024)
+    kinds = [oracle.UNIFORM, oracle.STRATIFIED, oracle.SEMI_STRATIFIED, oracle.OBSERVED]
+    for case in range(40):
+        d = int(rng.integers(2, 9))
+        dims = tuple(int(n) for n in rng.integers(1, 7, d))
+        while math.prod(dims) < 24:
+            dims = tuple(n + 1 for n in dims)
+        kind = kinds[case % 4]
+        seed, problem = (int(v) * 2 + 1 for v in rng.integers(0, 2**63, 2, dtype=np.int64))  # full 64-bit words
+        stream = 2**64 - 1 if case % 7 == 0 else int(rng.integers(0, 2**62))
+        p = 0 if kind in (oracle.UNIFORM, oracle.OBSERVED) or case % 5 == 0 else int(rng.integers(1, 40))
+        q = 0 if case % 5 == 1 else int(rng.integers(1, 60))
+        if kind in (oracle.UNIFORM, oracle.OBSERVED):
+            X = rng.standard_normal(dims)
+            if kind == oracle.OBSERVED:
+                v = rng.random(dims) * (rng.random(dims) >= rng.uniform(0.0, 0.8))
+                v.reshape(-1)[0] = 1.0  # at least one observed entry
+                S = oracle.sample(oracle.Tensor(dims, dense=X, weights=v), kind, 0, q, seed, stream, problem=problem)
+                twin = twin_observed(dims, X, v, q, seed, stream, problem=problem)
+            else:
+                S = oracle.sample(oracle.Tensor(dims, dense=X), kind, 0, q, seed, stream, problem=problem)
+                twin = twin_sample(dims, X, None, None, kind, 0, q, seed, stream, problem=problem)
+        else:
+            X, coo, vals = sparse_problem(dims, float(rng.uniform(0.05, 0.6)), case, binary=bool(case % 2))
+            if len(coo) == 0 or len(coo) == math.prod(dims):
+                continue
+            T = oracle.Tensor(dims, coo=coo, vals=vals)
+            S = oracle.sample(T, kind, p, q, seed, stream, problem=problem)
+            twin = twin_sample(dims, X, coo, vals, kind, p, q, seed, stream, problem=problem)
+        compare(S, twin)
