@@ -82,7 +82,7 @@ def test_gaussian_full_gradient_is_textbook_mttkrp():
 
 
 @pytest.mark.parametrize("loss", LOSSES)
-@pytest.mark.parametrize("dims", [(3, 4, 5), (2, 3, 2, 3), (2, 2, 3, 2, 2)])
+@pytest.mark.parametrize("dims", [(4, 5), (3, 4, 5), (1, 4, 3), (2, 3, 2, 3), (2, 2, 3, 2, 2), (2, 3, 2, 2, 1, 2, 2, 3)])
 def test_full_gradient_matches_einsum(loss, dims):
     X, A = problem(dims, 2, loss, 2)
     G, F = oracle.full_grad(dims, A, loss, X)
@@ -166,8 +166,8 @@ def random_sample_list(dims, X, n, seed):
 
 
 @pytest.mark.parametrize("loss", LOSSES)
-def test_gradient_is_derivative_of_estimate(loss):
-    dims = (3, 4, 2, 3)
+@pytest.mark.parametrize("dims", [(3, 4, 2, 3), (2, 3, 2, 2, 2, 3, 2, 2)], ids=["d4", "d8"])
+def test_gradient_is_derivative_of_estimate(loss, dims):
     X, A = problem(dims, 3, loss, 7)
     S = random_sample_list(dims, X, 40, 8)
     G = oracle.grad(dims, A, loss, S)
