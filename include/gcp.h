@@ -21,8 +21,8 @@
  *    mode k of draw j takes word k % 4 of that block and becomes
  *    randi(n_k) = floor(word * n_k / 2^64).  Tags: 0 uniform draw, 1 nonzero
  *    draw (word 0 gives xi = randi(nnz)), 2 stratified zero candidate,
- *    3 semi-stratified "zero".  The sample set is therefore a pure function
- *    of (seed, problem, stream) and the tensor.
+ *    3 semi-stratified "zero", 4 observed-entry candidate.  The sample set
+ *    is therefore a pure function of (seed, problem, stream) and the tensor.
  */
 #ifndef GCP_GB300_H
 #define GCP_GB300_H
@@ -129,17 +129,19 @@ typedef struct gcp_factors {
     uint16_t *A_bf16[GCP_MAX_MODES];
 } gcp_factors;
 
-/* What to draw (Sections 4.1-4.3).  uniform: s = q draws (p ignored);
-   stratified / semi-stratified: p nonzero draws then q zero draws.
+/* What to draw (Sections 4.1-4.4).  uniform: s = q draws (p ignored);
+   stratified / semi-stratified: p nonzero draws then q zero draws;
+   observed: s = q draws over the entries of nonzero weight (p must be 0).
    oversample is Section 4.2's rho (<= 0 selects 1.1): stratified zeros are
-   examined in batches of ceil(rho q omega / zeta) candidates and the first q
+   examined in batches of ceil(rho q omega / zeta) candidates (observed
+   entries in batches of ceil(rho q omega / |Omega_obs|)) and the first q
    accepted in candidate order are kept; after 64 batches the draw stops
    with GCP_ERR_SAMPLE_SHORTFALL in the device status. */
 typedef struct gcp_sampling {
     int32_t kind;     /* gcp_sampler */
     int32_t reserved;
-    int64_t p;
-    int64_t q;
+    int64_t p;        /* 0 .. 2^40 */
+    int64_t q;        /* 0 .. 2^40 */
     uint64_t seed;
     uint64_t problem; /* second key word: separates independent runs */
     uint64_t stream;  /* counter word: the iteration, or GCP_STREAM_EST */
@@ -219,8 +221,9 @@ gcp_status gcp_destroy(gcp_handle *h);
    Synchronises the device.  host_out: host. */
 gcp_status gcp_get_device_status(gcp_handle *h, int32_t *host_out);
 
-/* Number of entries a sampling spec draws: q for uniform, p + q otherwise.
-   Returns -1 for an invalid spec. */
+/* Number of entries a sampling spec draws: q for uniform and observed,
+   p + q for stratified and semi-stratified.  Returns -1 for an invalid
+   spec. */
 int64_t gcp_sample_count(const gcp_sampling *S);
 
 /* ------------------------------------------------------------------------ */
@@ -232,18 +235,20 @@ int64_t gcp_sample_count(const gcp_sampling *S);
    rejection against the nonzero keys), Alg. 3 (semi-stratified: p
    nonzeros, then q indices from all of Omega without rejection) or the
    observed-entry draw of Section 4.4 (q uniform draws over the entries of
-   nonzero weight, by rejection of the rest) into out, nonzero draws first.  Each entry gets its value x (0 for zeros), its
-   weight w (omega/s, eta/p, zeta/q or omega/q, computed in FP64 on the host
-   and rounded once) and its class.  out->n must equal gcp_sample_count(S).
+   nonzero weight, by rejection of the rest) into out, nonzero draws first.
+   Each entry gets its value x (0 for zeros), its weight w (omega/s, eta/p,
+   zeta/q, omega/q or (|Omega_obs|/q) v_i, computed in FP64 and rounded
+   once) and its class.  out->n must equal gcp_sample_count(S).
    stratified needs a sparse X with prod(dims) < 2^64 (else
    GCP_ERR_UNSUPPORTED); uniform over a sparse X looks each drawn index up
    among the nonzeros (value or 0; also prod(dims) < 2^64); uniform over a
-   dense X with entry weights gives the draw weight (omega/s) v_i.  May allocate library
-   scratch on the first stratified or observed call (cudaMalloc), and the
-   first observed call reads the count of entries of nonzero weight back to
-   the host: make that first call (or gcp_reserve) before any stream
-   capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
-   the device status; the unfilled zero slots then hold weight 0. */
+   dense X with entry weights gives the draw weight (omega/s) v_i; observed
+   needs a dense X with weights and p = 0 (else GCP_ERR_INVALID_ARG).  May
+   allocate library scratch on the first stratified or observed call
+   (cudaMalloc), and the first observed call reads the count of entries of
+   nonzero weight back to the host: make that first call (or gcp_reserve)
+   before any stream capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
+   the device status; the unfilled slots then hold weight 0. */
 gcp_status gcp_sample(gcp_handle *h, const gcp_sampling *S, const gcp_samples *out,
                       gcp_stream_t stream);
 
@@ -266,7 +271,8 @@ gcp_status gcp_reserve(gcp_handle *h, const gcp_sampling *S, gcp_stream_t stream
    fresh gradient -- gcp_adam_step leaves it zeroed).  For every drawn entry
    i: m_i = sum_j prod_k A_k(i_k, j) (Eq. (1.1)); y_i = w g(x_i, m_i), or
    w [g(x_i, m_i) - g(0, m_i)] for a semi-stratified nonzero; and for every
-   k, G_k(i_k, :) += y_i * prod_{l != k} A_l(i_l, :).
+   k, G_k(i_k, j) += y_i * prod_{l != k} A_l(i_l, j) for the columns
+   j < rank (the padding columns of G are not written).
    Exactly one of S and list is non-NULL:
      S    -- draws generated inside the kernel from the spec (fused
              sampling, nothing materialised except stratified zeros, which
@@ -280,7 +286,9 @@ gcp_status gcp_reserve(gcp_handle *h, const gcp_sampling *S, gcp_stream_t stream
    allocated on the first call that needs them (cudaMalloc: make that call
    before any stream capture) and are shared by every call on this handle,
    so calls on one handle must not overlap on the GPU.
-   Errors: GCP_ERR_INVALID_ARG; kernel-side shortfall as in gcp_sample. */
+   Errors: GCP_ERR_INVALID_ARG (a bad loss, spec, list or factor layout, a
+   misaligned G), GCP_ERR_NO_MEMORY (replica slabs, scratch), GCP_ERR_CUDA;
+   kernel-side shortfall as in gcp_sample. */
 gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
                     const gcp_sampling *S, const gcp_samples *list,
                     const int64_t *stream_dev, float *const G[GCP_MAX_MODES],
@@ -289,12 +297,16 @@ gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
 /* The full (non-stochastic) gradient G_k = Y_(k) Z_k of a dense X
    (Eq. (4.2); with entry weights, Eq. (4.5)): every index of Omega taken once
    with weight 1 (or v_i) through the gradient kernel, accumulated into G as
-   gcp_grad does.  O(r prod(dims)) work: for moderate tensors. */
+   gcp_grad does.  O(r prod(dims)) work: for moderate tensors.
+   Errors: GCP_ERR_INVALID_ARG (a sparse X, a bad loss or layout) and as
+   gcp_grad. */
 gcp_status gcp_full_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss, float *const G[GCP_MAX_MODES],
                          gcp_stream_t stream);
 
 /* The exact objective F(X, M) of Eq. (1.2) (weighted: Eq. (4.5)) of a dense X
-   over every index, FP32 terms summed in FP64, into *out_dev. */
+   over every index, FP32 terms summed in FP64, into *out_dev (one device
+   double, 8-byte aligned).  Errors: GCP_ERR_INVALID_ARG (a sparse X, a bad
+   loss, layout or out_dev), GCP_ERR_NO_MEMORY, GCP_ERR_CUDA. */
 gcp_status gcp_full_loss(gcp_handle *h, const gcp_factors *F, gcp_loss loss, double *out_dev, gcp_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
@@ -304,7 +316,10 @@ gcp_status gcp_full_loss(gcp_handle *h, const gcp_factors *F, gcp_loss loss, dou
 /* F-hat = sum over the fixed list of w f(x, m) (w [f(x,m) - f(0,m)] for
    semi-stratified nonzeros), each term in FP32, summed in FP64 in a fixed
    order (deterministic for a given list), written to *out_dev (device,
-   one double).  Uses library scratch for the per-block partial sums. */
+   one double, 8-byte aligned).  Uses library scratch for the per-block
+   partial sums (allocated on the first call: make it before any stream
+   capture).  Errors: GCP_ERR_INVALID_ARG (a bad loss, list, layout or
+   out_dev), GCP_ERR_NO_MEMORY, GCP_ERR_CUDA. */
 gcp_status gcp_loss_est(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
                         const gcp_samples *list, double *out_dev, gcp_stream_t stream);
 
@@ -359,7 +374,9 @@ gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
    gcp_grad followed by gcp_adam_step up to the summation order.  Between
    the two kernels state->t has already advanced (the gradient kernel does
    it, so that the Adam kernel's blocks need not wait for one another); on
-   return both t and iter have advanced by one, as with gcp_adam_step. */
+   return both t and iter have advanced by one, as with gcp_adam_step.
+   Errors: as gcp_grad and gcp_adam_step, checked before either kernel is
+   launched. */
 gcp_status gcp_iteration(gcp_handle *h, const gcp_factors *F, gcp_loss loss, const gcp_sampling *S,
                          const int64_t *stream_dev, float *const G[GCP_MAX_MODES], float *const B[GCP_MAX_MODES],
                          float *const C[GCP_MAX_MODES], const gcp_adam_params *prm, gcp_adam_state *state,
@@ -367,7 +384,9 @@ gcp_status gcp_iteration(gcp_handle *h, const gcp_factors *F, gcp_loss loss, con
 
 /* Saves the epoch-start copy of {A, B, C} into {SA, SB, SC} (same layouts)
    and sets F_old = F (the "save copies" step that opens each epoch of
-   Alg. 4).  Call once after the first loss estimate. */
+   Alg. 4).  Call once after the first loss estimate.  Errors:
+   GCP_ERR_INVALID_ARG (a bad layout, NULL or misaligned arrays or state),
+   GCP_ERR_CUDA. */
 gcp_status gcp_epoch_begin(const gcp_factors *F, int32_t d, const int64_t *dims,
                            float *const B[GCP_MAX_MODES], float *const C[GCP_MAX_MODES],
                            float *const SA[GCP_MAX_MODES], float *const SB[GCP_MAX_MODES],
@@ -379,7 +398,9 @@ gcp_status gcp_epoch_begin(const gcp_factors *F, int32_t d, const int64_t *dims,
    sets F = F_old, t -= tau, alpha *= nu, bad += 1, done = (bad > kappa);
    otherwise accepts, copying {A, B, C} into {SA, SB, SC} and setting
    F_old = F for the next epoch.  An equal estimate is accepted.  All on the
-   device; graph-capturable. */
+   device; graph-capturable.  A non-finite F also records GCP_ERR_NONFINITE
+   in state->status.  Errors: as gcp_epoch_begin, and a NULL ep, tau < 0 or
+   kappa < 0. */
 gcp_status gcp_epoch_end(const gcp_factors *F, int32_t d, const int64_t *dims,
                          float *const B[GCP_MAX_MODES], float *const C[GCP_MAX_MODES],
                          float *const SA[GCP_MAX_MODES], float *const SB[GCP_MAX_MODES],
@@ -421,8 +442,9 @@ typedef struct gcp_batch gcp_batch; /* opaque: the device-side problem table */
 
 /* Validates count problems (host array) and uploads their table to device
    memory owned by the batch (cudaMalloc; waits for the stream).  Errors:
-   GCP_ERR_INVALID_ARG for any invalid problem (sparse X, d > 4, a
-   non-uniform spec, misaligned pointers), GCP_ERR_NO_MEMORY. */
+   GCP_ERR_INVALID_ARG for any invalid problem (sparse X, d outside 2..4,
+   entry weights, a non-uniform spec, misaligned pointers) or count outside
+   1..1024, GCP_ERR_NO_MEMORY. */
 gcp_status gcp_batch_create(gcp_batch **out, const gcp_batch_problem *problems, int32_t count, gcp_stream_t stream);
 gcp_status gcp_batch_destroy(gcp_batch *b);
 
