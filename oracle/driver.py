@@ -25,7 +25,11 @@ EST_STREAM = 0xFFFFFFFFFFFFFFFF  # the Philox stream word of the fixed estimate 
 
 def gcp_adam(X, factors0, loss, kind, p, q, est_p, est_q, seed, est_seed,
              alpha=0.01, beta1=0.9, beta2=0.999, eps=1e-8, tau=1000, kappa=1, nu=0.1,
-             lower=-math.inf, max_epochs=1000, problem=0, log=None):
+             lower=-math.inf, max_epochs=1000, problem=0, log=None, first_iter=0):
+    """Runs Alg. 4 from factors0 and returns (factors, history of F-hat per
+    epoch).  first_iter is the stream word of the first iteration's draws
+    (0 for a run that starts fresh; tests use it to start a run where another
+    run's draws stand)."""
     dims = X.dims
     rank = factors0[0].shape[1]
     A = concat_factors(factors0).copy()
@@ -36,7 +40,7 @@ def gcp_adam(X, factors0, loss, kind, p, q, est_p, est_q, seed, est_seed,
     history = [F]
     c = 0
     t = 0
-    it = 0
+    it = first_iter
     epochs = 0
     while c <= kappa and epochs < max_epochs:
         saved = (A.copy(), B.copy(), C.copy())

@@ -26,10 +26,10 @@ def problem():
     return oracle.Tensor(DIMS, dense=X), A0
 
 
-def run(XO, A0, alpha, kappa=3, nu=0.5, max_epochs=30):
+def run(XO, A0, alpha, kappa=3, nu=0.5, max_epochs=30, first_iter=0):
     logs = []
     A, hist = gcp_adam(XO, A0, oracle.GAUSSIAN, oracle.UNIFORM, 0, 20, 0, 30, 5, 6, alpha=alpha, tau=TAU,
-                       kappa=kappa, nu=nu, max_epochs=max_epochs, log=logs.append)
+                       kappa=kappa, nu=nu, max_epochs=max_epochs, log=logs.append, first_iter=first_iter)
     return A, hist, logs
 
 
@@ -82,3 +82,35 @@ def test_every_epoch_failing_returns_the_initial_factors():
     assert all(F == hist[0] for F in hist)
     for a, a0 in zip(A, A0):
         np.testing.assert_array_equal(a, a0)
+
+
+def test_retried_epoch_draws_new_samples():
+    """With nu = 1 a retried epoch starts from exactly the state of the failed
+    one (factors, moments, t, alpha); only the draws can differ.  The stream
+    word counts every iteration ever run, so a retry eventually succeeds where
+    a wound-back stream would repeat the same failure forever."""
+    XO, A0 = problem()
+    _, _, logs = run(XO, A0, 0.3, kappa=5, nu=1.0, max_epochs=12)
+    failed = next(r for r in logs if r["bad"] == 1)  # holds the epoch-start t and F
+    retries = logs[failed["epoch"]:]
+    accepted = next((r for r in retries if r["t"] > failed["t"]), None)
+    assert accepted is not None, "no retry of the failed epoch was accepted"
+    assert accepted["t"] == failed["t"] + TAU and accepted["F"] < failed["F"]
+    assert all(r["t"] == failed["t"] for r in retries[:retries.index(accepted)])  # the retries in between failed
+
+
+def test_failed_epochs_leave_no_trace_but_alpha_and_the_stream():
+    """Failed epochs from the very start: once one succeeds, the run must be
+    exactly a fresh run from the initial factors (moments zero, t = 0) at the
+    reduced alpha whose draws start where the failed epochs' draws ended.  A
+    moment, step count or factor left over from a failed epoch changes it."""
+    XO, A0 = problem()
+    _, _, logs = run(XO, A0, 1e3, kappa=10, nu=0.1)
+    accepted = next(r for r in logs if r["t"] > 0)
+    fails = accepted["epoch"] - 1
+    assert fails >= 2 and accepted["bad"] == fails
+    A_run, _, _ = run(XO, A0, 1e3, kappa=10, nu=0.1, max_epochs=accepted["epoch"])
+    A_fresh, _, logs_fresh = run(XO, A0, accepted["alpha"], kappa=10, nu=0.1, max_epochs=1, first_iter=fails * TAU)
+    assert logs_fresh[0]["bad"] == 0 and logs_fresh[0]["F"] == accepted["F"]
+    for a, b in zip(A_run, A_fresh):
+        np.testing.assert_array_equal(a, b)
