@@ -67,6 +67,11 @@ def test_projection():
     oracle.adam_step(A, B, C, np.array([1.0, 1.0, 1.0]), 0.01, 0.9, 0.999, 1e-8, 0.0, 0)
     assert np.all(A >= 0.0)
     assert A[0] == 0.0 and A[2] == 0.0 and A[1] == pytest.approx(0.5 - 0.01, rel=1e-6)
+    # a nonzero bound: entries below it land on it, not on zero
+    A = np.array([0.3, 0.5, -0.2])
+    B, C = np.zeros(3), np.zeros(3)
+    oracle.adam_step(A, B, C, np.array([1.0, -1.0, 1.0]), 0.01, 0.9, 0.999, 1e-8, 0.295, 0)
+    assert A[0] == 0.295 and A[2] == 0.295 and A[1] == pytest.approx(0.5 + 0.01, rel=1e-6)
 
 
 def test_planted_recovery_gaussian():

@@ -114,3 +114,15 @@ def test_failed_epochs_leave_no_trace_but_alpha_and_the_stream():
     assert logs_fresh[0]["bad"] == 0 and logs_fresh[0]["F"] == accepted["F"]
     for a, b in zip(A_run, A_fresh):
         np.testing.assert_array_equal(a, b)
+
+
+def test_an_equal_estimate_is_accepted():
+    """alpha = 0 leaves every factor where it is, so each epoch's estimate
+    equals the previous one: equal is no increase, every epoch is accepted."""
+    XO, A0 = problem()
+    A, hist, logs = run(XO, A0, 0.0, kappa=0, max_epochs=3)
+    assert [r["bad"] for r in logs] == [0, 0, 0]
+    assert [r["t"] for r in logs] == [TAU, 2 * TAU, 3 * TAU]
+    assert len(set(hist)) == 1
+    for a, a0 in zip(A, A0):
+        np.testing.assert_array_equal(a, a0)

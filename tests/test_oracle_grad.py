@@ -103,6 +103,7 @@ def test_weighted_full_gradient():
     Y = v * numpy_g(oracle.BERNOULLI_LOGIT, X, M)
     for k in range(3):
         np.testing.assert_allclose(G[k], einsum_mttkrp(Y, A, k), rtol=1e-11, atol=1e-12)
+    assert F == pytest.approx((v * numpy_f(oracle.BERNOULLI_LOGIT, X, M)).sum(), rel=1e-12)
 
 
 @pytest.mark.parametrize("loss", LOSSES)
@@ -272,6 +273,15 @@ def test_abs_scales_bound_the_sums():
     Gabs = oracle.grad_abs(dims, Apos, oracle.GAUSSIAN, Spos)
     for g, ga in zip(G, Gabs):
         np.testing.assert_allclose(-g, ga, rtol=1e-12)
+    # Poisson-log terms e^m - x m change sign: the scale is the sum of the
+    # single-entry magnitudes, strictly above |F-hat|
+    Xp = np.random.default_rng(42).poisson(3.0, dims).astype(float)
+    Sp = Samples(S.idx, Xp[tuple(S.idx.T)], S.w, np.full(S.n, oracle.CLS_UNIFORM))
+    terms = [oracle.loss_estimate(dims, A, oracle.POISSON_LOG,
+                                  Samples(Sp.idx[e:e + 1], Sp.x[e:e + 1], Sp.w[e:e + 1], Sp.cls[e:e + 1]))
+             for e in range(Sp.n)]
+    assert min(terms) < 0 < max(terms)
+    assert oracle.loss_abs(dims, A, oracle.POISSON_LOG, Sp) == pytest.approx(np.abs(terms).sum(), rel=1e-12)
 
 
 def numpy_g_positive(loss, X, M):

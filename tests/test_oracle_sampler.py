@@ -251,3 +251,36 @@ def test_random_configurations_match_twin():
             S = oracle.sample(T, kind, p, q, seed, stream, problem=problem)
             twin = twin_sample(dims, X, coo, vals, kind, p, q, seed, stream, problem=problem)
         compare(S, twin)
+
+
+@pytest.mark.parametrize("kind", [oracle.STRATIFIED, oracle.OBSERVED])
+def test_rejection_stops_after_exactly_64_batches(kind):
+    """One acceptable entry in 10^4 and q = 1: the first acceptance comes at
+    candidate c*.  Batches of b candidates find it iff 64 b > c* (the cap is
+    64 batches), so a b with 64 b <= c* < 65 b falls short and b + 1 does not
+    once 64 (b + 1) > c*."""
+    dims = (10, 10, 100)
+    omega = math.prod(dims)
+    lone = (3, 7, 42)
+    for seed in range(1, 200):
+        if kind == oracle.STRATIFIED:
+            coo = np.array([c for c in np.ndindex(*dims) if c != lone])
+            T = oracle.Tensor(dims, coo=coo, vals=np.ones(len(coo)))
+            p = 1
+        else:
+            v = np.zeros(dims)
+            v[lone] = 1.0
+            T = oracle.Tensor(dims, dense=np.ones(dims), weights=v)
+            p = 0
+        c_star = oracle.sample(T, kind, p, 1, seed, 0, rho=1.0).candidates_used - 1
+        b = -(-(c_star + 1) // 65)  # ceil((c* + 1) / 65): 65 b > c*
+        if 64 * b <= c_star:
+            break
+    else:
+        pytest.fail("no seed puts the first acceptance at the cap boundary")
+    rho = lambda batch: (batch - 0.5) / omega  # ceil(rho q omega / 1) = batch
+    with pytest.raises(RuntimeError, match="short"):
+        oracle.sample(T, kind, p, 1, seed, 0, rho=rho(b))
+    ok_b = -(-(c_star + 1) // 64)
+    S = oracle.sample(T, kind, p, 1, seed, 0, rho=rho(ok_b))
+    assert S.candidates_used == c_star + 1 and tuple(S.idx[-1]) == lone
