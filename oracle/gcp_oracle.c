@@ -20,7 +20,31 @@
  *     takes word k % 4 of that block;
  *   - randi(n) = floor(W * n / 2^64) for a 64-bit word W (multiply-high).
  *
- * Parity status of each function is stated in its comment.
+ * Parity status: every function is pinned, by a check that does not go
+ * through this file's own formula (tests/):
+ *   orc_philox4x64          numpy.random.Philox, 56 counters and keys
+ *   orc_randi               the defining partition property at exact
+ *                           interval boundaries, in Python integers
+ *   orc_draw_*, orc_sample, a pure-Python twin (numpy's Philox, Python
+ *   orc_linear_key,         integers, a Python set and dict) for all four
+ *   orc_sparse_value,       samplers, 40 random configurations of 2-8
+ *   orc_count_observed      modes, candidate counts, the shortfall and the
+ *                           exact 64-batch cap
+ *   orc_sorted_keys,        every linear key of a small dense tensor
+ *   orc_is_nonzero
+ *   orc_loss_f, orc_loss_g  scipy's likelihoods, closed forms, central
+ *                           differences
+ *   orc_model_value,        numpy.einsum MTTKRP of the full gradient (also
+ *   orc_full_grad           the textbook 2 (M - X)_(k) Z_k), weighted form
+ *   orc_entry_y/f,          enumeration identities (each index once, weight
+ *   orc_grad_from_samples,  1, gives the full gradient and objective),
+ *   orc_loss_from_samples   finite differences of the estimate, Monte-Carlo
+ *                           unbiasedness
+ *   orc_*_abs_from_samples  bounds and equalities with sign-definite terms
+ *   orc_adam_step           torch.optim.Adam, the closed-form first step,
+ *                           the second step's bias correction, projection
+ * and tests/test_pins_catch_mistakes.py requires each of 59 planted mistakes
+ * in this file to fail one of these pins.
  */
 #include <math.h>
 #include <stdint.h>
@@ -455,8 +479,7 @@ double orc_entry_y(int loss, int cls, double x, double m, double w)
 }
 
 /* The loss-estimate term of a drawn entry (Eqs. (5.1)-(5.2); the semi-     */
-/* stratified */
-/* form is this library's reading, built like Alg. 3's gradient).          */
+/* stratified form is this library's reading, built like Alg. 3's gradient). */
 double orc_entry_f(int loss, int cls, double x, double m, double w)
 {
     if (cls == ORC_CLS_SEMI_NZ) return w * (orc_loss_f(loss, x, m) - orc_loss_f(loss, 0.0, m));
@@ -552,8 +575,7 @@ int orc_grad_abs_from_samples(int d, const int64_t *dims, int rank, const double
 /* Full (non-stochastic) gradient and objective over all of Omega of a     */
 /* dense tensor: G_k = Y_(k) Z_k with y_i = v_i g(x_i, m_i) (Eqs. (4.1),    */
 /* (4.2) and the weighted form (4.5); v = NULL means all weights 1).        */
-/* Enumerates   */
-/* every index; for tiny tensors only.                                      */
+/* Enumerates every index; for tiny tensors only.                           */
 /* ------------------------------------------------------------------------ */
 
 int orc_full_grad(int d, const int64_t *dims, int rank, const double *A, int loss,
