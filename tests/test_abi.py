@@ -92,3 +92,99 @@ def test_ctypes_layouts_match_the_c_compiler(tmp_path):
         if hasattr(gcp, n):
             assert ctypes.sizeof(getattr(gcp, n)) == size, n
     assert dict(zip(names, sizes))["gcp_adam_state"] == 64
+
+
+def _no_gpu():
+    try:
+        import torch
+        return not torch.cuda.is_available()
+    except ImportError:
+        return True
+
+
+@pytest.mark.skipif(not _no_gpu(), reason="hands the library fake device addresses: CPU-only machines")
+def test_invalid_descriptors_rejected_before_any_launch(lib_path):
+    """Each call gets one invalid field (all else well-formed, with fake but
+    aligned device addresses that nothing dereferences) and must return
+    GCP_ERR_INVALID_ARG from its host-side checks.  Without a GPU a call
+    that got past them would fail in CUDA instead (GCP_ERR_CUDA)."""
+    from paper_1906_01687_gb300 import gcp
+    lib, BAD = gcp._lib, gcp.ERR_INVALID_ARG
+    base = 1 << 20
+    dims3 = (ctypes.c_int64 * 3)(4, 5, 6)
+
+    def factors(rank=3, ld=4, misalign=0):
+        F = gcp.gcp_factors()
+        F.rank, F.ld = rank, ld
+        for k in range(3):
+            F.A[k] = base * (k + 1) + misalign
+        return F
+
+    def p8(offset=0, null_mode=None):
+        a = gcp._P8()
+        for k in range(3):
+            a[k] = None if k == null_mode else base * (10 + k) + offset
+        return a
+
+    prm = gcp.gcp_adam_params(0.9, 0.999, 1e-8, float("-inf"), 1, 0)
+    state = ctypes.c_void_p(base * 50)
+
+    def adam(F=None, d=3, dims=dims3, G=None, prm_=prm, st=state):
+        return lib.gcp_adam_step(ctypes.byref(F or factors()), d, dims, G or p8(), p8(), p8(), ctypes.byref(prm_), st,
+                                 None)
+
+    assert adam() == gcp.ERR_CUDA  # the control: well-formed, so it reaches CUDA, which has no device here
+    assert adam(d=0) == BAD and adam(d=9) == BAD
+    assert adam(F=factors(rank=0)) == BAD and adam(F=factors(rank=257, ld=260)) == BAD
+    assert adam(F=factors(rank=5, ld=4)) == BAD and adam(F=factors(ld=6)) == BAD
+    assert adam(F=factors(misalign=4)) == BAD  # rows must be 16-byte aligned
+    assert adam(dims=(ctypes.c_int64 * 3)(4, 0, 6)) == BAD
+    assert adam(dims=(ctypes.c_int64 * 3)(4, 2**31, 6)) == BAD
+    assert adam(G=p8(null_mode=1)) == BAD and adam(G=p8(offset=8)) == BAD
+    assert adam(prm_=gcp.gcp_adam_params(1.0, 0.999, 1e-8, 0.0, 1, 0)) == BAD
+    assert adam(prm_=gcp.gcp_adam_params(0.9, -0.1, 1e-8, 0.0, 1, 0)) == BAD
+    assert adam(prm_=gcp.gcp_adam_params(0.9, 0.999, -1.0, 0.0, 1, 0)) == BAD
+    assert adam(st=ctypes.c_void_p(base * 50 + 4)) == BAD and adam(st=None) == BAD
+    # a factor set of 2^31 float4 chunks or more
+    assert adam(dims=(ctypes.c_int64 * 3)(2**31 - 1, 2**31 - 1, 4), F=factors(rank=8, ld=8)) == BAD
+
+    ep = gcp.gcp_epoch_params(10, 0.1, 1)
+    assert lib.gcp_epoch_end(ctypes.byref(factors()), 3, dims3, p8(), p8(), p8(), p8(), p8(),
+                             ctypes.byref(gcp.gcp_epoch_params(-1, 0.1, 1)), state, None) == BAD
+    assert lib.gcp_epoch_end(ctypes.byref(factors()), 3, dims3, p8(), p8(), p8(), p8(), p8(),
+                             ctypes.byref(gcp.gcp_epoch_params(10, 0.1, -1)), state, None) == BAD
+    assert lib.gcp_epoch_end(ctypes.byref(factors()), 3, dims3, p8(), p8(), p8(), p8(), p8(null_mode=2),
+                             ctypes.byref(ep), state, None) == BAD
+    assert lib.gcp_state_init(ctypes.c_void_p(base + 4), ctypes.c_float(0.1), None) == BAD
+
+    # the handle-free loss estimate
+    L = gcp.gcp_samples()
+    L.n = 100
+    for k in range(3):
+        L.idx[k] = base * (20 + k)
+    L.x, L.w, L.cls = base * 30, base * 31, base * 32
+    out = ctypes.c_void_p(base * 40)
+
+    def noalloc(d=3, F=None, loss=0, L_=L, out_=out):
+        return lib.gcp_loss_est_noalloc(d, ctypes.byref(F or factors()), loss, ctypes.byref(L_), out_, None)
+
+    assert noalloc() == gcp.ERR_CUDA
+    assert noalloc(d=0) == BAD and noalloc(loss=7) == BAD and noalloc(loss=-1) == BAD
+    assert noalloc(F=factors(ld=3)) == BAD and noalloc(out_=ctypes.c_void_p(base * 40 + 4)) == BAD
+    L2 = gcp.gcp_samples.from_buffer_copy(L)
+    L2.n = 262_145  # more than one entry per thread of 1024 blocks of 256
+    assert noalloc(L_=L2) == BAD
+    L3 = gcp.gcp_samples.from_buffer_copy(L)
+    L3.idx[2] = None
+    assert noalloc(L_=L3) == BAD
+
+    # handles and batches
+    assert lib.gcp_profile(None, 1, 16) == BAD
+    assert lib.gcp_set_tuning(None, None) == BAD
+    assert lib.gcp_get_device_status(None, None) == BAD
+    b = ctypes.c_void_p()
+    assert lib.gcp_batch_create(ctypes.byref(b), None, 1, None) == BAD
+    probs = (gcp.gcp_batch_problem * 1)()
+    assert lib.gcp_batch_create(ctypes.byref(b), probs, 0, None) == BAD
+    assert lib.gcp_batch_create(ctypes.byref(b), probs, 1025, None) == BAD
+    assert lib.gcp_batch_create(ctypes.byref(b), probs, 1, None) == BAD  # an all-zero problem: d = 0
