@@ -188,3 +188,64 @@ def test_invalid_descriptors_rejected_before_any_launch(lib_path):
     assert lib.gcp_batch_create(ctypes.byref(b), probs, 0, None) == BAD
     assert lib.gcp_batch_create(ctypes.byref(b), probs, 1025, None) == BAD
     assert lib.gcp_batch_create(ctypes.byref(b), probs, 1, None) == BAD  # an all-zero problem: d = 0
+
+
+def header_prototypes():
+    """{name: [parameter declarations]} of every function include/gcp.h declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b([a-z_0-9]+\s*\**)\s*\b(gcp_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = [p.strip() for p in m.group(3).replace("\n", " ").split(",")]
+        protos[m.group(2)] = [] if params == ["void"] else params
+        RETURNS[m.group(2)] = m.group(1).replace(" ", "")
+    return protos
+
+
+RETURNS = {}
+
+
+def test_binding_signatures_follow_the_header(lib_path):
+    """Every ctypes signature has the header's parameter count, and each
+    parameter the ctypes type its C type calls for."""
+    from paper_1906_01687_gb300 import gcp
+    P = ctypes.POINTER
+    protos = header_prototypes()
+    assert set(protos) == set(gcp._SIGS)
+
+    def expected(decl):
+        decl = re.sub(r"\bconst\b", "", decl)
+        decl = re.sub(r"\s+", " ", decl).strip()
+        ty = decl.rsplit(" ", 1)[0] if not decl.endswith("]") else decl.split("[")[0].rsplit(" ", 1)[0]
+        if decl.endswith("[GCP_MAX_MODES]"):
+            return {gcp._P8}
+        stars = decl.count("*")
+        base = ty.replace("*", "").strip()
+        if stars == 2:
+            return {P(ctypes.c_void_p)}
+        if stars == 1:
+            structs = {"gcp_factors": gcp.gcp_factors, "gcp_sampling": gcp.gcp_sampling,
+                       "gcp_samples": gcp.gcp_samples, "gcp_adam_params": gcp.gcp_adam_params,
+                       "gcp_epoch_params": gcp.gcp_epoch_params, "gcp_tensor": gcp.gcp_tensor,
+                       "gcp_tuning": gcp.gcp_tuning, "gcp_launch_info": gcp.gcp_launch_info,
+                       "gcp_batch_problem": gcp.gcp_batch_problem}
+            if base in structs:
+                return {P(structs[base])}
+            if base in ("int32_t",):
+                return {P(ctypes.c_int32), ctypes.c_void_p}
+            if base in ("int64_t",):
+                return {P(ctypes.c_int64), ctypes.c_void_p}
+            if base == "double":
+                return {P(ctypes.c_double), ctypes.c_void_p}
+            return {ctypes.c_void_p}  # opaque handles, device buffers, the optimizer state
+        scalars = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "float": ctypes.c_float,
+                   "gcp_loss": ctypes.c_int, "gcp_status": ctypes.c_int, "gcp_stream_t": ctypes.c_void_p,
+                   "uint64_t": ctypes.c_uint64}
+        return {scalars[base]}
+
+    ret = {"gcp_status": {ctypes.c_int}, "int64_t": {ctypes.c_int64}, "char*": {ctypes.c_char_p}}
+    for name, params in protos.items():
+        args, res = gcp._SIGS[name]
+        assert res in ret[RETURNS[name]], f"{name} returns {RETURNS[name]}, bound as {res}"
+        assert len(args) == len(params), name
+        for k, (decl, got) in enumerate(zip(params, args)):
+            assert got in expected(decl), f"{name} parameter {k} ({decl}): {got}"
