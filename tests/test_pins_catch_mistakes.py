@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes: each mutant below plants one
 (a wrong constant, sign, index, weight, class, bound or dropped term, or a
-slip in the epoch logic of Alg. 4) in a copy of oracle/gcp_oracle.c or
-oracle/driver.py, on the CPU, and the oracle's pin tests
+slip in the epoch logic of Alg. 4 or in App. E's score) in a copy of
+oracle/gcp_oracle.c, oracle/driver.py or oracle/score.py, on the CPU, and the oracle's pin tests
 (tests/test_oracle_*.py, tests/test_paper_facts.py) must fail on it.  The
 product library is not involved.  A mutant whose site is no longer in the
 source fails this test too, so the list follows the oracle as it changes.
@@ -210,6 +210,13 @@ DRIVER_MUTANTS = [
     ('stream per epoch instead of per iteration', '            it += 1\n', '            it += 0\n'),
 ]
 
+# and for App. E's cosine score of oracle/score.py
+SCORE_MUTANTS = [
+    ('score not averaged over components', 'return float(best / r)', 'return float(best)'),
+    ('estimate columns not normalised', 'bn = b / np.linalg.norm(b, axis=0, keepdims=True)', 'bn = b'),
+    ('assignment minimises instead of maximising', 'linear_sum_assignment(-prod)', 'linear_sum_assignment(prod)'),
+]
+
 
 def pin_tests():
     tests = sorted(f for f in os.listdir(os.path.join(ROOT, "tests")) if f.startswith("test_oracle_"))
@@ -236,7 +243,8 @@ def run_mutant(workdir, rel, src, mutant):
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     jobs = []
     for rel, mutants in ((os.path.join("oracle", "gcp_oracle.c"), MUTANTS),
-                         (os.path.join("oracle", "driver.py"), DRIVER_MUTANTS)):
+                         (os.path.join("oracle", "driver.py"), DRIVER_MUTANTS),
+                         (os.path.join("oracle", "score.py"), SCORE_MUTANTS)):
         with open(os.path.join(ROOT, rel)) as f:
             src = f.read()
         missing = [m[0] for m in mutants if m[1] not in src]
