@@ -284,3 +284,25 @@ def test_rejection_stops_after_exactly_64_batches(kind):
     ok_b = -(-(c_star + 1) // 64)
     S = oracle.sample(T, kind, p, 1, seed, 0, rho=rho(ok_b))
     assert S.candidates_used == c_star + 1 and tuple(S.idx[-1]) == lone
+
+
+def test_first_batch_success_rate_is_binomial():
+    """App. B's oversampling argument: a batch of b candidates, each a zero
+    with probability zeta / omega, holds at least q zeros with probability
+    P(Binomial(b, zeta / omega) >= q).  Over many seeds the share of runs
+    that stop within the first batch matches it (scipy's binomial tail)."""
+    from scipy import stats
+    dims = (20, 20, 20)
+    omega = math.prod(dims)
+    rng = np.random.default_rng(77)
+    keys = rng.choice(omega, omega // 2, replace=False)
+    coo = np.stack(np.unravel_index(keys, dims), axis=1)
+    T = oracle.Tensor(dims, coo=coo, vals=np.ones(len(coo)))
+    q, rho = 200, 1.0
+    batch = math.ceil(rho * q * omega / (omega - len(coo)))
+    p_one = stats.binom.sf(q - 1, batch, (omega - len(coo)) / omega)
+    runs = 600
+    within = sum(oracle.sample(T, oracle.STRATIFIED, 0, q, seed, 0, rho=rho).candidates_used <= batch
+                 for seed in range(runs))
+    sd = math.sqrt(p_one * (1 - p_one) / runs)
+    assert abs(within / runs - p_one) < 5 * sd, (within / runs, p_one)
