@@ -150,7 +150,10 @@ typedef struct gcp_sampling {
 } gcp_sampling;
 
 /* An explicit list of drawn entries, struct of arrays, device memory owned
-   by the caller: idx[k][e] (int32), x[e], w[e] (FP32), cls[e] (gcp_class). */
+   by the caller: idx[k][e] (int32), x[e], w[e] (FP32), cls[e] (gcp_class).
+   A caller-made list must hold 0 <= idx[k][e] < n_k and a valid class: the
+   kernels read the factor rows at these indices without checking them (the
+   library's own lists hold them by construction). */
 typedef struct gcp_samples {
     int64_t n;
     int32_t *idx[GCP_MAX_MODES];
