@@ -98,9 +98,10 @@ typedef enum gcp_class {
 /* The data tensor X (Section 3.2).
    dense  (sparse = 0): vals = prod(dims) FP32 values, row-major, device.
    sparse (sparse = 1): coordinate format; idx[k][e] = i_k of nonzero e
-                        (int32, device), vals = nnz FP32 values or NULL for
-                        an all-ones (binary) tensor.  Positions must be
-                        unique for the stratified sampler's rejection test. */
+                        (int32, device, in [0, n_k): not checked on the
+                        device), vals = nnz FP32 values or NULL for an
+                        all-ones (binary) tensor.  Positions must be unique
+                        for the stratified sampler's rejection test. */
 typedef struct gcp_tensor {
     int32_t d;                        /* modes, 2..8 (one mode has no leave-one-out
                                          product in Eq. (4.3): rejected) */
