@@ -186,8 +186,8 @@ class Tensor:
         self.sparse = coo is not None
         if self.sparse:
             coo = np.asarray(coo)
-            if coo.shape[0] == self.d and coo.shape[1] != self.d:
-                coo = coo.T  # accept SoA input
+            if coo.ndim != 2 or coo.shape[1] != self.d:  # one orientation only: nnz == d would be ambiguous
+                raise ValueError(f"coo must be nnz x d (one row per nonzero), got shape {coo.shape}")
             self.coo = _i64(coo)
             self.nnz = self.coo.shape[0]
             self.vals = None if vals is None else _f64(vals)
