@@ -527,7 +527,8 @@ def large_sparse(torch, gcp, synth, stream, peak, iters=10):
 def forms_bf16(torch, gcp, synth, stream):
     """FP32 vs BF16 factor storage on the count tensor (6186x24x77x32, 5.33M
     nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): gradient
-    throughput and error against the FP64 oracle on the same draws."""
+    throughput, and the gradient's and the loss estimate's errors against the
+    FP64 oracle (at the FP32 factors) on the same draws."""
     import oracle
     from paper_1906_01687_gb300.autotune import autotune, candidates
     dims = (6186, 24, 77, 32)
@@ -538,6 +539,10 @@ def forms_bf16(torch, gcp, synth, stream):
     XO = oracle.Tensor(dims, coo=np.stack([i.astype(np.int64) for i in idx], axis=1), vals=vals.astype(np.float64))
     SO = oracle.sample(XO, oracle.STRATIFIED, 100_000, 100_000, 1687, 0)
     ref = oracle.grad(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SO)
+    # the fixed loss-estimate list (stratified 1e5 + 1e5, the estimate stream)
+    est_spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, 100_000, 100_000, 7, gcp.STREAM_EST)
+    SOe = oracle.sample(XO, oracle.STRATIFIED, 100_000, 100_000, 7, gcp.STREAM_EST)
+    F_ref = oracle.loss_estimate(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SOe)
     out = {"workload": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
            "metric": "entries/s of gcp_grad (zero pass + gradient)"}
     for name, bf16 in (("fp32", False), ("bf16", True)):
@@ -555,6 +560,15 @@ def forms_bf16(torch, gcp, synth, stream):
                         sum(np.linalg.norm(b) ** 2 for b in ref))
         out[name] = {"value": 200_000 / t, "us_per_call": t * 1e6, "grad_rel_err_vs_fp64_oracle": err,
                      "launch": gcp.gcp_get_launch(h, F, 200_000), "tuning": tuned["best"]}
+        try:
+            est = gcp.gcp_sample(h, est_spec, stream=stream)
+            F_dev = torch.zeros(1, dtype=torch.float64, device=G[0].device)
+            gcp.gcp_loss_est(h, F, gcp.LOSS_POISSON_LOG, est, F_dev, stream=stream)
+            stream.synchronize()
+            out[name]["loss_rel_err_vs_fp64_oracle"] = abs(F_dev.item() - F_ref) / abs(F_ref)
+        except Exception as e:  # a reporting extra: record the failure, keep the line
+            out[name]["loss_rel_err_vs_fp64_oracle"] = None
+            out[name]["loss_error"] = repr(e)
     out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
     return out
 
