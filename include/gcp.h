@@ -330,21 +330,25 @@ gcp_status gcp_loss_est(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
 
 /* The loss estimate of gcp_loss_est for callers that cannot allocate device
    memory at the time of the call: it needs no handle and allocates nothing.
-   This entry point has no counterpart in the paper; it exists for callers
-   such as code that enqueues work while a CUDA graph is being captured
-   (where cudaMalloc is not allowed) or hosts whose device memory is owned by
-   another allocator.  Its per-block partial sums live in a file-scope device
-   array of the library: 1024 doubles and a counter (about 8 KB), held by
-   every GPU that loads the library until the process exits.
-   d: modes; F, list: as for gcp_loss_est (device arrays, caller-owned); at
-   most 262,144 listed entries (one per thread of at most 1024 blocks of 256),
-   longer lists return GCP_ERR_INVALID_ARG.  out_dev: one device double.
-   The first call on a device looks up the array's device address and clears
-   its counter (with that device current, synchronising the device): make
-   that first call before any stream capture.  Every call shares the array:
-   calls whose kernels overlap on the GPU (other streams, other threads) race
-   and give wrong results.  Same arithmetic as gcp_loss_est (FP32 terms,
-   FP64 sums); the block count may differ, so the last bits may too. */
+   This entry point has no counterpart in the paper.  It exists for callers
+   that must not call cudaMalloc when they run the estimate: hosts whose
+   device memory is owned by another allocator (a framework's caching
+   allocator that has reserved the GPU's memory) and loops that forbid
+   allocation after start-up, where a cudaMalloc would stall or fail.  Its
+   per-block partial sums live in a file-scope device array of the library:
+   1024 doubles and a counter (about 8 KB), held by every GPU that loads the
+   library until the process exits.
+   d: modes, 2..8; F, list: as for gcp_loss_est (device arrays,
+   caller-owned); at most 262,144 listed entries (one per thread of at most
+   1024 blocks of 256), longer lists return GCP_ERR_INVALID_ARG.  out_dev:
+   one device double.  The first call on a device does a one-time set-up:
+   with that device current it looks up the array's device address
+   (cudaGetSymbolAddress); make that first call before any stream capture.
+   Every call clears the array's counter on the stream before its kernel.
+   Every call shares the array: calls whose kernels overlap on the GPU
+   (other streams, other threads) race and give wrong results.  Same
+   arithmetic as gcp_loss_est (FP32 terms, FP64 sums); the block count may
+   differ, so the last bits may too. */
 gcp_status gcp_loss_est_noalloc(int32_t d, const gcp_factors *F, gcp_loss loss, const gcp_samples *list,
                                 double *out_dev, gcp_stream_t stream);
 

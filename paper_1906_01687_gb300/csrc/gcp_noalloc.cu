@@ -4,10 +4,11 @@
 // The ordinary gcp_loss_est keeps its per-block partial sums in scratch that
 // gcp_create allocated with cudaMalloc.  This variant keeps them in a
 // file-scope device array instead, so it needs no handle and allocates
-// nothing, which suits callers that cannot call cudaMalloc at that point:
-// code enqueuing work while a CUDA graph is being captured, and hosts whose
-// memory budget is owned by another allocator (a framework's caching
-// allocator, a real-time loop that forbids allocation after start-up).
+// nothing.  It serves callers that must not call cudaMalloc when they run
+// the estimate: hosts whose device memory is owned by another allocator (a
+// framework's caching allocator that has reserved the GPU's memory), and
+// loops that forbid allocation after start-up (real-time or latency-bound
+// services), where a cudaMalloc would stall or fail.
 //
 // The array (kNoAllocBlocks partial sums plus a completion ticket, about
 // 8 KB) lives in every GPU that loads this library until the process exits,
@@ -44,13 +45,10 @@ gcp_status scratch_for_current_device(NoAllocScratch** out)
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GCP_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
+        // the array's device address on this device; the array itself starts
+        // zeroed (module load) and every call clears the ticket it uses
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return GCP_ERR_CUDA;
-        // the ticket must start at zero; the kernel's last block leaves it at zero again
-        if (cudaMemset(static_cast<char*>(p) + offsetof(NoAllocScratch, ticket), 0, sizeof(unsigned int)) !=
-            cudaSuccess)
-            return GCP_ERR_CUDA;
-        if (cudaDeviceSynchronize() != cudaSuccess) return GCP_ERR_CUDA;
         g_scratch_addr[dev] = static_cast<NoAllocScratch*>(p);
     }
     *out = g_scratch_addr[dev];
@@ -65,7 +63,7 @@ extern "C" gcp_status gcp_loss_est_noalloc(int32_t d, const gcp_factors* F, gcp_
                                            double* out_dev, gcp_stream_t stream)
 {
     using namespace gcpk;
-    if (d < 1 || d > GCP_MAX_MODES || !F || !list || !out_dev || !aligned_to(out_dev, 8)) return GCP_ERR_INVALID_ARG;
+    if (d < 2 || d > GCP_MAX_MODES || !F || !list || !out_dev || !aligned_to(out_dev, 8)) return GCP_ERR_INVALID_ARG;
     if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
     if (F->rank < 1 || F->rank > 256 || F->ld < F->rank || F->ld % 4 != 0) return GCP_ERR_INVALID_ARG;
     for (int k = 0; k < d; ++k) {
@@ -101,6 +99,7 @@ extern "C" gcp_status gcp_loss_est_noalloc(int32_t d, const gcp_factors* F, gcp_
     a.out = out_dev;
     // one entry per thread: ceil(n / 256) blocks, at most kNoAllocBlocks partial sums
     const int grid = static_cast<int>(list->n > 0 ? (list->n + kNoAllocThreads - 1) / kNoAllocThreads : 1);
+    // the completion ticket starts every call at zero (stream-ordered)
     if (cudaMemsetAsync(&scratch->ticket, 0, sizeof(unsigned int), s) != cudaSuccess) return GCP_ERR_CUDA;
     if (launch_loss(a, F->bf16 != 0, grid, kNoAllocThreads, s) != cudaSuccess) return GCP_ERR_CUDA;
     return GCP_OK;

@@ -2,6 +2,7 @@
 revert of Alg. 4), the BF16-storage form and the autograd form with the
 FP64 oracle, and planted recovery through the device-side GCP-Adam."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -12,6 +13,7 @@ from gpu_util import (BF16_RTOL, GRAD_RTOL, assert_grad_close, f64, gcp, grad_to
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 B1, B2, EPS = float(np.float32(0.9)), float(np.float32(0.999)), float(np.float32(1e-8))
 
@@ -346,18 +348,15 @@ def test_checkpoint_resume_reproduces_run(tmp_path):
     assert (s1["t"], s1["iter"], s1["bad"]) == (s2["t"], s2["iter"], s2["bad"])
 
 
-def test_readme_example_runs():
-    """The README's fitting example, as written, runs and lowers the estimated loss."""
-    from paper_1906_01687_gb300 import gcp as G, synth
-    from paper_1906_01687_gb300.adam import GcpAdam
-    X = synth.dense_small()[0]
-    A0 = synth.initial_guess(X.shape, 3, seed=1, target_norm=float(np.linalg.norm(X)))
-    run = GcpAdam(G.DataTensor.dense(X), A0, G.LOSS_GAUSSIAN, G.SAMPLER_UNIFORM, p=0, q=1000,
-                  est_p=0, est_q=500, seed=1, est_seed=2, tau=100)
-    state = run.fit(max_epochs=50)
-    A = run.factors()
-    assert len(A) == 3 and all(a.shape == (n, 3) for a, n in zip(A, X.shape))
-    assert state["status"] == 0 and math.isfinite(state["F"]) and state["F"] < run.history[0]
+def test_python_example_runs():
+    """The Python example (examples/fit_dense.py), as written, runs and lowers the estimated loss."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("fit_dense", os.path.join(ROOT, "examples", "fit_dense.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    state, history, A = mod.fit(max_epochs=50)
+    assert len(A) == 3 and all(a.shape == (n, 3) for a, n in zip(A, (20, 30, 40)))
+    assert state["status"] == 0 and math.isfinite(state["F"]) and state["F"] < history[0]
 
 
 def test_gcp_adam_with_observed_sampler():
