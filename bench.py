@@ -2,16 +2,25 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Workload: dense 100x100x100x100 FP32 tensor (1e8 entries, 400 MB), planted
-rank 10 plus N(0, 0.01) noise; Gaussian loss; uniform sampling with 1e5
-sampled entries per iteration; loss estimate on a fixed set of 1e5 entries.
-One step is one GCP-Adam epoch (Alg. 4): tau = 100 iterations of (fused
-sample + gradient, Adam step), the loss estimate, accept-or-revert; the epoch
-is captured once as a CUDA graph and replayed.  Metric: sampled-gradient
-entries processed per second (tau * s per step).
+Workload: a sparse binary 3-way tensor of 1e5 x 1e5 x 1e4 with 1e8 nonzeros
+in COO (int32 indices), drawn from a planted rank-32 logistic model;
+Bernoulli-logit loss; semi-stratified sampling (Alg. 3) with 1e6 nonzero and
+1e6 "zero" draws per iteration; rank 32; FP32 factors; the loss estimate on a
+fixed semi-stratified set of 1e5 + 1e5 entries.  One step is one GCP-Adam
+epoch (Alg. 4): tau = 100 iterations of (fused sample + gradient, Adam
+step), the loss estimate and the accept-or-revert decision, captured once as
+a CUDA graph and replayed.  Metric: sampled-gradient entries processed per
+second (tau (p + q) per step).
 
-Rank r of an N-rank run (torchrun) fits its own replica (seed + r): the path
-has no exchange step between independent decompositions ("replicas only").
+The same line carries the other workloads as forms, each beside the plain
+FP32 path with its roofline fraction: BF16-stored factors on this tensor;
+the dense 100^4 Gaussian tensor (uniform sampling, rank 10); the count tensor
+shaped like the Chicago crime data (stratified, Poisson-log, FP32 and BF16);
+64 batched problems; a draws-per-iteration sweep.
+
+Rank r of an N-rank run (torchrun) fits its own replica (seed + r): the
+benchmark's ranks are independent decompositions ("replicas only"; the
+sample-parallel split of one problem is in paper_1906_01687_gb300/parallel.py).
 """
 from __future__ import annotations
 
@@ -23,6 +32,7 @@ import statistics
 import subprocess
 import sys
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -31,16 +41,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sampled-gradient entries/s"
 UNIT = "entries/s"
-WORKLOAD = "dense-100x100x100x100-r10-gaussian-uniform-s1e5"
-DIMS, RANK, S_DRAWS, EST_DRAWS, TAU = (100, 100, 100, 100), 10, 100_000, 100_000, 100
-# Algorithmic bytes per draw of the gradient kernel: generated indices (0 B),
-# the dense value (4 B), the d row gathers and the d row updates of r FP32
-# entries each: 4 + d*r*4 + d*r*4.
-BYTES_PER_DRAW = 4 + 2 * len(DIMS) * RANK * 4
-
+WORKLOAD = "coo-1e5x1e5x1e4-nnz1e8-r32-bernoullilogit-semistratified-1e6+1e6"
+DIMS, NNZ, RANK = (100_000, 100_000, 10_000), 100_000_000, 32
+P_DRAWS, Q_DRAWS, EST_P, EST_Q, TAU = 1_000_000, 1_000_000, 100_000, 100_000, 100
+RECORD_BYTES = 16  # packed record of a nonzero of a 3-way tensor: three indices and the value's bits
 
 KERNEL_SOURCES = ("gcp_grad_impl.cuh", "gcp_draw.cuh", "gcp_device.cuh", "gcp_kernels.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "grad_kernel_dense100_r10_s1e5.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "grad_kernel_coo1e8_r32_semi2e6.json")
+
+
+def row_bytes(d, rank, b_f):
+    """Per draw: d factor rows of rank entries gathered (b_f bytes each) and
+    d rows of rank FP32 updates added into G."""
+    return d * rank * (b_f + 4)
+
+
+def grad_bytes(p, q, d, rank, b_f, nz_extra=RECORD_BYTES, zero_extra=0):
+    """Algorithmic bytes of one gradient launch: p nonzero draws reading
+    nz_extra bytes each (their packed record), q zero draws reading
+    zero_extra bytes (0 when their indices are generated), and the rows."""
+    return p * (nz_extra + row_bytes(d, rank, b_f)) + q * (zero_extra + row_bytes(d, rank, b_f))
+
+
+def adam_bytes(dims, rank, bf16=False):
+    """Algorithmic bytes of one Adam step: A, B, C, G read and written (32 B
+    per factor entry), plus the BF16 copy written."""
+    return sum(dims) * rank * (32 + (2 if bf16 else 0))
 
 
 def kernel_source_hash():
@@ -52,14 +78,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(launch):
+def recorded_traffic(launch, path=None):
     """DRAM bytes per launch of grad_kernel from the committed ncu summary, if
     the kernel sources and the kernel instance (lanes x chunks, draw layout,
     early draws) are those the counters were taken with; otherwise None.
     The block size is not compared: it changes neither the kernel's code nor
-    its DRAM traffic, which is the random gathers of X."""
+    its DRAM traffic."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(path or TRAFFIC_FILE) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
@@ -85,6 +111,14 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def max_over_ranks(value, world, device="cpu"):
@@ -163,62 +197,121 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def large_input(init_seed=3):
+    """The benchmark tensor's nonzero positions (host int32 SoA; generated
+    with torch's seeded generator on the GPU when there is one) and the
+    initial factors: N(0,1) entries scaled so that the model's norm equals
+    the data's, sqrt(nnz)."""
+    import torch
+    from paper_1906_01687_gb300 import synth
+    device = "cuda" if torch.cuda.is_available() else "cpu"
+    idx, _, _ = synth.binary_tensor(DIMS, NNZ, RANK, device=device)
+    A0 = synth.initial_guess(DIMS, RANK, seed=init_seed, target_norm=math.sqrt(NNZ))
+    return idx, A0
+
+
+# ---------------------------------------------------------------------------
 # the FP64 oracle on the host cores (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_tensor(X32):
+def oracle_large_tensor(idx):
     import oracle
-    return oracle.Tensor(DIMS, dense=X32.astype(np.float64).reshape(-1))
+    return oracle.Tensor(DIMS, coo=np.stack([np.asarray(i, np.int64) for i in idx], axis=1), vals=None)
 
 
-def oracle_epoch_rate(XO, A0, budget_s=12.0, seed=1687):
-    """Entries/s of the oracle doing the same epoch: tau iterations of
-    (sample, gradient, Adam) plus one loss estimate, extrapolated from a
-    bounded number of iterations and one estimate."""
+def _slices(S, parts):
     import oracle
-    A = oracle.concat_factors([a.astype(np.float64) for a in A0])
-    B, C = np.zeros_like(A), np.zeros_like(A)
+    cuts = [S.n * i // parts for i in range(parts + 1)]
+    return [oracle.Samples(S.idx[a:b], S.x[a:b], S.w[a:b], S.cls[a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
+
+
+def oracle_grad_threads(dims, A, loss, S, cores):
+    """The oracle's sampled gradient over S on `cores` host threads: the draws
+    split into contiguous slices, one oracle call per slice on its own thread
+    (the C oracle runs without the interpreter lock), the partial gradients
+    summed in slice order."""
+    import oracle
+    if cores <= 1:
+        return oracle.grad(dims, A, loss, S)
+    with ThreadPoolExecutor(cores) as ex:
+        parts = list(ex.map(lambda s: oracle.grad(dims, A, loss, s), _slices(S, cores)))
+    out = [p.copy() for p in parts[0]]
+    for part in parts[1:]:
+        for k in range(len(dims)):
+            out[k] += part[k]
+    return out
+
+
+def oracle_loss_threads(dims, A, loss, S, cores):
+    """The oracle's loss estimate over S, split over `cores` host threads like the gradient."""
+    import oracle
+    if cores <= 1:
+        return oracle.loss_estimate(dims, A, loss, S)
+    with ThreadPoolExecutor(cores) as ex:
+        return sum(ex.map(lambda s: oracle.loss_estimate(dims, A, loss, s), _slices(S, cores)))
+
+
+def oracle_epoch_rate(XO, A0, cores, iters=1, seed=1687):
+    """Entries/s of the FP64 oracle doing the benchmark's epoch on `cores`
+    host threads: per iteration the draws (one thread: the oracle's sampler
+    has no draw range), the gradient split over the threads and summed, and
+    the Adam step; one loss estimate per epoch (split the same way).  Timed
+    over `iters` iterations and one estimate, scaled to a tau-iteration epoch."""
+    import oracle
+    A = [np.asarray(a, np.float64) for a in A0]
+    flat = oracle.concat_factors(A)
+    B, C = np.zeros_like(flat), np.zeros_like(flat)
+    est = oracle.sample(XO, oracle.SEMI_STRATIFIED, EST_P, EST_Q, 7, 2**64 - 1)
     t0 = time.perf_counter()
-    est = oracle.sample(XO, oracle.UNIFORM, 0, EST_DRAWS, 7, 2**64 - 1)
-    oracle.loss_estimate(DIMS, oracle.split_factors(A, DIMS, RANK), oracle.GAUSSIAN, est)
+    oracle_loss_threads(DIMS, oracle.split_factors(flat, DIMS, RANK), oracle.BERNOULLI_LOGIT, est, cores)
     t_est = time.perf_counter() - t0
-    iters, t_it = 0, 0.0
-    while t_it < budget_s and iters < TAU:
+    t_it = 0.0
+    for it in range(iters):
         t0 = time.perf_counter()
-        S = oracle.sample(XO, oracle.UNIFORM, 0, S_DRAWS, seed, iters)
-        G = oracle.concat_factors(oracle.grad(DIMS, oracle.split_factors(A, DIMS, RANK), oracle.GAUSSIAN, S))
-        oracle.adam_step(A, B, C, G, 1e-3, t=iters)
+        S = oracle.sample(XO, oracle.SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, seed, it)
+        G = oracle_grad_threads(DIMS, oracle.split_factors(flat, DIMS, RANK), oracle.BERNOULLI_LOGIT, S, cores)
+        oracle.adam_step(flat, B, C, oracle.concat_factors(G), 1e-3, t=it)
         t_it += time.perf_counter() - t0
-        iters += 1
     per_it = t_it / iters
-    rate = TAU * S_DRAWS / (TAU * per_it + t_est)
-    sample = (f"{iters} oracle iterations of {S_DRAWS} draws (sample + gradient + Adam) and one "
-              f"{EST_DRAWS}-entry loss estimate, scaled to a {TAU}-iteration epoch")
+    rate = TAU * (P_DRAWS + Q_DRAWS) / (TAU * per_it + t_est)
+    sample = (f"{iters} oracle iteration(s) of {P_DRAWS}+{Q_DRAWS} semi-stratified draws (sample on one thread, "
+              f"gradient on {cores} thread(s), Adam) and one {EST_P}+{EST_Q}-entry loss estimate, "
+              f"scaled to a {TAU}-iteration epoch")
     return rate, sample
+
+
+def cpu_baseline(XO, A0, budget_iters=(1, 2)):
+    """The oracle on one host core and on all of them (threads over draw slices)."""
+    cores = host_cores()
+    rate1, sample1 = oracle_epoch_rate(XO, A0, 1, iters=budget_iters[0])
+    rate_n, sample_n = oracle_epoch_rate(XO, A0, cores, iters=budget_iters[1])
+    return {"value": rate_n, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_n,
+            "value_1core": rate1, "sample_1core": sample1, "cores_from": "os.sched_getaffinity(0)"}
 
 
 def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_1906_01687_gb300 import synth
-    X32, _ = synth.dense_100_4()
-    A0 = synth.initial_guess(DIMS, RANK, seed=3, target_norm=float(np.linalg.norm(X32)))
-    XO = oracle_tensor(X32)
-    budget = max(1.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
+    idx, A0 = large_input()
+    XO = oracle_large_tensor(idx)
+    cores = host_cores()
     rates = []
     for step in range(args.warmup + args.steps):
-        rate, sample = oracle_epoch_rate(XO, A0, budget_s=budget)
+        rate, sample = oracle_epoch_rate(XO, A0, cores, iters=1, seed=1687 + step)
         if step >= args.warmup:
             rates.append(rate)
     value = statistics.median(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": TAU * S_DRAWS / value * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": TAU * (P_DRAWS + Q_DRAWS) / value * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded planted model)",
-            "config": {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "samples_per_iter": S_DRAWS,
-                       "tau": TAU, "est_samples": EST_DRAWS},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic (seeded planted rank-32 logistic model)",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "nnz": NNZ, "rank": RANK,
+                       "samples_per_iter": [P_DRAWS, Q_DRAWS], "tau": TAU, "est_samples": [EST_P, EST_Q]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -228,26 +321,76 @@ def reference_arm(args):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
-def time_grad_kernel(torch, gcp, run, stream, launches=200):
-    """Average device duration of the fused-gradient kernel: the library
-    records CUDA events on the launching stream around each kernel launch of
-    `launches` GCP-Adam iterations, queued behind a sleep so that they run
-    back to back as in the replayed epochs."""
-    gcp.gcp_profile(run.h, True, launches)
+def time_grad_kernel(torch, gcp, h, iterate, stream, launches=50):
+    """Average device duration of the fused-gradient kernel and of the Adam
+    kernel: the library records CUDA events on the launching stream around
+    each kernel launch of `launches` GCP-Adam iterations (iterate()), queued
+    behind a sleep so that they run back to back."""
+    gcp.gcp_profile(h, True, launches)
     with torch.cuda.stream(stream):
         torch.cuda._sleep(200_000_000)
         for _ in range(launches):
-            run.iteration()
+            iterate()
     stream.synchronize()
-    ms, n = gcp.gcp_profile_read(run.h, 0)
-    ms_adam, n_adam = gcp.gcp_profile_read(run.h, 1)
-    gcp.gcp_profile(run.h, False)
+    ms, n = gcp.gcp_profile_read(h, 0)
+    ms_adam, n_adam = gcp.gcp_profile_read(h, 1)
+    gcp.gcp_profile(h, False)
     return ms * 1e-3 / n, n, ms_adam * 1e-3 / max(n_adam, 1)
+
+
+def time_iterations(torch, gcp, h, F, loss, spec, stream, iters=10, replays=3):
+    """Device time (s) per whole GCP-Adam iteration (gradient + Adam) of a
+    captured sequence of iterations on throwaway optimizer state."""
+    from paper_1906_01687_gb300.autotune import side_stream
+    with torch.cuda.stream(stream):
+        G, B, C = F.like(), F.like(), F.like()
+        st = gcp.new_state(F.A[0].device)
+        gcp.gcp_state_init(st, 1e-4, stream=stream)
+
+    def one(strm):
+        gcp.gcp_iteration(h, F, loss, spec, G, B, C, st, stream_dev=st[3:4], stream=strm)
+    with torch.cuda.stream(stream):
+        one(stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side_stream(stream)):
+        for _ in range(iters):
+            one(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(replays):
+            g.replay()
+        b.record(stream)
+    stream.synchronize()
+    del g
+    return a.elapsed_time(b) * 1e-3 / (replays * iters)
+
+
+def grad_launch_time(torch, gcp, h, F, loss, spec, stream, launches=50):
+    """Per-launch device time of the gradient kernel inside GCP-Adam
+    iterations on throwaway state (events around each gradient launch)."""
+    with torch.cuda.stream(stream):
+        G, B, C = F.like(), F.like(), F.like()
+        st = gcp.new_state(F.A[0].device)
+        gcp.gcp_state_init(st, 1e-4, stream=stream)
+
+    def it():
+        gcp.gcp_iteration(h, F, loss, spec, G, B, C, st, stream_dev=st[3:4], stream=stream)
+    with torch.cuda.stream(stream):
+        it()
+    return time_grad_kernel(torch, gcp, h, it, stream, launches)
+
+
+def rel_err(got, ref):
+    return math.sqrt(sum(float(np.linalg.norm(a - b)) ** 2 for a, b in zip(got, ref)) /
+                     sum(float(np.linalg.norm(b)) ** 2 for b in ref))
 
 
 def ours_arm(args):
     import torch
-    from paper_1906_01687_gb300 import gcp, synth
+    from paper_1906_01687_gb300 import gcp
     from paper_1906_01687_gb300.adam import GcpAdam
 
     world, rank, local = dist_env()
@@ -263,13 +406,14 @@ def ours_arm(args):
     copy_stream = torch.cuda.Stream(device=dev)
     assert copy_stream.cuda_stream != stream.cuda_stream
 
-    X32, _ = synth.dense_100_4()
     init_seed, seed = replica_seeds(rank)
-    A0 = synth.initial_guess(DIMS, RANK, seed=init_seed, target_norm=float(np.linalg.norm(X32)))
-    XT = gcp.DataTensor.dense(X32, device=dev)
+    t_gen = time.time()
+    idx, A0 = large_input(init_seed)
+    gen_s = time.time() - t_gen
+    XT = gcp.DataTensor.coo(DIMS, idx, None, device=dev)
     with torch.cuda.stream(stream):
-        run = GcpAdam(XT, A0, gcp.LOSS_GAUSSIAN, gcp.SAMPLER_UNIFORM, 0, S_DRAWS, 0, EST_DRAWS, seed=seed,
-                      est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream,
+        run = GcpAdam(XT, A0, gcp.LOSS_BERNOULLI_LOGIT, gcp.SAMPLER_SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, EST_P, EST_Q,
+                      seed=seed, est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream,
                       autotune=not (args.no_autotune or args.tuning))
         if args.tuning:
             gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
@@ -295,32 +439,37 @@ def ours_arm(args):
         barrier()
     elapsed = max_over_ranks(start.elapsed_time(end) * 1e-3, world, dev)
     st = run.status()
-    entries = args.steps * TAU * S_DRAWS * world
-    value = whole_job_rate(args.steps * TAU * S_DRAWS, world, elapsed)
+    per_step = TAU * (P_DRAWS + Q_DRAWS)
+    entries = args.steps * per_step * world
+    value = whole_job_rate(args.steps * per_step, world, elapsed)
 
-    # end to end through the public API with host buffers: every step copies X
-    # and the initial factors from pinned memory, runs the epoch and reads
-    # F-hat and the factors back.  X is double-buffered: step e + 1's copy (on
-    # a copy stream, into the other device buffer, read by a second handle
-    # and graph) runs while step e computes.  All host-to-device copies go
-    # through the copy stream in step order (factors of step e, then X of step
-    # e + 1), so that the small copies never queue behind a large one.
-    X_pin = torch.from_numpy(X32.reshape(-1)).pin_memory()
+    # end to end through the public API with host buffers: every step copies
+    # the COO index arrays (1.2 GB) and the initial factors from pinned
+    # memory, re-packs the nonzero records (gcp_refresh, first node of the
+    # step's graph), runs the epoch and reads F-hat and the factors back.
+    # The tensor is double-buffered: step e + 1's copy (on a copy stream,
+    # into the other device buffer, read by a second handle and graph) runs
+    # while step e computes.  All host-to-device copies go through the copy
+    # stream in step order (factors of step e, then the tensor of step e + 1).
+    idx_pin = [torch.from_numpy(np.ascontiguousarray(i)).pin_memory() for i in idx]
     A_pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in A0]
     F_out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in A0]
     state_out = torch.empty(8, dtype=torch.float64).pin_memory()
-    h2d = X_pin.numel() * 4 + sum(a.numel() * 4 for a in A_pin)
+    h2d = sum(i.numel() * 4 for i in idx_pin) + sum(a.numel() * 4 for a in A_pin)
     d2h = state_out.numel() * 8 + sum(a.numel() * 4 for a in F_out)
-    XT2 = gcp.DataTensor.dense(X32, device=dev)
-    handles, graphs, xbufs = [run.h], [run.graph], [XT.vals, XT2.vals]
+    XT2 = gcp.DataTensor.coo(DIMS, idx, None, device=dev)
+    tuning = dict(run.tuned["best"]) if run.tuned else {"early_draws": 1}
     with torch.cuda.stream(stream):
+        h1 = run.h
+        run.capture(refresh=True)
+        g1 = run.graph
         h2 = gcp.Handle(XT2, stream=stream)
-        gcp.gcp_set_tuning(h2, **(run.tuned["best"] if run.tuned else {"early_draws": 1}))
+        gcp.gcp_set_tuning(h2, **tuning)
         run.h = h2
-        run.capture()
-    handles.append(h2)
-    graphs.append(run.graph)
-    run.h, run.graph = handles[0], graphs[0]
+        run.capture(refresh=True)
+        g2 = run.graph
+        run.h = h1
+    handles, graphs, xbufs = [h1, h2], [g1, g2], [XT.idx, XT2.idx]
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     step_done = [torch.cuda.Event(), torch.cuda.Event()]
     factors_in = torch.cuda.Event()
@@ -329,7 +478,8 @@ def ours_arm(args):
     e_start.record(stream)
     copy_stream.wait_stream(stream)
     with torch.cuda.stream(copy_stream):
-        xbufs[0].copy_(X_pin, non_blocking=True)
+        for dst, src in zip(xbufs[0], idx_pin):
+            dst.copy_(src, non_blocking=True)
         copied[0].record(copy_stream)
     for e in range(args.steps):
         buf = e % 2
@@ -340,7 +490,8 @@ def ours_arm(args):
                 a_dev[:, :RANK].copy_(a_host, non_blocking=True)
             factors_in.record(copy_stream)
             if e + 1 < args.steps:
-                xbufs[1 - buf].copy_(X_pin, non_blocking=True)
+                for dst, src in zip(xbufs[1 - buf], idx_pin):
+                    dst.copy_(src, non_blocking=True)
                 copied[1 - buf].record(copy_stream)
         with torch.cuda.stream(stream):
             stream.wait_event(factors_in)
@@ -354,35 +505,51 @@ def ours_arm(args):
     barrier()
     e2e_elapsed = max_over_ranks(e_start.elapsed_time(e_end) * 1e-3, world, dev)
     e2e_value = entries / e2e_elapsed
+    e2e_state = gcp.read_state(state_out)
+    del graphs, g1, g2
 
-    # the dominant kernel (the fused sampled gradient), timed alone
-    mean_s, n_timed, adam_s = time_grad_kernel(torch, gcp, run, stream)
+    # the dominant kernel (the fused sampled gradient), timed on its stream
     peak, peak_kind = peaks()
-    achieved = BYTES_PER_DRAW * S_DRAWS / mean_s / 1e9
-    launch = gcp.gcp_get_launch(run.h, run.F, S_DRAWS)
+    mean_s, n_timed, adam_s = time_grad_kernel(torch, gcp, run.h, run.iteration, stream)
+    bytes_launch = grad_bytes(P_DRAWS, Q_DRAWS, len(DIMS), RANK, 4)
+    achieved = bytes_launch / mean_s / 1e9
+    launch = gcp.gcp_get_launch(run.h, run.F, P_DRAWS + Q_DRAWS)
+    iter_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream)
 
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0
+    ms_per_step = elapsed / args.steps * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded planted rank-10 model + N(0,0.01) noise)",
-            "config": {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "loss": "gaussian",
-                       "sampler": "uniform", "samples_per_iter": S_DRAWS, "tau": TAU, "est_samples": EST_DRAWS,
+            "data": "synthetic (seeded planted rank-32 logistic model; COO int32)",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "nnz": NNZ, "rank": RANK,
+                       "loss": "bernoulli_logit", "sampler": "semi_stratified",
+                       "samples_per_iter": [P_DRAWS, Q_DRAWS], "tau": TAU, "est_samples": [EST_P, EST_Q],
+                       "factors": "fp32",
                        "step": "one GCP-Adam epoch (tau iterations + loss estimate + accept/revert), CUDA graph",
-                       "l2": "inputs larger than L2 (X = 400 MB, gathered at random)",
-                       "parallelism": f"replicas{world}", "grad_launch": launch,
-                       "autotuned": run.tuned},
+                       "l2": "inputs larger than L2 (1.6 GB of packed nonzero records gathered at random; "
+                             "factors and gradients, 27 MB each, L2-resident)",
+                       "parallelism": f"replicas{world}", "grad_launch": launch, "autotuned": run.tuned,
+                       "generation_s": gen_s},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "overlap": "X double-buffered: step e+1's H2D copy runs during step e"},
+                    "overlap": "tensor double-buffered: step e+1's H2D copy runs during step e; each step "
+                               "re-packs its records (gcp_refresh) inside its graph",
+                    "final_F": e2e_state["F"]},
             "gpu_launches": args.steps * (2 * TAU + 2),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(launch), "kernel": "grad_kernel (fused sample/gather/model/derivative/MTTKRP scatter)",
-                         "bytes_per_draw": BYTES_PER_DRAW, "draws_per_launch": S_DRAWS,
+                         "frac": achieved / peak, "traffic": recorded_traffic(launch),
+                         "kernel": "grad_kernel (fused sample/gather/model/derivative/MTTKRP scatter)",
+                         "bytes_per_launch": bytes_launch,
+                         "bytes_per_draw": {"nonzero": RECORD_BYTES + row_bytes(3, RANK, 4),
+                                            "zero": row_bytes(3, RANK, 4)},
+                         "draws_per_launch": P_DRAWS + Q_DRAWS,
                          "launch_us_mean": mean_s * 1e6, "launches_timed": n_timed,
                          "adam_us_mean": adam_s * 1e6,
-                         "share_of_iteration_kernels": mean_s / (mean_s + adam_s),
+                         "iteration_us_in_graph": iter_s * 1e6,
+                         "in_step_check": {"grad_ms_per_step": TAU * mean_s * 1e3, "ms_per_step": ms_per_step,
+                                           "fits": TAU * mean_s * 1e3 <= ms_per_step},
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "final_state": {k: st[k] for k in ("F", "t", "iter", "alpha", "bad")}}
     clocks = clk.summary()
@@ -390,16 +557,23 @@ def ours_arm(args):
     # the single-GPU characterisations and the CPU baseline belong to the
     # one-GPU line; with N replicas they would only hold the N GPUs longer
     single = world == 1
-    if single and not args.no_sweep:
-        line["sweep"] = sweep_draws(torch, gcp, run, stream, peak)
-    if single and not args.no_large:
-        line["large_sparse"] = large_sparse(torch, gcp, synth, stream, peak)
+    XO = None
+    if single and not (args.no_cpu_baseline and args.no_forms):
+        XO = oracle_large_tensor(idx)
     if single and not args.no_forms:
-        line["forms"] = {"bf16": forms_bf16(torch, gcp, synth, stream),
-                         "batched": forms_batched(torch, gcp, synth, stream)}
+        forms = {}
+        for name, fn in (("bf16", lambda: form_large_bf16(torch, gcp, run, XO, A0, stream, peak, launch)),
+                         ("dense100", lambda: form_dense100(torch, gcp, stream, peak, args)),
+                         ("count", lambda: form_count(torch, gcp, stream, peak)),
+                         ("batched", lambda: form_batched(torch, gcp, stream, peak))):
+            try:
+                forms[name] = fn()
+            except Exception as e:  # a reporting extra: record the failure, keep the line
+                forms[name] = {"error": repr(e)}
+            torch.cuda.empty_cache()
+        line["forms"] = forms
     if single and not args.no_cpu_baseline:
-        rate, sample = oracle_epoch_rate(oracle_tensor(X32), A0, budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = cpu_baseline(XO, A0)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -423,143 +597,147 @@ def _time_calls(torch, fn, stream, reps):
     return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
 
 
-def sweep_draws(torch, gcp, run, stream, peak, sizes=(100_000, 1_000_000, 10_000_000)):
-    """Whole GCP-Adam iterations (gradient + Adam) on the benchmark tensor at
-    larger draw counts per iteration, each size captured as a CUDA graph of
-    back-to-back iterations on throwaway copies of the factors: the
-    bandwidth-bound reading of the same kernels."""
-    out = []
-    with torch.cuda.stream(stream):
-        F = gcp.Factors([a[:, :RANK] for a in run.F.A])
-        G, B, C = F.like(), F.like(), F.like()
-        st = gcp.new_state()
-        gcp.gcp_state_init(st, 1e-4, stream=stream)
-    from paper_1906_01687_gb300.autotune import side_stream
-    cap = side_stream(stream)
-    for s in sizes:
-        spec = gcp.Sampling(gcp.SAMPLER_UNIFORM, 0, s, 99, 0)
-        iters = max(3, min(50, 5_000_000 // s))
-
-        def one(strm):
-            gcp.gcp_iteration(run.h, F, gcp.LOSS_GAUSSIAN, spec, G, B, C, st, stream_dev=st[3:4], stream=strm)
-        with torch.cuda.stream(stream):
-            one(stream)
-        stream.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=cap):
-            for _ in range(iters):
-                one(cap)
-        with torch.cuda.stream(stream):
-            g.replay()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(3):
-                g.replay()
-            b.record(stream)
-        stream.synchronize()
-        us = a.elapsed_time(b) * 1e3 / (3 * iters)
-        gbs = BYTES_PER_DRAW * s / us / 1e3
-        out.append({"draws_per_iteration": s, "us_per_iteration": us, "entries_per_s": s / us * 1e6,
-                    "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peak})
-        del g
-    return {"what": "whole iterations (gradient + Adam), CUDA graph, dense 100^4 rank 10, Gaussian, uniform",
-            "points": out}
-
-
-def large_sparse(torch, gcp, synth, stream, peak, iters=10):
-    """The largest sparse workload: the 1e5 x 1e5 x 1e4 binary tensor with 1e8
-    nonzeros, rank 32, Bernoulli-logit, semi-stratified 1e6 + 1e6 draws per
-    iteration, whole GCP-Adam iterations (gradient + Adam over all 2.1e5 x 32
-    factor entries) captured in a CUDA graph; FP32 and BF16 factor storage.
-    Algorithmic bytes per iteration: nonzero draws 16 B (packed record) +
-    d r b_f B rows + d r 4 B updates (784 B in FP32, 592 B with BF16 rows),
-    "zero" draws the same without the record (no value read), plus the Adam
-    pass (32 B per factor entry, + 2 B for the BF16 copy)."""
-    t0 = time.time()
-    dims, rank, p, q = (100_000, 100_000, 10_000), 32, 1_000_000, 1_000_000
-    idx, _, _ = synth.binary_tensor(device=stream.device)
-    h = gcp.Handle(gcp.DataTensor.coo(dims, idx, None, device=stream.device), stream=stream)
-    gen_s = time.time() - t0
-    A = [(a / math.sqrt(rank) ** (1 / 3)).astype(np.float32) for a in synth.initial_guess(dims, rank, 5)]
-    entries = sum(dims) * rank
-    out = {"workload": "coo-1e5x1e5x1e4-nnz1e8-r32-bernoullilogit-semistratified-1e6+1e6",
-           "what": "whole iterations (gradient + Adam), CUDA graph", "generation_s": gen_s}
-    from paper_1906_01687_gb300.autotune import side_stream
-    cap = side_stream(stream)
+def form_large_bf16(torch, gcp, run, XO, A0, stream, peak, launch32):
+    """FP32 vs BF16 factor storage on the benchmark tensor: per-launch
+    gradient kernel time and roofline fraction of each, whole-iteration time,
+    and the gradient's and the loss estimate's errors against the FP64
+    oracle on the same draws (at the FP32 factors; for BF16 also at the
+    BF16-rounded factors, which separates storage from arithmetic error)."""
+    import oracle
+    out = {"workload": WORKLOAD, "metric": "entries/s of the gradient kernel; whole GCP-Adam iterations"}
+    spec = gcp.Sampling(gcp.SAMPLER_SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, 4242, 0)
+    SO = oracle.sample(XO, oracle.SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, 4242, 0)
+    cores = host_cores()
+    A64 = [np.asarray(a, np.float32).astype(np.float64) for a in A0]
+    G_ref = oracle_grad_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, SO, cores)
+    estO = oracle.sample(XO, oracle.SEMI_STRATIFIED, EST_P, EST_Q, 7, gcp.STREAM_EST)
+    F_ref = oracle_loss_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, estO, cores)
     for name, bf16 in (("fp32", False), ("bf16", True)):
         b_f = 2 if bf16 else 4
-        grad_bytes = p * (16 + len(dims) * rank * (b_f + 4)) + q * (len(dims) * rank * (b_f + 4))
-        adam_bytes = entries * (32 + (2 if bf16 else 0))
         with torch.cuda.stream(stream):
-            F = gcp.Factors(A, bf16=bf16)
-            G, B, C = F.like(), F.like(), F.like()
-            st = gcp.new_state()
-            gcp.gcp_state_init(st, 1e-4, stream=stream)
-        spec = gcp.Sampling(gcp.SAMPLER_SEMI_STRATIFIED, p, q, 1687, 0)
-        gcp.gcp_set_tuning(h, early_draws=1)
-
-        def one(strm):
-            gcp.gcp_iteration(h, F, gcp.LOSS_BERNOULLI_LOGIT, spec, G, B, C, st, stream_dev=st[3:4], stream=strm)
+            F = gcp.Factors(A0, bf16=bf16)
+        mean_s, n, adam_s = grad_launch_time(torch, gcp, run.h, F, run.loss, spec, stream)
+        iter_s = time_iterations(torch, gcp, run.h, F, run.loss, spec, stream)
+        gb = grad_bytes(P_DRAWS, Q_DRAWS, len(DIMS), RANK, b_f)
+        ab = adam_bytes(DIMS, RANK, bf16)
         with torch.cuda.stream(stream):
-            one(stream)
+            G = F.like()
+            gcp.gcp_grad(run.h, F, run.loss, G, S=spec, stream=stream)
+            F_dev = torch.zeros(1, dtype=torch.float64, device=G[0].device)
+            gcp.gcp_loss_est(run.h, F, run.loss, run.est, F_dev, stream=stream)
         stream.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=cap):
-            for _ in range(iters):
-                one(cap)
-        with torch.cuda.stream(stream):
-            g.replay()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(3):
-                g.replay()
-            b.record(stream)
-        stream.synchronize()
-        us = a.elapsed_time(b) * 1e3 / (3 * iters)
-        gbs = (grad_bytes + adam_bytes) / us / 1e3
-        out[name] = {"us_per_iteration": us, "entries_per_s": (p + q) / us * 1e6,
-                     "algorithmic_bytes_per_iteration": grad_bytes + adam_bytes, "algorithmic_gbs": gbs,
-                     "frac_of_measured_hbm": gbs / peak}
-        del g
+        got = [x[:, :RANK].double().cpu().numpy() for x in G]
+        rec = {"grad_kernel_us": mean_s * 1e6, "entries_per_s": (P_DRAWS + Q_DRAWS) / mean_s,
+               "grad_bytes_per_launch": gb, "grad_frac_of_measured_hbm": gb / mean_s / 1e9 / peak,
+               "iteration_us": iter_s * 1e6, "iteration_frac_of_measured_hbm": (gb + ab) / iter_s / 1e9 / peak,
+               "grad_rel_err_vs_fp64_oracle": rel_err(got, G_ref),
+               "loss_rel_err_vs_fp64_oracle": abs(F_dev.item() - F_ref) / abs(F_ref),
+               "launch": gcp.gcp_get_launch(run.h, F, P_DRAWS + Q_DRAWS)}
+        if bf16:
+            Ab = [a.double().cpu().numpy()[:, :RANK] for a in F.A_bf16]
+            G_rb = oracle_grad_threads(DIMS, Ab, oracle.BERNOULLI_LOGIT, SO, cores)
+            rec["grad_rel_err_vs_fp64_oracle_at_bf16_factors"] = rel_err(got, G_rb)
+        out[name] = rec
+    out["bf16_over_fp32_grad_kernel"] = out["fp32"]["grad_kernel_us"] / out["bf16"]["grad_kernel_us"]
+    out["bound"] = ("L2: the gathered rows and the row updates of both forms are L2 hits (factors 27 MB); "
+                    "BF16 halves the gathered bytes, not the L2 vector reductions of the updates")
     return out
 
 
-def forms_bf16(torch, gcp, synth, stream):
+def form_dense100(torch, gcp, stream, peak, args, tau=100, epochs=5):
+    """The dense 100^4 FP32 tensor (planted rank 10 + N(0, 0.01) noise),
+    Gaussian loss, uniform 1e5 draws per iteration: graph-replayed epochs,
+    the gradient kernel per launch, and a draws-per-iteration sweep."""
+    from paper_1906_01687_gb300 import synth
+    from paper_1906_01687_gb300.adam import GcpAdam
+    dims, rank, s = (100, 100, 100, 100), 10, 100_000
+    X32, _ = synth.dense_100_4()
+    A0 = synth.initial_guess(dims, rank, seed=3, target_norm=float(np.linalg.norm(X32)))
+    XT = gcp.DataTensor.dense(X32, device=stream.device)
+    with torch.cuda.stream(stream):
+        run = GcpAdam(XT, A0, gcp.LOSS_GAUSSIAN, gcp.SAMPLER_UNIFORM, 0, s, 0, 100_000, seed=1687, est_seed=7,
+                      alpha=1e-3, tau=tau, kappa=1_000_000, stream=stream, autotune=not args.no_autotune)
+        run.capture()
+    run.run_epoch()
+    stream.synchronize()
+    t_epoch = _time_calls(torch, run.run_epoch, stream, epochs)
+    mean_s, n, adam_s = time_grad_kernel(torch, gcp, run.h, run.iteration, stream)
+    iter_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
+    gb = s * (4 + row_bytes(4, rank, 4))
+    out = {"workload": "dense-100x100x100x100-r10-gaussian-uniform-s1e5", "tau": tau,
+           "entries_per_s": tau * s / t_epoch, "ms_per_epoch": t_epoch * 1e3,
+           "grad_bytes_per_launch": gb, "grad_kernel_us": mean_s * 1e6, "adam_us": adam_s * 1e6,
+           "grad_frac_of_measured_hbm": gb / mean_s / 1e9 / peak,
+           "iteration_us_in_graph": iter_s * 1e6,
+           "iteration_frac_of_measured_hbm": (gb + adam_bytes(dims, rank)) / iter_s / 1e9 / peak,
+           "launch": gcp.gcp_get_launch(run.h, run.F, s), "autotuned": run.tuned,
+           "traffic_note": "factors and G are 16 KB: rows and updates are L2 hits; DRAM traffic is the X gathers"}
+    if not args.no_sweep:
+        out["sweep"] = sweep_draws(torch, gcp, run, stream, peak, rank)
+    return out
+
+
+def sweep_draws(torch, gcp, run, stream, peak, rank, sizes=(100_000, 1_000_000, 10_000_000)):
+    """Whole GCP-Adam iterations (gradient + Adam) on the dense tensor at
+    larger draw counts per iteration: the bandwidth-bound reading of the same
+    kernels."""
+    out = []
+    F = gcp.Factors([a[:, :rank] for a in run.F.A])
+    for s in sizes:
+        spec = gcp.Sampling(gcp.SAMPLER_UNIFORM, 0, s, 99, 0)
+        iters = max(3, min(50, 5_000_000 // s))
+        us = time_iterations(torch, gcp, run.h, F, gcp.LOSS_GAUSSIAN, spec, stream, iters=iters) * 1e6
+        gbs = s * (4 + row_bytes(4, rank, 4)) / us / 1e3
+        out.append({"draws_per_iteration": s, "us_per_iteration": us, "entries_per_s": s / us * 1e6,
+                    "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peak})
+    return out
+
+
+def form_count(torch, gcp, stream, peak):
     """FP32 vs BF16 factor storage on the count tensor (6186x24x77x32, 5.33M
-    nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): gradient
-    throughput, and the gradient's and the loss estimate's errors against the
-    FP64 oracle (at the FP32 factors) on the same draws."""
+    nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): the whole
+    gcp_grad call (ordered zero pass + gradient), its roofline fraction, and
+    the gradient's and the loss estimate's errors against the FP64 oracle (at
+    the FP32 factors) on the same draws."""
     import oracle
+    from paper_1906_01687_gb300 import synth
     from paper_1906_01687_gb300.autotune import autotune, candidates
-    dims = (6186, 24, 77, 32)
+    dims, rank, p, q = (6186, 24, 77, 32), 10, 100_000, 100_000
     idx, vals, _ = synth.count_tensor()
     h = gcp.Handle(gcp.DataTensor.coo(dims, idx, vals))
-    A = [(a * 0.3).astype(np.float32) for a in synth.initial_guess(dims, 10, 4, positive=True)]
-    spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, 100_000, 100_000, 1687, 0)
+    A = [(a * 0.3).astype(np.float32) for a in synth.initial_guess(dims, rank, 4, positive=True)]
+    spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, p, q, 1687, 0)
     XO = oracle.Tensor(dims, coo=np.stack([i.astype(np.int64) for i in idx], axis=1), vals=vals.astype(np.float64))
-    SO = oracle.sample(XO, oracle.STRATIFIED, 100_000, 100_000, 1687, 0)
+    SO = oracle.sample(XO, oracle.STRATIFIED, p, q, 1687, 0)
     ref = oracle.grad(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SO)
-    # the fixed loss-estimate list (stratified 1e5 + 1e5, the estimate stream)
-    est_spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, 100_000, 100_000, 7, gcp.STREAM_EST)
-    SOe = oracle.sample(XO, oracle.STRATIFIED, 100_000, 100_000, 7, gcp.STREAM_EST)
+    est_spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, p, q, 7, gcp.STREAM_EST)
+    SOe = oracle.sample(XO, oracle.STRATIFIED, p, q, 7, gcp.STREAM_EST)
     F_ref = oracle.loss_estimate(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SOe)
+    # the call's algorithmic bytes: nonzero draws read a 32-byte record; the
+    # zero pass probes the 8-byte hash slot of ~1.1 candidates per accepted
+    # zero (rho = 1.1, 1.5% of entries are nonzeros) and writes 4d bytes of
+    # indices that the gradient reads back
+    omega = float(np.prod(dims))
+    cand_per_zero = 1.1 * omega / (omega - len(vals))
+    zero_extra = 2 * 4 * len(dims) + 8 * cand_per_zero
+    call_bytes = {b_f: grad_bytes(p, q, len(dims), rank, b_f, nz_extra=32, zero_extra=zero_extra) for b_f in (4, 2)}
     out = {"workload": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
            "metric": "entries/s of gcp_grad (zero pass + gradient)"}
     for name, bf16 in (("fp32", False), ("bf16", True)):
         F = gcp.Factors(A, bf16=bf16)
         tuned = autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream,
-                         configs=[dict(c, early_draws=1) for c in candidates(10)])
+                         configs=[dict(c, early_draws=1) for c in candidates(rank)])
         G = F.like()
         t = _time_calls(torch, lambda: gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream), stream, 50)
         for x in G:
             x.zero_()
         gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream)
         stream.synchronize()
-        got = [x[:, :10].double().cpu().numpy() for x in G]
-        err = math.sqrt(sum(np.linalg.norm(a - b) ** 2 for a, b in zip(got, ref)) /
-                        sum(np.linalg.norm(b) ** 2 for b in ref))
-        out[name] = {"value": 200_000 / t, "us_per_call": t * 1e6, "grad_rel_err_vs_fp64_oracle": err,
-                     "launch": gcp.gcp_get_launch(h, F, 200_000), "tuning": tuned["best"]}
+        got = [x[:, :rank].double().cpu().numpy() for x in G]
+        cb = call_bytes[2 if bf16 else 4]
+        out[name] = {"value": (p + q) / t, "us_per_call": t * 1e6, "grad_rel_err_vs_fp64_oracle": rel_err(got, ref),
+                     "call_bytes": cb, "frac_of_measured_hbm": cb / t / 1e9 / peak,
+                     "launch": gcp.gcp_get_launch(h, F, p + q), "tuning": tuned["best"]}
         try:
             est = gcp.gcp_sample(h, est_spec, stream=stream)
             F_dev = torch.zeros(1, dtype=torch.float64, device=G[0].device)
@@ -573,11 +751,12 @@ def forms_bf16(torch, gcp, synth, stream):
     return out
 
 
-def forms_batched(torch, gcp, synth, stream, tau=20, epochs=3):
+def form_batched(torch, gcp, stream, peak, tau=20, epochs=3):
     """64 independent dense problems (d in {3,4}, dims U[50,2000] with at most
     2e7 entries, ranks {4,8,16,32,64}, mixed losses, 1e4-1e5 draws/iteration):
     one batched launch per step under one CUDA graph, against the same 64
     problems run one after another (each its own graph-replayed epoch)."""
+    from paper_1906_01687_gb300 import synth
     from paper_1906_01687_gb300.adam import GcpAdam
     from paper_1906_01687_gb300.batch import GcpAdamBatch
     shapes = synth.batched_problems()
@@ -600,6 +779,10 @@ def forms_batched(torch, gcp, synth, stream, tau=20, epochs=3):
         specs.append(dict(X=X, A0=A0, loss=gcp.LOSSES[sh["loss"]], s=sh["s"], est=10_000, seed=1687 + i,
                           est_seed=7, problem=i))
     draws = sum(sp["s"] for sp in specs)
+    # algorithmic bytes per iteration over all problems: each draw reads its
+    # dense value and d rows and adds d rows; each Adam step moves 32 B per entry
+    it_bytes = sum(sh["s"] * (4 + row_bytes(len(sh["dims"]), sh["rank"], 4)) + adam_bytes(sh["dims"], sh["rank"])
+                   for sh in shapes)
     torch.cuda.synchronize()
     batch = GcpAdamBatch(specs, tau=tau, alpha=1e-3, kappa=1_000_000, stream=stream, autotune=True)
     batch.capture()
@@ -628,15 +811,17 @@ def forms_batched(torch, gcp, synth, stream, tau=20, epochs=3):
         single.run_epoch()
         single.run_epoch()
         a, b = batch2.factors(i), single.factors()
-        errs.append(math.sqrt(sum(np.linalg.norm(x - y) ** 2 for x, y in zip(a, b)) /
-                              sum(np.linalg.norm(y) ** 2 for y in b)))
+        errs.append(rel_err(a, b))
     entries = tau * draws
     return {"workload": f"64 dense problems, d 3-4, dims 50-2000 (<= 2e7 entries), ranks 4-64, mixed losses, "
                         f"{draws} draws/iteration in total, tau {tau}",
             "metric": "sampled-gradient entries/s over one epoch (all problems)",
-            "batched": {"value": entries / t_batch, "ms_per_epoch": t_batch * 1e3, "launches_per_iteration": 2,
-                        "tuning": batch.tuned},
+            "bytes_per_iteration": it_bytes,
+            "batched": {"value": entries / t_batch, "ms_per_epoch": t_batch * 1e3,
+                        "frac_of_measured_hbm": tau * it_bytes / t_batch / 1e9 / peak,
+                        "launches_per_iteration": 2, "tuning": batch.tuned},
             "sequential": {"value": entries / t_seq, "ms_per_epoch": t_seq * 1e3,
+                           "frac_of_measured_hbm": tau * it_bytes / t_seq / 1e9 / peak,
                            "launches_per_iteration": 2 * len(specs)},
             "batched_over_sequential": t_seq / t_batch,
             "factor_rel_diff_vs_single_runs_after_2_epochs_max": max(errs)}
@@ -645,35 +830,20 @@ def forms_batched(torch, gcp, synth, stream, tau=20, epochs=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form comparisons")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other workloads and forms")
     ap.add_argument("--no-sweep", action="store_true", help="skip the draws-per-iteration sweep")
-    ap.add_argument("--no-large", action="store_true", help="skip the 1e8-nonzero sparse workload")
     ap.add_argument("--tuning", default=None, help="JSON gcp_tuning fields to use instead of autotuning")
-    ap.add_argument("--only-forms", action="store_true",
-                    help="run only the BF16 and batched form comparisons (one JSON object; for profiling them)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return reference_arm(args)
-    if args.only_forms:
-        return forms_only()
     return ours_arm(args)
-
-
-def forms_only():
-    import torch
-    from paper_1906_01687_gb300 import gcp, synth
-    stream = torch.cuda.Stream()
-    print(json.dumps({"forms": {"bf16": forms_bf16(torch, gcp, synth, stream),
-                                "batched": forms_batched(torch, gcp, synth, stream)}}), flush=True)
-    return 0
 
 
 if __name__ == "__main__":

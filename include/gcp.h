@@ -219,6 +219,18 @@ typedef struct gcp_handle gcp_handle; /* opaque: a prepared tensor */
    GCP_ERR_CUDA. */
 gcp_status gcp_create(gcp_handle **out, const gcp_tensor *X, gcp_stream_t stream);
 
+/* Takes up new contents of X's device arrays after the caller has rewritten
+   them in place (same d, dims, nnz and pointers; Section 3.2 storage): for a
+   sparse X it re-packs the nonzero records and, if the stratified
+   sampler's nonzero-key hash was built, rebuilds it in place; for a dense X
+   with entry weights, the count of entries of nonzero weight is taken
+   again on the observed sampler's next use (a host read, as on first use).
+   Stream-ordered, allocates nothing and waits for nothing (graph-capturable
+   for a sparse X).  The first gradient launch after it draws after its
+   dependency wait even with early_draws.  Errors: GCP_ERR_INVALID_ARG (NULL
+   handle), GCP_ERR_CUDA. */
+gcp_status gcp_refresh(gcp_handle *h, gcp_stream_t stream);
+
 /* Frees the handle's device memory (synchronises the device first). */
 gcp_status gcp_destroy(gcp_handle *h);
 
@@ -298,6 +310,25 @@ gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
                     const gcp_sampling *S, const gcp_samples *list,
                     const int64_t *stream_dev, float *const G[GCP_MAX_MODES],
                     gcp_stream_t stream);
+
+/* The part of gcp_grad's sampled gradient (Eq. (4.3), Algs. 1-3) that comes
+   from the draws j in [first, first + count) of spec S, accumulated into G
+   as gcp_grad does.  Draws are numbered as gcp_sample lists them: uniform
+   and observed 0..q-1; stratified and semi-stratified the p nonzero draws
+   0..p-1, then the q zero draws p..p+q-1.  Because every draw is a pure
+   function of its number (counter-based sampling), the results over any
+   partition of [0, gcp_sample_count(S)) sum to gcp_grad's G (up to the
+   FP32 summation order): this is the sample-parallel split of one problem
+   across GPUs, each GPU taking one range and a sum of G across GPUs
+   following -- the parallel use of sampling that Section 6 points to.  With
+   a stratified spec each call runs the whole ordered zero pass (the zeros
+   of a range depend on every earlier candidate) and then takes its range.
+   stream_dev, replica slabs, allocation and overlap rules as for gcp_grad.
+   Errors: GCP_ERR_INVALID_ARG (S NULL, first < 0, count < 0, or
+   first + count beyond gcp_sample_count(S)) and as gcp_grad. */
+gcp_status gcp_grad_range(gcp_handle *h, const gcp_factors *F, gcp_loss loss, const gcp_sampling *S,
+                          int64_t first, int64_t count, const int64_t *stream_dev,
+                          float *const G[GCP_MAX_MODES], gcp_stream_t stream);
 
 /* The full (non-stochastic) gradient G_k = Y_(k) Z_k of a dense X
    (Eq. (4.2); with entry weights, Eq. (4.5)): every index of Omega taken once

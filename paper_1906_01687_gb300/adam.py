@@ -112,8 +112,11 @@ class GcpAdam:
         return _autotune(self.h, F, self.loss, self.spec, configs=configs, launches=launches, stream=self.stream,
                          call=call, graph=True)
 
-    def capture(self):
-        """Captures one epoch's launches in a CUDA graph (replayed by run_epoch)."""
+    def capture(self, refresh: bool = False):
+        """Captures one epoch's launches in a CUDA graph (replayed by run_epoch).
+        With refresh the graph first takes up new contents of the data
+        tensor's arrays (gcp_refresh: the caller rewrites them in place
+        between replays, e.g. a new upload of the same-shaped tensor)."""
         self._warm()
         self.stream.synchronize()
         g = torch.cuda.CUDAGraph()
@@ -122,6 +125,8 @@ class GcpAdam:
         with torch.cuda.graph(g, stream=cap):
             saved, self.stream = self.stream, torch.cuda.current_stream()
             try:
+                if refresh:
+                    gcp.gcp_refresh(self.h, stream=self.stream)
                 self.enqueue_epoch()
             finally:
                 self.stream = saved

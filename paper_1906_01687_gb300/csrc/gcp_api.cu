@@ -35,6 +35,9 @@ struct gcp_handle {
     cudaStream_t last_stream = nullptr;
     int device = 0;
     int num_sms = 0;
+    // set by gcp_refresh: the next gradient launch must not draw before its
+    // dependency wait, since the kernel just before it rewrote the records
+    bool fresh_data = false;
     // nonzero-key hash (stratified)
     unsigned long long* table = nullptr;
     float* table_vals = nullptr;
@@ -764,10 +767,11 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
 
 // advance_t (gcp_iteration): the gradient kernel advances advance_t->t for the
 // Adam step that follows; *launched reports whether a gradient kernel ran.
+// first / count (count >= 0): only the draws j in [first, first + count) of the spec.
 static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
                             const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
                             cudaStream_t s, FoldArgs* deferred_fold, gcp_adam_state* advance_t = nullptr,
-                            bool* launched = nullptr)
+                            bool* launched = nullptr, int64_t first = 0, int64_t count = -1)
 {
     if (launched) *launched = false;
     if (!h || (S == nullptr) == (list == nullptr)) return GCP_ERR_INVALID_ARG;
@@ -789,12 +793,19 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     }
     GradArgs a{};
     a.dr = make_draw_args(h, S, list, stream_dev);
+    if (count >= 0) {  // a draw range of the spec
+        if (first < 0 || first > a.dr.n_total || count > a.dr.n_total - first) return GCP_ERR_INVALID_ARG;
+        a.dr.j_begin = first;
+        a.dr.n_total = first + count;
+    }
+    const int64_t n_draws = a.dr.n_total - a.dr.j_begin;
     // early descriptors only for draws that read nothing but the data tensor and
     // tables built before this call (not a list; with stratified sampling the
-    // kernel keeps them to warps whose first batch holds nonzero draws only)
-    const bool early_ok = a.dr.src == kSrcUniformDense || (a.dr.src == kSrcUniformSparse && table_ready) ||
-                          a.dr.src == kSrcSparse;
-    if (a.dr.n_total == 0) return GCP_OK;
+    // kernel keeps them to warps whose first batch holds nonzero draws only),
+    // and not right after gcp_refresh rewrote the records
+    const bool early_ok = (a.dr.src == kSrcUniformDense || (a.dr.src == kSrcUniformSparse && table_ready) ||
+                           a.dr.src == kSrcSparse) && !h->fresh_data;
+    if (n_draws == 0) return GCP_OK;
     if (S && (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
         st = ensure_zero_list(h, S->q);
         if (st != GCP_OK) return st;
@@ -806,7 +817,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
         a.dr.zcount = h->zcount;
     }
     Shape sh;
-    st = choose_shape(h, F, a.dr.n_total, &sh);
+    st = choose_shape(h, F, n_draws, &sh);
     if (st != GCP_OK) return st;
     if (sh.rep_floats > h->rep_ws_cap) {
         cudaFree(h->rep_ws);
@@ -861,6 +872,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));
     GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.layout(), sh.grid, sh.block, sh.smem, s));
+    h->fresh_data = false;
     if (launched) *launched = true;
     if (timed) {
         GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s));
@@ -950,6 +962,34 @@ gcp_status gcp_grad(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gc
                     gcp_stream_t stream)
 {
     return grad_impl(h, F, loss, S, list, stream_dev, G, reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
+
+gcp_status gcp_grad_range(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S, int64_t first,
+                          int64_t count, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
+                          gcp_stream_t stream)
+{
+    if (!S || count < 0) return GCP_ERR_INVALID_ARG;
+    return grad_impl(h, F, loss, S, nullptr, stream_dev, G, reinterpret_cast<cudaStream_t>(stream), nullptr,
+                     nullptr, nullptr, first, count);
+}
+
+gcp_status gcp_refresh(gcp_handle* h, gcp_stream_t stream)
+{
+    if (!h) return GCP_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_stream = s;
+    if (!h->X.sparse) {
+        h->n_observed = -1;  // the entries of nonzero weight are counted again on next use
+        return GCP_OK;
+    }
+    GCP_CUDA_TRY(launch_pack_records(h->X, h->recs, h->rec_int4, s));
+    if (h->table) {  // rebuilt in place: same nonzero count, same table size
+        GCP_CUDA_TRY(cudaMemsetAsync(h->table, 0xFF, (h->table_mask + 1) * sizeof(unsigned long long), s));
+        GCP_CUDA_TRY(launch_hash_build(h->recs, h->rec_int4, h->X.d, h->strides, h->X.nnz, h->table, h->table_vals,
+                                       h->table_mask, h->d_status, s));
+    }
+    h->fresh_data = true;
+    return GCP_OK;
 }
 
 gcp_status gcp_loss_est(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_samples* list,

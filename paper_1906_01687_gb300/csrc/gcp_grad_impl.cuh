@@ -63,7 +63,9 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     const int per_warp = a.group_draws ? 32 / L : 32;
     const int steps = a.group_draws ? 1 : L;
     const int sub = a.group_draws ? lane / L : lane;
-    const int64_t wb0 = (static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * per_warp;
+    // (draws j_begin .. n_total - 1: a draw range of the spec when j_begin > 0)
+    const int64_t wb0 =
+        a.dr.j_begin + (static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * per_warp;
     // early descriptors for this warp: every draw of its first batch reads only
     // data written before the preceding kernel (with stratified sampling, the
     // nonzero draws j < p; the zeros come from the zero pass just before)

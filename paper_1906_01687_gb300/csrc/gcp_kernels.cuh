@@ -28,7 +28,8 @@ struct DrawArgs {
     uint32_t dims[GCP_MAX_MODES];
     uint64_t strides[GCP_MAX_MODES];  // row-major strides of the linear index
     int64_t p;            // nonzero draws: j in [0, p)
-    int64_t n_total;      // all draws
+    int64_t n_total;      // end of the draws this launch takes (exclusive)
+    int64_t j_begin;      // first draw this launch takes (a draw range; 0 = from the start)
     uint64_t seed, problem, stream;
     const int64_t* stream_dev;
     float w_first;        // uniform: omega/s; sparse: eta/p

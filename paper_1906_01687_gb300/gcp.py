@@ -108,6 +108,9 @@ _SIGS = {
     "gcp_sample": ([_vp, _P(gcp_sampling), _P(gcp_samples), _vp], ctypes.c_int),
     "gcp_reserve": ([_vp, _P(gcp_sampling), _vp], ctypes.c_int),
     "gcp_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _P(gcp_samples), _vp, _P8, _vp], ctypes.c_int),
+    "gcp_grad_range": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_sampling), _i64, _i64, _vp, _P8, _vp],
+                       ctypes.c_int),
+    "gcp_refresh": ([_vp, _vp], ctypes.c_int),
     "gcp_full_grad": ([_vp, _P(gcp_factors), ctypes.c_int, _P8, _vp], ctypes.c_int),
     "gcp_full_loss": ([_vp, _P(gcp_factors), ctypes.c_int, _vp, _vp], ctypes.c_int),
     "gcp_loss_est": ([_vp, _P(gcp_factors), ctypes.c_int, _P(gcp_samples), _vp, _vp], ctypes.c_int),
@@ -417,6 +420,19 @@ def gcp_grad(h: Handle, F: Factors, loss: int, G: Sequence[torch.Tensor], S: Opt
     lp = ctypes.byref(samples._c()) if samples is not None else None
     _check(_lib.gcp_grad(h.ptr, ctypes.byref(F._c(gather_bf16)), int(loss), sp, lp, _ptr(stream_dev), _p8(G),
                          _stream(stream)), "gcp_grad")
+
+
+def gcp_grad_range(h: Handle, F: Factors, loss: int, G: Sequence[torch.Tensor], S: Sampling, first: int,
+                   count: int, stream_dev: Optional[torch.Tensor] = None, stream=None,
+                   gather_bf16: Optional[bool] = None):
+    """Accumulates into G the sampled gradient of the draws [first, first + count) of spec S."""
+    _check(_lib.gcp_grad_range(h.ptr, ctypes.byref(F._c(gather_bf16)), int(loss), ctypes.byref(S._c()), int(first),
+                               int(count), _ptr(stream_dev), _p8(G), _stream(stream)), "gcp_grad_range")
+
+
+def gcp_refresh(h: Handle, stream=None):
+    """Takes up new contents of the handle's tensor arrays (rewritten in place by the caller)."""
+    _check(_lib.gcp_refresh(h.ptr, _stream(stream)), "gcp_refresh")
 
 
 def gcp_full_grad(h: Handle, F: Factors, loss: int, G, stream=None):

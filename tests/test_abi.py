@@ -169,7 +169,7 @@ def test_invalid_descriptors_rejected_before_any_launch(lib_path):
         return lib.gcp_loss_est_noalloc(d, ctypes.byref(F or factors()), loss, ctypes.byref(L_), out_, None)
 
     assert noalloc() == gcp.ERR_CUDA
-    assert noalloc(d=0) == BAD and noalloc(loss=7) == BAD and noalloc(loss=-1) == BAD
+    assert noalloc(d=0) == BAD and noalloc(d=1) == BAD and noalloc(loss=7) == BAD and noalloc(loss=-1) == BAD
     assert noalloc(F=factors(ld=3)) == BAD and noalloc(out_=ctypes.c_void_p(base * 40 + 4)) == BAD
     L2 = gcp.gcp_samples.from_buffer_copy(L)
     L2.n = 262_145  # more than one entry per thread of 1024 blocks of 256
@@ -180,6 +180,9 @@ def test_invalid_descriptors_rejected_before_any_launch(lib_path):
 
     # handles and batches
     assert lib.gcp_profile(None, 1, 16) == BAD
+    assert lib.gcp_refresh(None, None) == BAD
+    spec = gcp.Sampling(gcp.SAMPLER_UNIFORM, 0, 10, 1)._c()
+    assert lib.gcp_grad_range(None, ctypes.byref(factors()), 0, ctypes.byref(spec), 0, 5, None, p8(), None) == BAD
     assert lib.gcp_set_tuning(None, None) == BAD
     assert lib.gcp_get_device_status(None, None) == BAD
     b = ctypes.c_void_p()

@@ -65,18 +65,18 @@ def test_reference_arm_is_rank0_only(monkeypatch):
 
 
 def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
-    """Rank 0 prints one JSON line with the arm's keys; the oracle's timing is
-    replaced by a fixed rate here (the line's assembly is what is checked)."""
+    """Rank 0 prints one JSON line with the arm's keys; the input and the
+    oracle's timing are replaced by stand-ins here (the line's assembly is
+    what is checked)."""
     import json
     sys.path.insert(0, ROOT)
     import bench
-    from paper_1906_01687_gb300 import synth
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    monkeypatch.setattr(synth, "dense_100_4", lambda: (np.zeros((2, 2, 2, 2), np.float32), None))
-    monkeypatch.setattr(bench, "oracle_tensor", lambda X: None)
-    monkeypatch.setattr(bench, "oracle_epoch_rate", lambda XO, A0, budget_s: (2.0e6, "a bounded sample"))
-    monkeypatch.setattr(bench, "DIMS", (2, 2, 2, 2))
+    monkeypatch.setattr(bench, "large_input", lambda init_seed=3: (None, None))
+    monkeypatch.setattr(bench, "oracle_large_tensor", lambda idx: None)
+    monkeypatch.setattr(bench, "oracle_epoch_rate",
+                        lambda XO, A0, cores, iters=1, seed=1687: (2.0e6, "a bounded sample"))
 
     class A:
         steps, warmup, gpus = 2, 3, 1
@@ -85,7 +85,7 @@ def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
     assert line["impl"] == "reference" and line["value"] == 2.0e6 and line["higher_is_better"] is True
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["dtype"] == "f64"
     assert line["steps"] == 2 and line["warmup"] == 3 and line["n_gpus"] == 1
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == bench.host_cores()
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": 2.0e6, "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == bench.WORKLOAD
