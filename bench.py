@@ -44,6 +44,7 @@ UNIT = "entries/s"
 WORKLOAD = "coo-1e5x1e5x1e4-nnz1e8-r32-bernoullilogit-semistratified-1e6+1e6"
 DIMS, NNZ, RANK = (100_000, 100_000, 10_000), 100_000_000, 32
 P_DRAWS, Q_DRAWS, EST_P, EST_Q, TAU = 1_000_000, 1_000_000, 100_000, 100_000, 100
+ALPHA = 1e-3  # Adam learning rate of the benchmark run
 RECORD_BYTES = 16  # packed record of a nonzero of a 3-way tensor: three indices and the value's bits
 
 KERNEL_SOURCES = ("gcp_grad_impl.cuh", "gcp_draw.cuh", "gcp_device.cuh", "gcp_kernels.cuh")
@@ -413,7 +414,7 @@ def ours_arm(args):
     XT = gcp.DataTensor.coo(DIMS, idx, None, device=dev)
     with torch.cuda.stream(stream):
         run = GcpAdam(XT, A0, gcp.LOSS_BERNOULLI_LOGIT, gcp.SAMPLER_SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, EST_P, EST_Q,
-                      seed=seed, est_seed=7, alpha=1e-3, tau=TAU, kappa=1_000_000, stream=stream,
+                      seed=seed, est_seed=7, alpha=ALPHA, tau=TAU, kappa=1_000_000, stream=stream,
                       autotune=not (args.no_autotune or args.tuning))
         if args.tuning:
             gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
@@ -614,13 +615,15 @@ def form_large_bf16(torch, gcp, run, XO, A0, stream, peak, launch32):
     F_ref = oracle_loss_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, estO, cores)
     for name, bf16 in (("fp32", False), ("bf16", True)):
         b_f = 2 if bf16 else 4
-        with torch.cuda.stream(stream):
-            F = gcp.Factors(A0, bf16=bf16)
-        mean_s, n, adam_s = grad_launch_time(torch, gcp, run.h, F, run.loss, spec, stream)
-        iter_s = time_iterations(torch, gcp, run.h, F, run.loss, spec, stream)
+        with torch.cuda.stream(stream):  # the timing steps its own copy of the factors
+            F_t = gcp.Factors(A0, bf16=bf16)
+        mean_s, n, adam_s = grad_launch_time(torch, gcp, run.h, F_t, run.loss, spec, stream)
+        iter_s = time_iterations(torch, gcp, run.h, F_t, run.loss, spec, stream)
+        del F_t
         gb = grad_bytes(P_DRAWS, Q_DRAWS, len(DIMS), RANK, b_f)
         ab = adam_bytes(DIMS, RANK, bf16)
-        with torch.cuda.stream(stream):
+        with torch.cuda.stream(stream):  # the error check: the initial factors A0
+            F = gcp.Factors(A0, bf16=bf16)
             G = F.like()
             gcp.gcp_grad(run.h, F, run.loss, G, S=spec, stream=stream)
             F_dev = torch.zeros(1, dtype=torch.float64, device=G[0].device)
@@ -838,12 +841,52 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the other workloads and forms")
     ap.add_argument("--no-sweep", action="store_true", help="skip the draws-per-iteration sweep")
     ap.add_argument("--tuning", default=None, help="JSON gcp_tuning fields to use instead of autotuning")
+    ap.add_argument("--nnz", type=int, default=None,
+                    help="nonzeros of the benchmark tensor (default 1e8); a smaller tensor of the same shape, "
+                         "draws and rank is the small case for profiling")
+    ap.add_argument("--profile", type=int, default=0, metavar="ITERS",
+                    help="only set up the benchmark's run and take ITERS eager GCP-Adam iterations, then exit "
+                         "(the command profiled with ncu; prints one line of timing)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.nnz is not None:
+        global NNZ, WORKLOAD
+        NNZ = int(args.nnz)
+        WORKLOAD = WORKLOAD.replace("nnz1e8", f"nnz{NNZ:.0e}".replace("+0", ""))
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile:
+        return profile_arm(args)
     return ours_arm(args)
+
+
+def profile_arm(args):
+    """The benchmark's run set up as in ours_arm (no autotuning: the shape
+    given by --tuning, else the automatic one), then --profile eager
+    iterations: a short, bounded command for ncu."""
+    import torch
+    from paper_1906_01687_gb300 import gcp
+    from paper_1906_01687_gb300.adam import GcpAdam
+    stream = torch.cuda.Stream()
+    idx, A0 = large_input()
+    XT = gcp.DataTensor.coo(DIMS, idx, None)
+    with torch.cuda.stream(stream):
+        run = GcpAdam(XT, A0, gcp.LOSS_BERNOULLI_LOGIT, gcp.SAMPLER_SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, EST_P, EST_Q,
+                      seed=1687, est_seed=7, alpha=ALPHA, tau=TAU, kappa=1_000_000, stream=stream)
+        if args.tuning:
+            gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(args.profile):
+            run.iteration()
+        b.record(stream)
+    stream.synchronize()
+    print(json.dumps({"profile": WORKLOAD, "iterations": args.profile,
+                      "us_per_iteration": a.elapsed_time(b) * 1e3 / args.profile,
+                      "launch": gcp.gcp_get_launch(run.h, run.F, P_DRAWS + Q_DRAWS)}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

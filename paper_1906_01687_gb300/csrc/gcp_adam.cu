@@ -144,9 +144,99 @@ __global__ void __launch_bounds__(64) adam_split_kernel(const AdamArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.st->iter += 1;
 }
 
+// The same step for large factor sets (bandwidth-bound): every thread takes
+// kStreamU float4 elements per round, a block's threads adjacent elements
+// (coalesced), with the loads of all of them -- G, its replica slabs, A, B, C
+// -- issued before any is used.  Replicated modes fold their slabs in the
+// thread that owns the element.  t was advanced by the gradient kernel;
+// block 0 advances iter, which no Adam block reads.
+constexpr int kStreamU = 4;
+constexpr int kStreamBlock = 256;
+
+__global__ void __launch_bounds__(kStreamBlock, 2) adam_stream_kernel(const AdamArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    const ModeTable& mt = a.mt;
+    const float alpha = a.st->alpha;
+    const int done = a.st->done;
+    const float n = static_cast<float>(a.st->t);
+    const float ic1 = inv_bias_correction(a.beta1, n);
+    const float ic2 = inv_bias_correction(a.beta2, n);
+    const bool inside = a.eps_inside_sqrt != 0;
+    const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
+    const uint32_t ld4 = static_cast<uint32_t>(mt.ld) / 4;
+    const uint32_t round = gridDim.x * kStreamBlock * kStreamU;
+    for (uint32_t base = blockIdx.x * kStreamBlock * kStreamU + threadIdx.x; base < total4; base += round) {
+        int k[kStreamU];
+        uint32_t loc[kStreamU];
+        float4 g[kStreamU], A4[kStreamU], B4[kStreamU], C4[kStreamU];
+#pragma unroll
+        for (int u = 0; u < kStreamU; ++u) {
+            const uint32_t i4 = base + static_cast<uint32_t>(u) * kStreamBlock;
+            k[u] = 0;
+            loc[u] = 0;
+            g[u] = A4[u] = B4[u] = C4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i4 < total4) {
+                k[u] = mode_of(mt, i4);
+                loc[u] = i4 - static_cast<uint32_t>(mt.off4[k[u]]);
+                g[u] = reinterpret_cast<const float4*>(mt.G[k[u]])[loc[u]];
+                A4[u] = reinterpret_cast<const float4*>(mt.A[k[u]])[loc[u]];
+                B4[u] = reinterpret_cast<const float4*>(mt.B[k[u]])[loc[u]];
+                C4[u] = reinterpret_cast<const float4*>(mt.C[k[u]])[loc[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStreamU; ++u) {
+            const uint32_t i4 = base + static_cast<uint32_t>(u) * kStreamBlock;
+            if (i4 >= total4) continue;
+            if (a.reps[k[u]] > 1) {  // fold the replica slabs of this mode in order, leaving them zero
+                // (replicated modes are short, so few elements take this path)
+                float4* r = reinterpret_cast<float4*>(a.R[k[u]]) + loc[u];
+                const uint64_t rs = a.rep_stride4[k[u]];
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (uint32_t q = 0; q < a.reps[k[u]]; ++q) {
+                    acc = add4(acc, r[q * rs]);
+                    r[q * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                g[u] = add4(g[u], acc);
+            }
+            const int col = static_cast<int>((loc[u] % ld4) * 4);
+            if (!done && col < mt.rank) {
+                const int live = mt.rank - col;  // columns of this chunk below rank
+                adam_one(A4[u].x, B4[u].x, C4[u].x, g[u].x, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+                if (live > 1)
+                    adam_one(A4[u].y, B4[u].y, C4[u].y, g[u].y, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+                if (live > 2)
+                    adam_one(A4[u].z, B4[u].z, C4[u].z, g[u].z, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+                if (live > 3)
+                    adam_one(A4[u].w, B4[u].w, C4[u].w, g[u].w, a.beta1, a.beta2, ic1, ic2, a.eps, alpha, a.lower, inside);
+                reinterpret_cast<float4*>(mt.A[k[u]])[loc[u]] = A4[u];
+                reinterpret_cast<float4*>(mt.B[k[u]])[loc[u]] = B4[u];
+                reinterpret_cast<float4*>(mt.C[k[u]])[loc[u]] = C4[u];
+                if (mt.Abf[k[u]]) store_bf16x4(mt.Abf[k[u]] + static_cast<size_t>(loc[u]) * 4, A4[u]);
+            }
+            reinterpret_cast<float4*>(mt.G[k[u]])[loc[u]] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->iter += 1;
+}
+
+// Factor sets of at least this many float4 elements take the streaming
+// kernel (bandwidth-bound); smaller ones the split kernel (latency-bound,
+// many replica slabs to fold).
+constexpr int64_t kStreamMin4 = 1 << 18;
+
 cudaError_t launch_adam_advanced(const AdamArgs& a, int num_sms, cudaStream_t s)
 {
-    const int64_t threads = a.mt.off4[a.mt.d] * kParts;
+    const int64_t total4 = a.mt.off4[a.mt.d];
+    if (total4 >= kStreamMin4) {
+        const int64_t per_block = int64_t(kStreamBlock) * kStreamU;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total4 + per_block - 1) / per_block,
+                                                                    int64_t(num_sms) * 8));
+        return launch_pdl(adam_stream_kernel, dim3(static_cast<unsigned>(grid)), dim3(kStreamBlock), 0, s, a);
+    }
+    const int64_t threads = total4 * kParts;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((threads + 63) / 64, int64_t(num_sms) * 32));
     return launch_pdl(adam_split_kernel, dim3(static_cast<unsigned>(grid)), dim3(64), 0, s, a);
 }

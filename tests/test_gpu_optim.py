@@ -237,15 +237,21 @@ def test_planted_recovery_on_gpu():
     assert cosine_score(true, run.factors()) >= 0.9
 
 
-@pytest.mark.parametrize("kind", ["uniform", "stratified", "uniform_large"])
+@pytest.mark.parametrize("kind", ["uniform", "stratified", "uniform_large", "semi_stream"])
 def test_fused_iteration_equals_grad_then_adam(kind):
     """gcp_iteration (gradient + Adam with the replica fold inside Adam) gives
     the factors of gcp_grad followed by gcp_adam_step on the same draws: with
-    more than 16 replicas per mode (the fold's tail), and with factor sets
-    small enough for the one-cluster Adam launch and large enough for the
-    ticket launch."""
+    more than 16 replicas per mode (the fold's tail), with factor sets small
+    enough for the one-cluster Adam launch and large enough for the ticket
+    launch, and (semi_stream: 1.2M float4 elements, short modes replicated)
+    large enough for gcp_iteration's streaming Adam kernel."""
     g = gcp()
-    if kind in ("uniform", "uniform_large"):
+    if kind == "semi_stream":
+        dims = (400_000, 40, 30)
+        idx, vals = sparse_random(dims, 20000, 10)
+        h = g.Handle(g.DataTensor.coo(dims, idx, vals))
+        S = g.Sampling(g.SAMPLER_SEMI_STRATIFIED, 20000, 20000, seed=3, stream=5)
+    elif kind in ("uniform", "uniform_large"):
         dims = (60, 50, 40, 30) if kind == "uniform" else (3000, 40, 30)
         X = np.random.default_rng(3).standard_normal(dims).astype(np.float32)
         h = g.Handle(g.DataTensor.dense(X))
