@@ -203,15 +203,28 @@ class Clocks:
 
 def large_input(init_seed=3):
     """The benchmark tensor's nonzero positions (host int32 SoA; generated
-    with torch's seeded generator on the GPU when there is one) and the
-    initial factors: N(0,1) entries scaled so that the model's norm equals
-    the data's, sqrt(nnz)."""
+    with torch's seeded generator on the GPU when there is one), the initial
+    factors -- entries uniform in (0, 1), scaled so that the model's norm
+    equals the data's, sqrt(nnz) (the paper's initial guesses for its binary
+    problems, Sections 5.4-5.5) -- and the planted factors."""
     import torch
     from paper_1906_01687_gb300 import synth
     device = "cuda" if torch.cuda.is_available() else "cpu"
-    idx, _, _ = synth.binary_tensor(DIMS, NNZ, RANK, device=device)
-    A0 = synth.initial_guess(DIMS, RANK, seed=init_seed, target_norm=math.sqrt(NNZ))
-    return idx, A0
+    idx, _, planted = synth.binary_tensor(DIMS, NNZ, RANK, device=device)
+    A0 = synth.initial_guess(DIMS, RANK, seed=init_seed, target_norm=math.sqrt(NNZ), positive=True)
+    return idx, A0, planted
+
+
+def near_fitted(planted):
+    """Factors near a fitted model of the benchmark tensor: the planted
+    model with its first column a constant c, c^3 = log(1e-6) (the density),
+    so that sigma(m) of a zero is about 1e-6 and a zero draw's y, (omega/q)
+    sigma(m) ~ 100, nearly cancels a nonzero draw's, -(eta/p) = -100."""
+    c = -(-math.log(1e-6)) ** (1.0 / 3.0)
+    A = [np.array(a, dtype=np.float32) for a in planted]
+    for a in A:
+        a[:, 0] = c
+    return A
 
 
 # ---------------------------------------------------------------------------
@@ -297,7 +310,7 @@ def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    idx, A0 = large_input()
+    idx, A0, _ = large_input()
     XO = oracle_large_tensor(idx)
     cores = host_cores()
     rates = []
@@ -409,7 +422,7 @@ def ours_arm(args):
 
     init_seed, seed = replica_seeds(rank)
     t_gen = time.time()
-    idx, A0 = large_input(init_seed)
+    idx, A0, planted = large_input(init_seed)
     gen_s = time.time() - t_gen
     XT = gcp.DataTensor.coo(DIMS, idx, None, device=dev)
     with torch.cuda.stream(stream):
@@ -563,7 +576,7 @@ def ours_arm(args):
         XO = oracle_large_tensor(idx)
     if single and not args.no_forms:
         forms = {}
-        for name, fn in (("bf16", lambda: form_large_bf16(torch, gcp, run, XO, A0, stream, peak, launch)),
+        for name, fn in (("bf16", lambda: form_large_bf16(torch, gcp, run, XO, A0, planted, stream, peak)),
                          ("dense100", lambda: form_dense100(torch, gcp, stream, peak, args)),
                          ("count", lambda: form_count(torch, gcp, stream, peak)),
                          ("batched", lambda: form_batched(torch, gcp, stream, peak))):
@@ -598,7 +611,7 @@ def _time_calls(torch, fn, stream, reps):
     return statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
 
 
-def form_large_bf16(torch, gcp, run, XO, A0, stream, peak, launch32):
+def form_large_bf16(torch, gcp, run, XO, A0, planted, stream, peak):
     """FP32 vs BF16 factor storage on the benchmark tensor: per-launch
     gradient kernel time and roofline fraction of each, whole-iteration time,
     and the gradient's and the loss estimate's errors against the FP64
@@ -641,6 +654,24 @@ def form_large_bf16(torch, gcp, run, XO, A0, stream, peak, launch32):
             G_rb = oracle_grad_threads(DIMS, Ab, oracle.BERNOULLI_LOGIT, SO, cores)
             rec["grad_rel_err_vs_fp64_oracle_at_bf16_factors"] = rel_err(got, G_rb)
         out[name] = rec
+    # near a fitted model: the terms of opposite sign that nearly cancel in FP32
+    An = near_fitted(planted)
+    Gn_ref = oracle_grad_threads(DIMS, [a.astype(np.float64) for a in An], oracle.BERNOULLI_LOGIT, SO, cores)
+    near = {}
+    for name, bf16 in (("fp32", False), ("bf16", True)):
+        with torch.cuda.stream(stream):
+            F = gcp.Factors(An, bf16=bf16)
+            G = F.like()
+            gcp.gcp_grad(run.h, F, run.loss, G, S=spec, stream=stream)
+        stream.synchronize()
+        got = [x[:, :RANK].double().cpu().numpy() for x in G]
+        near[name] = {"grad_rel_err_vs_fp64_oracle": rel_err(got, Gn_ref)}
+        if bf16:
+            Ab = [a.double().cpu().numpy()[:, :RANK] for a in F.A_bf16]
+            near[name]["grad_rel_err_vs_fp64_oracle_at_bf16_factors"] = rel_err(
+                got, oracle_grad_threads(DIMS, Ab, oracle.BERNOULLI_LOGIT, SO, cores))
+    out["near_fitted"] = dict(near, what="planted factors with a constant column, c^3 = log(1e-6): "
+                                         "zero and nonzero draws' terms of about +-100 nearly cancel")
     out["bf16_over_fp32_grad_kernel"] = out["fp32"]["grad_kernel_us"] / out["bf16"]["grad_kernel_us"]
     out["bound"] = ("L2: the gathered rows and the row updates of both forms are L2 hits (factors 27 MB); "
                     "BF16 halves the gathered bytes, not the L2 vector reductions of the updates")
@@ -869,7 +900,7 @@ def profile_arm(args):
     from paper_1906_01687_gb300 import gcp
     from paper_1906_01687_gb300.adam import GcpAdam
     stream = torch.cuda.Stream()
-    idx, A0 = large_input()
+    idx, A0, _ = large_input()
     XT = gcp.DataTensor.coo(DIMS, idx, None)
     with torch.cuda.stream(stream):
         run = GcpAdam(XT, A0, gcp.LOSS_BERNOULLI_LOGIT, gcp.SAMPLER_SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, EST_P, EST_Q,
@@ -877,14 +908,18 @@ def profile_arm(args):
         if args.tuning:
             gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gcp.gcp_profile(run.h, True, args.profile)
     with torch.cuda.stream(stream):
         a.record(stream)
         for _ in range(args.profile):
             run.iteration()
         b.record(stream)
     stream.synchronize()
+    ms, n = gcp.gcp_profile_read(run.h, 0)
+    gcp.gcp_profile(run.h, False)
     print(json.dumps({"profile": WORKLOAD, "iterations": args.profile,
                       "us_per_iteration": a.elapsed_time(b) * 1e3 / args.profile,
+                      "grad_kernel_us": ms * 1e3 / max(n, 1),
                       "launch": gcp.gcp_get_launch(run.h, run.F, P_DRAWS + Q_DRAWS)}), flush=True)
     return 0
 

@@ -123,7 +123,7 @@ __device__ __forceinline__ void make_draw(const DrawArgs& a, int64_t j, uint64_t
         o.w = a.w_first;
         o.cls = GCP_CLS_UNIFORM;
         if (a.src == kSrcUniformDense) {
-            o.x = __ldg(a.X + lin);
+            o.x = __ldcs(a.X + lin);  // read once: evict-first
             if (a.W) o.w *= __ldg(a.W + lin);
         } else {  // a sparse tensor: the value of a nonzero, else 0
             const int64_t slot = hash_find(a.table, a.table_mask, lin);
@@ -143,7 +143,7 @@ __device__ __forceinline__ void make_draw(const DrawArgs& a, int64_t j, uint64_t
 #pragma unroll
         for (int r = 0; r < kRecMax; ++r) {
             if (r < a.rec_int4) {
-                const int4 v = __ldg(rec + r);
+                const int4 v = __ldcs(rec + r);  // read once: evict-first
                 words[4 * r + 0] = v.x;
                 words[4 * r + 1] = v.y;
                 words[4 * r + 2] = v.z;

@@ -73,7 +73,7 @@ def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
     import bench
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    monkeypatch.setattr(bench, "large_input", lambda init_seed=3: (None, None))
+    monkeypatch.setattr(bench, "large_input", lambda init_seed=3: (None, None, None))
     monkeypatch.setattr(bench, "oracle_large_tensor", lambda idx: None)
     monkeypatch.setattr(bench, "oracle_epoch_rate",
                         lambda XO, A0, cores, iters=1, seed=1687: (2.0e6, "a bounded sample"))
