@@ -537,12 +537,6 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    prefetch = 1 (one chunk per lane, 2 or 4 lanes, at most 4 modes): a group
    issues the row loads of all its draws before consuming any (one round
    trip to L2 per group walk instead of one per draw; more registers).
-   prefetch = 2 (one chunk per lane, group_draws = 0): the pipelined walk --
-   a group issues the row loads of its next draw before consuming the
-   current one, and a warp makes its next batch of draws (Philox, the value
-   or record gather) before walking the current batch; factor rows are read
-   with an L2 evict-last hint.  A shape without a compiled instance of the
-   requested layout falls back to the group walk.
    early_draws = 1: where the draws read nothing but the data tensor (uniform
    sampling, semi-stratified sampling, the nonzero draws of stratified
    sampling, or uniform over a sparse tensor whose nonzero table was built by

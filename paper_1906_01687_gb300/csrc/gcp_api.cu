@@ -49,9 +49,8 @@ struct gcp_handle {
     int32_t* zidx_base = nullptr;
     int64_t* zcount = nullptr;
     int64_t ztiles_cap = 0;
-    uint32_t* mask_words = nullptr;
-    int32_t* tile_counts = nullptr;
-    int64_t* tile_offsets = nullptr;
+    unsigned long long* tile_status = nullptr;  // zero between calls (the zero pass clears it)
+    unsigned int* zero_ctrs = nullptr;          // the zero pass's tile and completion counters
     // loss-estimate partial sums
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
@@ -228,19 +227,18 @@ gcp_status ensure_zero_list(gcp_handle* h, int64_t q)
     return GCP_OK;
 }
 
-gcp_status ensure_zero_scratch(gcp_handle* h, int64_t tiles)
+gcp_status ensure_zero_scratch(gcp_handle* h, int64_t tiles, cudaStream_t s)
 {
     if (tiles <= h->ztiles_cap) return GCP_OK;
-    cudaFree(h->mask_words);
-    cudaFree(h->tile_counts);
-    cudaFree(h->tile_offsets);
-    h->mask_words = nullptr;
-    h->tile_counts = nullptr;
-    h->tile_offsets = nullptr;
+    cudaFree(h->tile_status);
+    cudaFree(h->zero_ctrs);
+    h->tile_status = nullptr;
+    h->zero_ctrs = nullptr;
     h->ztiles_cap = 0;
-    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->mask_words), static_cast<size_t>(tiles) * 32 * sizeof(uint32_t)));
-    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->tile_counts), static_cast<size_t>(tiles) * sizeof(int32_t)));
-    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->tile_offsets), static_cast<size_t>(tiles) * sizeof(int64_t)));
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->tile_status), static_cast<size_t>(tiles) * sizeof(unsigned long long)));
+    GCP_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&h->zero_ctrs), 2 * sizeof(unsigned int)));
+    GCP_CUDA_TRY(cudaMemsetAsync(h->tile_status, 0, static_cast<size_t>(tiles) * sizeof(unsigned long long), s));
+    GCP_CUDA_TRY(cudaMemsetAsync(h->zero_ctrs, 0, 2 * sizeof(unsigned int), s));
     h->ztiles_cap = tiles;
     return GCP_OK;
 }
@@ -278,7 +276,7 @@ gcp_status run_zero_pass(gcp_handle* h, const gcp_sampling* S, const int64_t* st
     if (st != GCP_OK) return st;
     const int64_t batch = zero_batch(h, S);
     const int64_t tiles = (batch + 1023) / 1024;
-    st = ensure_zero_scratch(h, tiles);
+    st = ensure_zero_scratch(h, tiles, s);
     if (st != GCP_OK) return st;
     ZeroArgs z{};
     z.d = h->X.d;
@@ -302,9 +300,9 @@ gcp_status run_zero_pass(gcp_handle* h, const gcp_sampling* S, const int64_t* st
         z.obs_x = h->X.vals;
         z.w_obs = static_cast<double>(h->n_observed) / static_cast<double>(S->q);
     }
-    z.mask_words = h->mask_words;
-    z.tile_counts = h->tile_counts;
-    z.tile_offsets = h->tile_offsets;
+    z.tile_status = h->tile_status;
+    z.tile_ctr = h->zero_ctrs;
+    z.done_ctr = h->zero_ctrs + 1;
     z.count_out = h->zcount;
     z.status = h->d_status;
     z.out_x = out_x;
@@ -327,7 +325,7 @@ struct Shape {
     uint32_t reps[GCP_MAX_MODES] = {};
     int64_t rep_floats = 0;  // replica workspace the shape needs
     int group = 0;           // group_draws layout
-    int pf = 0;              // 1: prefetch layout, 2: pipelined walk
+    int pf = 0;              // prefetch layout
     int early = 0;           // early descriptors (where the draw source allows)
     int layout() const { return pf; }
 };
@@ -396,11 +394,8 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
     sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;
     sh->early = t.early_draws == 1 ? 1 : 0;
-    sh->pf = 0;
-    if (t.prefetch == 2 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 2))
-        sh->pf = 2;  // the pipelined walk
-    else if (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 1) && h->X.d == sh->D)
-        sh->pf = 1;  // the prefetch layout
+    sh->pf = (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 1) &&
+              h->X.d == sh->D) ? 1 : 0;
     const int64_t per_warp = sh->group ? 32 / sh->L : 32;
     const int64_t warps = (n_total + per_warp - 1) / per_warp;
     const int64_t blocks_needed = std::max<int64_t>(1, (warps + sh->block / 32 - 1) / (sh->block / 32));
@@ -655,9 +650,8 @@ gcp_status gcp_destroy(gcp_handle* h)
     cudaFree(h->table_vals);
     cudaFree(h->zidx_base);
     cudaFree(h->zcount);
-    cudaFree(h->mask_words);
-    cudaFree(h->tile_counts);
-    cudaFree(h->tile_offsets);
+    cudaFree(h->tile_status);
+    cudaFree(h->zero_ctrs);
     cudaFree(h->partials);
     cudaFree(h->ticket);
     cudaFree(h->rep_ws);
@@ -684,7 +678,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, 0)) return GCP_ERR_INVALID_ARG;
-    if (t->prefetch < 0 || t->prefetch > 2) return GCP_ERR_INVALID_ARG;
+    if (t->prefetch < 0 || t->prefetch > 1) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
         t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1)
@@ -761,7 +755,7 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
     if ((S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
         st = S->kind == GCP_SAMPLER_OBSERVED ? ensure_observed(h, s) : ensure_hash(h, s);
         if (st != GCP_OK) return st;
-        if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 1023) / 1024)) != GCP_OK) return st;
+        if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 1023) / 1024, s)) != GCP_OK) return st;
         if ((st = ensure_zero_list(h, S->q)) != GCP_OK) return st;
     }
     GCP_CUDA_TRY(cudaStreamSynchronize(s));

@@ -168,38 +168,6 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16* __restrict__ p)
     return out;
 }
 
-// Row loads that ask L2 to keep the line (evict-last priority for every
-// access of the policy): factor rows are gathered again and again within a
-// launch and across launches, while the streamed data (nonzero records, dense
-// values) is read with the evict-first loads below.
-__device__ __forceinline__ uint64_t l2_keep_policy()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ float4 load4_keep(const float* __restrict__ p, uint64_t pol)
-{
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-
-__device__ __forceinline__ float4 load4_keep(const __nv_bfloat16* __restrict__ p, uint64_t pol)
-{
-    uint32_t lo, hi;
-    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(lo), "=r"(hi) : "l"(p), "l"(pol));
-    float4 out;
-    out.x = __uint_as_float(lo << 16);
-    out.y = __uint_as_float(lo & 0xFFFF0000u);
-    out.z = __uint_as_float(hi << 16);
-    out.w = __uint_as_float(hi & 0xFFFF0000u);
-    return out;
-}
-
 __device__ __forceinline__ float4 mul4(float4 a, float4 b)
 {
     return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);

@@ -35,12 +35,11 @@
 
 namespace gcpk {
 
-// LAYOUT 0: the group walk; 1: the prefetch layout; 2: the pipelined walk.
+// LAYOUT 0: the group walk; 1: the prefetch layout.
 template <int D, int L, int NC, bool BF16, int LAYOUT>
 __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_kernel(const GradArgs a)
 {
     constexpr bool PF = LAYOUT == 1;
-    constexpr bool PIPE = LAYOUT == 2;
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     bool verify = false;
     if (a.dr.stream_dev) {
         actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
-        if (early && !PF && !PIPE) {
+        if (early && !PF) {
             verify = true;
         } else {
             if (early && actual != stream) make_draw<D>(a.dr, wb0 + sub, actual, my);  // mispredicted: redraw
@@ -117,125 +116,6 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     for (int k = 0; k < D; ++k)
         gdst[k] = k < d ? a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k] : nullptr;
 
-    if constexpr (PIPE) {
-        // The pipelined walk (one float4 chunk per lane, a warp's 32 draws per
-        // batch, groups of L lanes walking their L draws): the row gathers of
-        // step b + 1 are issued before step b is consumed, and the next batch's
-        // descriptors (Philox, the record or value gather) before this batch's
-        // walk, so a warp keeps two rounds of loads in flight.  Factor rows are
-        // read with an L2 evict-last hint.
-        static_assert(NC == 1, "pipelined walk: one chunk per lane");
-        const uint64_t keep = l2_keep_policy();
-        const int col = gl * 4;
-        const bool colok = col < rank;
-        const int64_t round = nwarps * 32;
-        // the rows of step b (draw gbase + b of the batch in `src_draw`)
-        auto fetch_rows = [&](const Draw<D>& src_draw, int b, float4 (&r)[D]) {
-            const int src = gbase + b;
-            const bool v = __shfl_sync(kFull, static_cast<int>(src_draw.valid), src) != 0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const uint32_t i = __shfl_sync(kFull, src_draw.ix[k], src);
-                if (k >= d)
-                    r[k] = make_float4(1.f, 1.f, 1.f, 1.f);
-                else if (v && colok)
-                    r[k] = load4_keep(static_cast<const T*>(a.A[k]) + static_cast<size_t>(i) * ld + col, keep);
-                else
-                    r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        };
-        Draw<D> nxt;
-        for (int64_t wb = wb0; wb < a.dr.n_total; wb += round) {
-            const bool more = wb + round < a.dr.n_total;  // warp-uniform
-            if (more) make_draw<D>(a.dr, wb + round + sub, stream, nxt);
-            float4 rc[D], rn[D];
-            fetch_rows(my, 0, rc);
-#pragma unroll 2
-            for (int b = 0; b < L; ++b) {
-                if (b + 1 < L) fetch_rows(my, b + 1, rn);
-                // this step's draw: its descriptor, shuffled again from the batch
-                struct {
-                    uint32_t ix[D];
-                    float x, w;
-                    int cls;
-                    bool valid;
-                    float4 r[D];
-                } cur;
-                {
-                    const int src = gbase + b;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        cur.ix[k] = __shfl_sync(kFull, my.ix[k], src);
-                        cur.r[k] = rc[k];
-                    }
-                    cur.x = __shfl_sync(kFull, my.x, src);
-                    cur.w = __shfl_sync(kFull, my.w, src);
-                    cur.cls = __shfl_sync(kFull, my.cls, src);
-                    cur.valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
-                }
-                // m_i over this lane's chunk, reduced across the group
-                float4 p01, p23 = make_float4(1.f, 1.f, 1.f, 1.f), prod;
-                if constexpr (D == 3 || D == 4) {
-                    p01 = mul4(cur.r[0], cur.r[1]);
-                    p23 = D == 4 ? mul4(cur.r[2], cur.r[3]) : cur.r[2];
-                    prod = mul4(p01, p23);
-                } else {
-                    p01 = cur.r[0];
-                    prod = cur.r[0];
-#pragma unroll
-                    for (int k = 1; k < D; ++k) prod = mul4(prod, cur.r[k]);
-                }
-                float part = sum4(prod);
-#pragma unroll
-                for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
-                if (cur.valid && colok) {
-                    const float y = entry_y(a.loss, cur.cls, cur.x, part, cur.w);
-                    float4 upd[D];
-                    if constexpr (D == 4) {
-                        const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
-                        upd[0] = mul4(yp23, cur.r[1]);
-                        upd[1] = mul4(yp23, cur.r[0]);
-                        upd[2] = mul4(yp01, cur.r[3]);
-                        upd[3] = mul4(yp01, cur.r[2]);
-                    } else if constexpr (D == 3) {
-                        const float4 yr2 = scale4(y, cur.r[2]);
-                        upd[0] = mul4(yr2, cur.r[1]);
-                        upd[1] = mul4(yr2, cur.r[0]);
-                        upd[2] = scale4(y, p01);
-                    } else {
-                        float4 pre[D], suf[D];
-                        pre[0] = make_float4(y, y, y, y);
-#pragma unroll
-                        for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], cur.r[k - 1]);
-                        suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
-#pragma unroll
-                        for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], cur.r[k + 1]);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) upd[k] = mul4(pre[k], suf[k]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        if (k >= d) continue;
-                        if ((a.smem_mask >> k) & 1u) {
-                            float* sp = sG + a.smem_off[k] + static_cast<size_t>(cur.ix[k]) * ld + col;
-                            atomicAdd(sp + 0, upd[k].x);
-                            atomicAdd(sp + 1, upd[k].y);
-                            atomicAdd(sp + 2, upd[k].z);
-                            atomicAdd(sp + 3, upd[k].w);
-                        } else {
-                            atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(cur.ix[k]) * ld + col),
-                                      upd[k]);
-                        }
-                    }
-                }
-                if (b + 1 < L) {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) rc[k] = rn[k];
-                }
-            }
-            if (more) my = nxt;
-        }
-    } else
     // warp-uniform loop over this warp's batches
     for (int64_t wb = wb0; wb < a.dr.n_total; wb += nwarps * per_warp) {
         if (wb != wb0) make_draw<D>(a.dr, wb + sub, stream, my);
@@ -438,18 +318,6 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
 template <int D, bool BF16>
 const void* grad_kernel_ptr(int L, int NC, int layout)
 {
-    if (layout == 2) {  // the pipelined walk: one chunk per lane
-        if (NC != 1) return nullptr;
-        switch (L) {
-        case 1: return reinterpret_cast<const void*>(&grad_kernel<D, 1, 1, BF16, 2>);
-        case 2: return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, 2>);
-        case 4: return reinterpret_cast<const void*>(&grad_kernel<D, 4, 1, BF16, 2>);
-        case 8: return reinterpret_cast<const void*>(&grad_kernel<D, 8, 1, BF16, 2>);
-        case 16: return reinterpret_cast<const void*>(&grad_kernel<D, 16, 1, BF16, 2>);
-        case 32: return reinterpret_cast<const void*>(&grad_kernel<D, 32, 1, BF16, 2>);
-        default: return nullptr;
-        }
-    }
     if (layout == 1) {
         if constexpr (D <= 4) {
             if (NC == 1 && L == 2) return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, 1>);

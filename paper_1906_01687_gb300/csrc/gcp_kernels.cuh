@@ -130,7 +130,7 @@ struct ZeroArgs {
     uint64_t seed, problem, stream;
     const int64_t* stream_dev;
     int64_t q;
-    int64_t first_tiles;      // tiles of 1024 candidates examined in parallel
+    int64_t first_tiles;      // tiles of 1024 candidates examined in parallel (one block each)
     int64_t cap;              // candidates allowed in total (64 batches)
     const unsigned long long* table;  // nonzero key hash (open addressing)
     uint64_t table_mask;
@@ -138,9 +138,9 @@ struct ZeroArgs {
     const float* obs_w;       // observed-entry pass (Section 4.4): accept v_i != 0 (else: not a nonzero)
     const float* obs_x;       //   and list x = X(i), w = w_obs v_i
     double w_obs;             //   |Omega_obs| / q (the list weight is rounded once, from FP64)
-    uint32_t* mask_words;     // accept bits of the parallel pass
-    int32_t* tile_counts;
-    int64_t* tile_offsets;
+    unsigned long long* tile_status;  // per tile: flag and count or inclusive prefix (zero between calls)
+    unsigned int* tile_ctr;   // next tile to take (zero between calls)
+    unsigned int* done_ctr;   // blocks finished (zero between calls)
     int64_t* count_out;       // accepted zeros kept (<= q)
     int32_t* status;
     // destination list (zero draw e goes to slot e)

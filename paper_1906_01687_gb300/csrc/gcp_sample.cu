@@ -169,15 +169,32 @@ cudaError_t launch_materialise(const DrawArgs& dr, int32_t* const idx[GCP_MAX_MO
 // Stratified zeros (Alg. 2): candidates c = 0, 1, 2, ... each a uniform
 // multi-index from the zero-candidate stream; a candidate is accepted when
 // c < cap and its linear key is not a nonzero's; the first q accepted in
-// candidate order are kept.  Three launches, no inter-block waiting:
-//   count   -- tiles of 1024 candidates in parallel: accept bits + counts;
-//   scan    -- one block: exclusive scan of the tile counts; if the parallel
-//              pass fell short, the same block continues through further
-//              candidates in order (1024 at a time) up to cap;
-//   scatter -- each tile writes its accepted candidates' slots below q.
+// candidate order are kept.  One launch, an ordered compaction with
+// decoupled look-back:
+//   - tiles of 1024 candidates, one per thread (every hash probe of a tile
+//     in flight at once);
+//   - a block takes the next tile in launch order from a counter, so every
+//     tile it waits on belongs to a block that is already running or done;
+//   - the block counts its accepted candidates and publishes the count, then
+//     looks back over the earlier tiles (adding their counts) until it meets
+//     a published prefix, and publishes its own inclusive prefix;
+//   - accepted candidates whose slot (prefix + rank in the tile) is below q
+//     are written;
+//   - the block of the last tile, once it knows the batch's total, continues
+//     in candidate order (1024 at a time) up to cap if the batch fell short,
+//     and records how many were kept;
+//   - the last block to finish clears the tile words and counters for the
+//     next call.
+// Every look-back wait is bounded: after kSpinLimit polls the block records
+// GCP_ERR_TIMEOUT and writes nothing (it cannot happen while the blocks it
+// waits on run, which the launch-order tiles guarantee).
 // ---------------------------------------------------------------------------
 constexpr int kZeroTile = 1024;
-constexpr int kZeroBlock = 1024;  // one candidate per thread: every hash probe of a tile in flight at once
+constexpr int kZeroBlock = 1024;  // one candidate per thread
+constexpr unsigned long long kTileCount = 1ull << 62;   // tile word: this tile's count is published
+constexpr unsigned long long kTilePrefix = 2ull << 62;  // tile word: its inclusive prefix is published
+constexpr unsigned long long kTileValue = (1ull << 62) - 1ull;
+constexpr int kSpinLimit = 1 << 21;
 
 template <int D>
 __device__ __forceinline__ bool zero_candidate(const ZeroArgs& a, uint64_t stream, int64_t c, uint32_t (&ix)[D])
@@ -221,36 +238,6 @@ __device__ __forceinline__ uint64_t zero_stream(const ZeroArgs& a)
     return a.stream_dev ? static_cast<uint64_t>(*a.stream_dev) : a.stream;
 }
 
-template <int D>
-__global__ void __launch_bounds__(kZeroBlock) zero_count_kernel(const ZeroArgs a)
-{
-    pdl_wait();
-    pdl_trigger();
-    __shared__ int warp_counts[kZeroBlock / 32];
-    const uint64_t stream = zero_stream(a);
-    const int64_t tile = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int count = 0;
-#pragma unroll 1
-    for (int r = 0; r < kZeroTile / kZeroBlock; ++r) {
-        const int64_t c = tile * kZeroTile + r * kZeroBlock + threadIdx.x;
-        uint32_t ix[D];
-        const bool acc = zero_candidate<D>(a, stream, c, ix);
-        const unsigned bits = __ballot_sync(0xFFFFFFFFu, acc);
-        if (lane == 0) {
-            a.mask_words[tile * (kZeroTile / 32) + r * (kZeroBlock / 32) + warp] = bits;
-            count += __popc(bits);
-        }
-    }
-    if (lane == 0) warp_counts[warp] = count;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int total = 0;
-        for (int w = 0; w < kZeroBlock / 32; ++w) total += warp_counts[w];
-        a.tile_counts[tile] = total;
-    }
-}
-
 // Block-wide exclusive scan of one int64 per thread (1024 threads); returns
 // the exclusive prefix, and the block total through *total.
 __device__ __forceinline__ int64_t block_exclusive_scan_1024(int64_t v, int64_t* sh_warp, int64_t* total)
@@ -283,99 +270,108 @@ __device__ __forceinline__ int64_t block_exclusive_scan_1024(int64_t v, int64_t*
 }
 
 template <int D>
-__global__ void __launch_bounds__(1024) zero_scan_kernel(const ZeroArgs a)
+__global__ void __launch_bounds__(kZeroBlock) zero_pass_kernel(const ZeroArgs a)
 {
     pdl_wait();
     pdl_trigger();
     __shared__ int64_t sh_warp[33];
-    int64_t running = 0;
-#pragma unroll 1
-    for (int64_t base = 0; base < a.first_tiles; base += 1024) {
-        const int64_t t = base + threadIdx.x;
-        const int64_t v = t < a.first_tiles ? a.tile_counts[t] : 0;
-        int64_t total;
-        const int64_t ex = block_exclusive_scan_1024(v, sh_warp, &total);
-        if (t < a.first_tiles) a.tile_offsets[t] = running + ex;
-        running += total;
-    }
-    // continuation in candidate order when the parallel pass fell short
+    __shared__ int64_t s_tile, s_excl;
+    __shared__ int s_ok, s_last;
+    if (threadIdx.x == 0) s_tile = static_cast<int64_t>(atomicAdd(a.tile_ctr, 1u));
+    __syncthreads();
+    const int64_t tile = s_tile;
     const uint64_t stream = zero_stream(a);
-    int64_t count = running;
-#pragma unroll 1
-    for (int64_t c0 = a.first_tiles * kZeroTile; count < a.q && c0 < a.cap; c0 += 1024) {
-        const int64_t c = c0 + threadIdx.x;
-        uint32_t ix[D];
-        const bool acc = zero_candidate<D>(a, stream, c, ix);
-        int64_t total;
-        const int64_t rank = block_exclusive_scan_1024(acc ? 1 : 0, sh_warp, &total);
-        if (acc && count + rank < a.q) write_zero<D>(a, count + rank, ix);
-        count += total;
-    }
-    const int64_t kept = count < a.q ? count : a.q;
+    uint32_t ix[D];
+    const bool acc = zero_candidate<D>(a, stream, tile * kZeroTile + threadIdx.x, ix);
+    int64_t total;
+    const int64_t rank = block_exclusive_scan_1024(acc ? 1 : 0, sh_warp, &total);
     if (threadIdx.x == 0) {
-        *a.count_out = kept;
-        if (kept < a.q) set_status(a.status, GCP_ERR_SAMPLE_SHORTFALL);
-    }
-    // unfilled slots of a shortfall carry weight 0
-    if (a.out_w) {
-        for (int64_t s = kept + threadIdx.x; s < a.q; s += blockDim.x) {
-            uint32_t ix[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) ix[k] = 0u;
-            write_zero<D>(a, s, ix);
-            a.out_w[s] = 0.0f;
-            if (a.out_x) a.out_x[s] = 0.0f;
+        unsigned long long* words = a.tile_status;
+        int64_t excl = 0;
+        int ok = 1;
+        if (tile == 0) {
+            atomicExch(words, kTilePrefix | static_cast<unsigned long long>(total));
+        } else {
+            atomicExch(words + tile, kTileCount | static_cast<unsigned long long>(total));
+            int64_t j = tile - 1;
+            int spins = 0;
+            while (true) {
+                const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(words + j);
+                const unsigned long long flag = w & ~kTileValue;
+                if (flag == 0ull) {
+                    if (++spins > kSpinLimit) {
+                        ok = 0;
+                        break;
+                    }
+                    continue;
+                }
+                excl += static_cast<int64_t>(w & kTileValue);
+                if (flag == kTilePrefix) break;
+                --j;  // stops at tile 0 at the latest: it publishes a prefix
+            }
+            if (ok)
+                atomicExch(words + tile, kTilePrefix | static_cast<unsigned long long>(excl + total));
+            else
+                set_status(a.status, GCP_ERR_TIMEOUT);
         }
+        s_excl = excl;
+        s_ok = ok;
     }
-}
+    __syncthreads();
+    const int64_t excl = s_excl;
+    const bool ok = s_ok != 0;
+    if (ok && acc && excl + rank < a.q) write_zero<D>(a, excl + rank, ix);
 
-template <int D>
-__global__ void __launch_bounds__(kZeroBlock) zero_scatter_kernel(const ZeroArgs a)
-{
-    pdl_wait();
-    pdl_trigger();
-    __shared__ unsigned words[kZeroTile / 32];
-    __shared__ int prefix[kZeroTile / 32];
-    const int64_t tile = blockIdx.x;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < kZeroTile / 32) words[threadIdx.x] = a.mask_words[tile * (kZeroTile / 32) + threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int v = __popc(words[lane]);
-        int inc = v;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int n = __shfl_up_sync(0xFFFFFFFFu, inc, off);
-            if (lane >= off) inc += n;
+    if (tile == a.first_tiles - 1) {
+        // the batch's total is known here: continue in candidate order if it fell short
+        int64_t count = ok ? excl + total : 0;
+#pragma unroll 1
+        for (int64_t c0 = a.first_tiles * kZeroTile; ok && count < a.q && c0 < a.cap; c0 += kZeroBlock) {
+            uint32_t cix[D];
+            const bool cacc = zero_candidate<D>(a, stream, c0 + threadIdx.x, cix);
+            int64_t ctotal;
+            const int64_t crank = block_exclusive_scan_1024(cacc ? 1 : 0, sh_warp, &ctotal);
+            if (cacc && count + crank < a.q) write_zero<D>(a, count + crank, cix);
+            count += ctotal;
         }
-        prefix[lane] = inc - v;
+        const int64_t kept = count < a.q ? count : a.q;
+        if (threadIdx.x == 0) {
+            *a.count_out = kept;
+            if (kept < a.q) set_status(a.status, ok ? GCP_ERR_SAMPLE_SHORTFALL : GCP_ERR_TIMEOUT);
+        }
+        // unfilled slots of a shortfall carry weight 0
+        if (a.out_w) {
+            for (int64_t s = kept + threadIdx.x; s < a.q; s += blockDim.x) {
+                uint32_t zix[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) zix[k] = 0u;
+                write_zero<D>(a, s, zix);
+                a.out_w[s] = 0.0f;
+                if (a.out_x) a.out_x[s] = 0.0f;
+            }
+        }
+    }
+
+    // the last block to finish clears the tile words and counters for the next call
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.done_ctr, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    const int64_t base = a.tile_offsets[tile];
-    if (base >= a.q) return;
-    const uint64_t stream = zero_stream(a);
-#pragma unroll 1
-    for (int r = 0; r < kZeroTile / kZeroBlock; ++r) {
-        const int widx = r * (kZeroBlock / 32) + (threadIdx.x >> 5);
-        const unsigned wbits = words[widx];
-        if (!((wbits >> lane) & 1u)) continue;
-        const int64_t slot = base + prefix[widx] + __popc(wbits & ((1u << lane) - 1u));
-        if (slot >= a.q) continue;
-        const int64_t c = tile * kZeroTile + r * kZeroBlock + threadIdx.x;
-        uint32_t ix[D];
-        draw_index<D>(a.dims, a.seed, a.problem, stream, a.tag, static_cast<uint64_t>(c), a.d, ix);
-        write_zero<D>(a, slot, ix);
+    if (s_last) {
+        for (int64_t t = threadIdx.x; t < a.first_tiles; t += blockDim.x) a.tile_status[t] = 0ull;
+        if (threadIdx.x == 0) {
+            *a.tile_ctr = 0u;
+            *a.done_ctr = 0u;
+        }
     }
 }
 
 template <int D>
 static cudaError_t zero_launch(const ZeroArgs& a, cudaStream_t s)
 {
-    const dim3 tiles(static_cast<unsigned>(a.first_tiles));
-    cudaError_t e = launch_pdl(zero_count_kernel<D>, tiles, dim3(kZeroBlock), 0, s, a);
-    if (e == cudaSuccess) e = launch_pdl(zero_scan_kernel<D>, dim3(1), dim3(1024), 0, s, a);
-    if (e == cudaSuccess) e = launch_pdl(zero_scatter_kernel<D>, tiles, dim3(kZeroBlock), 0, s, a);
-    return e;
+    return launch_pdl(zero_pass_kernel<D>, dim3(static_cast<unsigned>(a.first_tiles)), dim3(kZeroBlock), 0, s, a);
 }
 
 __global__ void __launch_bounds__(256) count_nonzero_kernel(const float* w, int64_t n, int64_t* out)

@@ -11,7 +11,12 @@ constant whose cube is log(1e-6), so that m = log(1e-6) + (planted
 structure).  The FP32 gradient must stay within 1e-5 of the FP64 oracle
 norm-wise and within the element-wise bound of each element's sum of
 |contributions|; the BF16 form within 1e-5 of the oracle at the BF16-rounded
-factors and 1e-2 at the FP32 factors.
+factors.  Against the oracle at the FP32 factors the BF16 form is far from
+1e-2 here: rounding a factor entry of about 2.4 to BF16 moves m by about
+0.05, which moves sigma(m) = e^m of every zero term by about 5%, and the
+terms cancel.  That is the storage format's own sensitivity, which the FP64
+oracle shows just the same between the two sets of factors; the test checks
+that the GPU's BF16 error equals it.
 """
 import math
 
@@ -67,7 +72,10 @@ def test_semi_stratified_cancellation_near_a_fitted_model():
         got = grad_to_numpy(G, RANK)
         if bf16:
             A_bf = [a.float()[:, :RANK].double().cpu().numpy() for a in F.A_bf16]
-            assert_grad_close(got, oracle.grad(DIMS, A_bf, oracle.BERNOULLI_LOGIT, SO))
-            assert rel_norm(got, ref) <= BF16_RTOL
+            ref_bf = oracle.grad(DIMS, A_bf, oracle.BERNOULLI_LOGIT, SO)
+            assert_grad_close(got, ref_bf)
+            storage = rel_norm(ref_bf, ref)  # the FP64 oracle's own change from rounding the factors
+            assert storage > BF16_RTOL  # the cancellation regime (about 0.2)
+            assert abs(rel_norm(got, ref) - storage) <= 1e-4 * storage
         else:
             assert_grad_close(got, ref, gabs)
