@@ -823,6 +823,15 @@ def form_batched(torch, gcp, stream, peak, tau=20, epochs=3):
     batch.run_epoch()
     stream.synchronize()
     t_batch = _time_calls(torch, batch.run_epoch, stream, epochs)
+    # the Adam step's share of a batched iteration (what fusing it into the
+    # gradient launch could save at most): a captured sequence of Adam steps alone
+    from paper_1906_01687_gb300.autotune import side_stream
+    g_adam = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_adam, stream=side_stream(stream)):
+        for _ in range(tau):
+            batch.batch.adam_step(stream=torch.cuda.current_stream())
+    t_adam = _time_calls(torch, g_adam.replay, stream, epochs) / tau
+    del g_adam
     singles = []
     for i, sp in enumerate(specs):
         run = GcpAdam(sp["X"], sp["A0"], sp["loss"], gcp.SAMPLER_UNIFORM, 0, sp["s"], 0, sp["est"], seed=sp["seed"],
@@ -853,7 +862,9 @@ def form_batched(torch, gcp, stream, peak, tau=20, epochs=3):
             "bytes_per_iteration": it_bytes,
             "batched": {"value": entries / t_batch, "ms_per_epoch": t_batch * 1e3,
                         "frac_of_measured_hbm": tau * it_bytes / t_batch / 1e9 / peak,
-                        "launches_per_iteration": 2, "tuning": batch.tuned},
+                        "launches_per_iteration": 2, "tuning": batch.tuned,
+                        "adam_us_per_iteration": t_adam * 1e6,
+                        "adam_share_of_iteration": t_adam * tau / t_batch},
             "sequential": {"value": entries / t_seq, "ms_per_epoch": t_seq * 1e3,
                            "frac_of_measured_hbm": tau * it_bytes / t_seq / 1e9 / peak,
                            "launches_per_iteration": 2 * len(specs)},
@@ -875,6 +886,9 @@ def main():
     ap.add_argument("--nnz", type=int, default=None,
                     help="nonzeros of the benchmark tensor (default 1e8); a smaller tensor of the same shape, "
                          "draws and rank is the small case for profiling")
+    ap.add_argument("--form", default=None, choices=["dense100", "count", "batched"],
+                    help="run one of the other workloads alone and print its JSON object (the command "
+                         "profiled for that workload's kernel breakdown)")
     ap.add_argument("--profile", type=int, default=0, metavar="ITERS",
                     help="only set up the benchmark's run and take ITERS eager GCP-Adam iterations, then exit "
                          "(the command profiled with ncu; prints one line of timing)")
@@ -889,7 +903,22 @@ def main():
         return reference_arm(args)
     if args.profile:
         return profile_arm(args)
+    if args.form:
+        return form_arm(args)
     return ours_arm(args)
+
+
+def form_arm(args):
+    """One of the other workloads alone (one JSON object)."""
+    import torch
+    from paper_1906_01687_gb300 import gcp
+    stream = torch.cuda.Stream()
+    peak, _ = peaks()
+    fn = {"dense100": lambda: form_dense100(torch, gcp, stream, peak, args),
+          "count": lambda: form_count(torch, gcp, stream, peak),
+          "batched": lambda: form_batched(torch, gcp, stream, peak)}[args.form]
+    print(json.dumps({"form": args.form, args.form: fn()}), flush=True)
+    return 0
 
 
 def profile_arm(args):

@@ -492,6 +492,27 @@ gcp_status gcp_batch_destroy(gcp_batch *b);
    <= 256; 0 = 256) and blocks (0 = one resident wave). */
 gcp_status gcp_batch_set_tuning(gcp_batch *b, int32_t block, int32_t grid_blocks);
 
+/* Shape of the batched gradient for every problem: chunks_per_lane (1..8;
+   0 = 1) float4 chunks of a factor row per lane, so a rank-r problem takes
+   L = the power of two (at most 32) covering ceil(ceil(r / 4) / chunks_per_lane)
+   lanes per draw and 32 / L draws per warp step (the rows per warp);
+   replica_target (0 = 64) and max_replicas (0 = 32; 1 = none): a mode whose
+   rows receive more than replica_target updates per iteration on average
+   spreads them over ceil(updates / replica_target) replica slabs, at most
+   max_replicas (the pre-reduction width before the Adam step's fold).
+   Re-uploads the problem table and reallocates the replica slabs
+   (cudaMalloc; waits for the stream): call it before any stream capture.
+   Changes only the summation order of the gradients.  Errors:
+   GCP_ERR_INVALID_ARG (values out of range), GCP_ERR_NO_MEMORY,
+   GCP_ERR_CUDA. */
+gcp_status gcp_batch_set_shape(gcp_batch *b, int32_t chunks_per_lane, int32_t replica_target, int32_t max_replicas,
+                               gcp_stream_t stream);
+
+/* The shape problem `problem` runs with: lanes per draw, chunks per lane and
+   the replica slabs of each mode (host outputs; replicas holds 4 entries,
+   0 beyond the problem's modes). */
+gcp_status gcp_batch_get_shape(gcp_batch *b, int32_t problem, int32_t *lanes, int32_t *chunks, int32_t *replicas);
+
 /* The sampled gradients of every problem (Eq. (4.3), Alg. 1) into G: warps
    take 32 consecutive draws of one problem at a time from a table of all
    problems' draws; a mode whose rows receive many updates adds them into

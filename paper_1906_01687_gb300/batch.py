@@ -109,11 +109,17 @@ class GcpAdamBatch:
         return sum(p["S"].q for p in self.problems)
 
     # -- launch shape ---------------------------------------------------------------
-    def autotune(self, launches: int = 10):
-        """Times the batched gradient for block sizes and grid sizes on a
-        throwaway copy of the batch (same draws and shapes) and keeps the
-        fastest; returns it with its time."""
-        import statistics
+    SHAPES = [(cpl, target, maxr) for cpl in (1, 2, 4) for target, maxr in ((64, 32), (16, 32), (0, 1))]
+
+    def autotune(self, iterations: int = 10, shapes=None):
+        """Chooses the batched gradient's shape -- threads per block and blocks
+        (grid waves), chunks per lane (the rows per warp step) and the replica
+        width (the pre-reduction of heavily hit rows) -- by timing whole
+        iterations (gradient + Adam with the fold) on a throwaway copy of the
+        batch (same draws and shapes), captured in a CUDA graph as an epoch
+        is; keeps the fastest.  Returns it with its time per iteration and the
+        per-problem shapes it gives."""
+        from .autotune import side_stream
         shadow = []
         with torch.cuda.stream(self.stream):
             for p in self.problems:
@@ -124,26 +130,44 @@ class GcpAdamBatch:
                 q.update(F=F, state=st, G=F.like(), B=F.like(), C=F.like(), SA=F.like(), SB=F.like(), SC=F.like())
                 shadow.append(q)
         tb = gcp.Batch(shadow, stream=self.stream)
-        best, best_t = None, float("inf")
+        cap = side_stream(self.stream)
         sms = torch.cuda.get_device_properties(self.stream.device).multi_processor_count
-        for block in (128, 256):
-            for waves in (0, 1, 2, 4):
-                grid = 0 if waves == 0 else sms * waves * (256 // block)
-                tb.set_tuning(block, grid)
-                tb.grad(stream=self.stream)
-                self.stream.synchronize()
-                evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                       for _ in range(launches)]
-                with torch.cuda.stream(self.stream):
-                    torch.cuda._sleep(50_000_000)
-                    for a, b in evs:
+        best, best_t, tried = None, float("inf"), 0
+        for cpl, target, maxr in (shapes or self.SHAPES):
+            tb.set_shape(cpl, target, maxr, stream=self.stream)
+            for block in (128, 256):
+                for waves in (0, 1, 2, 4):
+                    grid = 0 if waves == 0 else sms * waves * (256 // block)
+                    tb.set_tuning(block, grid)
+                    with torch.cuda.stream(self.stream):
+                        tb.iteration(stream=self.stream)
+                    self.stream.synchronize()
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=cap):
+                        for _ in range(iterations):
+                            tb.iteration(stream=cap)
+                    with torch.cuda.stream(self.stream):
+                        g.replay()
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         a.record(self.stream)
-                        tb.grad(stream=self.stream)
+                        g.replay()
+                        g.replay()
                         b.record(self.stream)
-                self.stream.synchronize()
-                t = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
-                if t < best_t:
-                    best, best_t = dict(block=block, grid_blocks=grid), t
+                    self.stream.synchronize()
+                    t = a.elapsed_time(b) * 1e-3 / (2 * iterations)
+                    del g
+                    tried += 1
+                    if t < best_t:
+                        best_t = t
+                        best = dict(block=block, grid_blocks=grid, chunks_per_lane=cpl, replica_target=target,
+                                    max_replicas=maxr)
         tb.close()
-        self.batch.set_tuning(**best)
-        return dict(best=best, seconds=best_t)
+        self.set_shape(**best)
+        shapes = [self.batch.get_shape(i) for i in range(len(self.problems))]
+        return dict(best=best, seconds_per_iteration=best_t, tried=tried, shapes=shapes)
+
+    def set_shape(self, block=0, grid_blocks=0, chunks_per_lane=0, replica_target=0, max_replicas=0):
+        """Sets the batched gradient's launch and per-problem shape (before capture)."""
+        self.batch.set_shape(chunks_per_lane, replica_target, max_replicas, stream=self.stream)
+        self.batch.set_tuning(block, grid_blocks)
+        self.graph = None

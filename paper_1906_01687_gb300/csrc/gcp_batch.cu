@@ -427,6 +427,8 @@ struct gcp_batch {
     int64_t total_work = 0, total_param4 = 0, est_blocks = 0;
     int num_sms = 1;
     int block = 0, grid = 0;
+    std::vector<BatchDesc> host_desc;  // the uploaded table, for reshaping
+    int chunks_per_lane = 1, replica_target = 64, max_replicas = 32;
 };
 
 namespace {
@@ -447,6 +449,26 @@ gcp_status to_status(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? GCP_ERR_NO_MEMORY : GCP_ERR_CUDA;
 }
 
+// Lanes per draw and float4 chunks per lane of a rank-r problem: a lane takes
+// up to cpl chunks of a row, and the lanes per draw are the power of two that
+// covers the rest (at most 32); more chunks per lane, more draws per warp step.
+void lanes_chunks(int rank, int cpl, int32_t* L_out, int32_t* NC_out)
+{
+    const int chunks = (rank + 3) / 4;
+    const int per = (chunks + cpl - 1) / cpl;
+    int L = 1;
+    while (L < per && L < 32) L <<= 1;
+    *L_out = L;
+    *NC_out = (chunks + L - 1) / L;
+}
+
+// Replica slabs of mode k: ceil(updates per row / target), at most max_reps.
+int64_t replicas_for(const BatchDesc& d, int k, int target, int max_reps)
+{
+    const double hits = static_cast<double>(d.s) / static_cast<double>(d.dims[k]);
+    return std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(std::ceil(hits / target)), max_reps));
+}
+
 gcp_status fill_desc(const gcp_batch_problem& p, BatchDesc* o)
 {
     const gcp_tensor& X = p.X;
@@ -463,11 +485,7 @@ gcp_status fill_desc(const gcp_batch_problem& p, BatchDesc* o)
     o->ld = F.ld;
     o->rank = F.rank;
     o->loss = p.loss;
-    const int chunks = (F.rank + 3) / 4;
-    int L = 1;
-    while (L < chunks && L < 32) L <<= 1;
-    o->L = L;
-    o->NC = (chunks + L - 1) / L;
+    lanes_chunks(F.rank, 1, &o->L, &o->NC);
     o->bf16 = F.bf16 ? 1 : 0;
     double omega = 1.0;
     uint64_t stride = 1;
@@ -561,9 +579,7 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
     int64_t rep_floats = 0;
     for (int i = 0; i < count; ++i) {
         for (int k = 0; k < desc[i].d; ++k) {
-            const double hits = static_cast<double>(desc[i].s) / static_cast<double>(desc[i].dims[k]);
-            const int64_t r = std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(std::ceil(hits / kBatchRepTarget)),
-                                                                      kBatchMaxReps));
+            const int64_t r = replicas_for(desc[i], k, static_cast<int>(kBatchRepTarget), static_cast<int>(kBatchMaxReps));
             desc[i].reps[k] = static_cast<uint32_t>(r);
             desc[i].rep_stride[k] = static_cast<uint64_t>(desc[i].dims[k]) * desc[i].ld;
             if (r > 1) {
@@ -613,7 +629,74 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
         return fail(e);
     if ((e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
+    b->host_desc = desc;
     *out = b;
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_set_shape(gcp_batch* b, int32_t chunks_per_lane, int32_t replica_target, int32_t max_replicas,
+                               gcp_stream_t stream)
+{
+    if (!b || chunks_per_lane < 0 || chunks_per_lane > 8 || replica_target < 0 || max_replicas < 0 ||
+        max_replicas > 1024)
+        return GCP_ERR_INVALID_ARG;
+    const int cpl = chunks_per_lane > 0 ? chunks_per_lane : 1;
+    const int target = replica_target > 0 ? replica_target : static_cast<int>(kBatchRepTarget);
+    const int maxr = max_replicas > 0 ? max_replicas : static_cast<int>(kBatchMaxReps);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<BatchDesc> desc = b->host_desc;
+    std::vector<int64_t> rep_off(desc.size() * kBatchMaxD, -1);
+    int64_t rep_floats = 0;
+    for (size_t i = 0; i < desc.size(); ++i) {
+        lanes_chunks(desc[i].rank, cpl, &desc[i].L, &desc[i].NC);
+        for (int k = 0; k < desc[i].d; ++k) {
+            const int64_t r = replicas_for(desc[i], k, target, maxr);
+            desc[i].reps[k] = static_cast<uint32_t>(r);
+            if (r > 1) {
+                rep_off[i * kBatchMaxD + k] = rep_floats;
+                rep_floats += r * static_cast<int64_t>(desc[i].rep_stride[k]);
+            }
+        }
+    }
+    // new replica slabs (zeroed) once the stream has finished with the old ones
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return to_status(e);
+    float* rep = nullptr;
+    if (rep_floats > 0) {
+        if ((e = cudaMalloc(reinterpret_cast<void**>(&rep), sizeof(float) * rep_floats)) != cudaSuccess)
+            return to_status(e);
+        if ((e = cudaMemsetAsync(rep, 0, sizeof(float) * rep_floats, s)) != cudaSuccess) {
+            cudaFree(rep);
+            return to_status(e);
+        }
+    }
+    for (size_t i = 0; i < desc.size(); ++i)
+        for (int k = 0; k < desc[i].d; ++k) {
+            const int64_t off = rep_off[i * kBatchMaxD + k];
+            desc[i].R[k] = off >= 0 ? rep + off : nullptr;
+        }
+    if ((e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(BatchDesc) * desc.size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cudaFree(rep);
+        return to_status(e);
+    }
+    cudaFree(b->d_rep);
+    b->d_rep = rep;
+    b->host_desc = desc;
+    b->chunks_per_lane = cpl;
+    b->replica_target = target;
+    b->max_replicas = maxr;
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_get_shape(gcp_batch* b, int32_t problem, int32_t* lanes, int32_t* chunks, int32_t* replicas)
+{
+    if (!b || problem < 0 || problem >= b->count || !lanes || !chunks || !replicas) return GCP_ERR_INVALID_ARG;
+    const BatchDesc& d = b->host_desc[static_cast<size_t>(problem)];
+    *lanes = d.L;
+    *chunks = d.NC;
+    for (int k = 0; k < kBatchMaxD; ++k) replicas[k] = k < d.d ? static_cast<int32_t>(d.reps[k]) : 0;
     return GCP_OK;
 }
 

@@ -125,6 +125,8 @@ _SIGS = {
     "gcp_batch_create": ([_P(_vp), _P(gcp_batch_problem), _i32, _vp], ctypes.c_int),
     "gcp_batch_destroy": ([_vp], ctypes.c_int),
     "gcp_batch_set_tuning": ([_vp, _i32, _i32], ctypes.c_int),
+    "gcp_batch_set_shape": ([_vp, _i32, _i32, _i32, _vp], ctypes.c_int),
+    "gcp_batch_get_shape": ([_vp, _i32, _P(_i32), _P(_i32), _P(_i32)], ctypes.c_int),
     "gcp_batch_grad": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_adam_step": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_iteration": ([_vp, _vp], ctypes.c_int),
@@ -573,6 +575,19 @@ class Batch:
 
     def set_tuning(self, block=0, grid_blocks=0):
         _check(_lib.gcp_batch_set_tuning(self._b, int(block), int(grid_blocks)), "gcp_batch_set_tuning")
+
+    def set_shape(self, chunks_per_lane=0, replica_target=0, max_replicas=0, stream=None):
+        """Rows per warp (chunks per lane) and replica slabs of every problem (before graph capture)."""
+        _check(_lib.gcp_batch_set_shape(self._b, int(chunks_per_lane), int(replica_target), int(max_replicas),
+                                        _stream(stream)), "gcp_batch_set_shape")
+
+    def get_shape(self, problem):
+        """(lanes per draw, chunks per lane, replica slabs per mode) of one problem."""
+        L, NC = ctypes.c_int32(0), ctypes.c_int32(0)
+        reps = (ctypes.c_int32 * 4)()
+        _check(_lib.gcp_batch_get_shape(self._b, int(problem), ctypes.byref(L), ctypes.byref(NC), reps),
+               "gcp_batch_get_shape")
+        return dict(lanes=L.value, chunks=NC.value, replicas=[r for r in reps if r > 0])
 
     def _call(self, name, stream):
         _check(getattr(_lib, name)(self._b, _stream(stream)), name)

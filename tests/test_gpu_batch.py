@@ -119,10 +119,42 @@ def test_batch_autotune_and_graph_replay():
     from paper_1906_01687_gb300.batch import GcpAdamBatch
     specs = make_specs(5000)
     run = GcpAdamBatch(specs, tau=4, alpha=0.01, autotune=True)
-    assert run.tuned["seconds"] > 0
+    assert run.tuned["seconds_per_iteration"] > 0 and run.tuned["tried"] >= 8
+    assert set(run.tuned["best"]) == {"block", "grid_blocks", "chunks_per_lane", "replica_target", "max_replicas"}
+    assert len(run.tuned["shapes"]) == len(specs)
     sts = run.fit(max_epochs=3)
     assert all(st["iter"] == 12 for st in sts)
     assert all(math.isfinite(st["F"]) for st in sts)
+
+
+@pytest.mark.parametrize("cpl,target,maxr", [(2, 0, 0), (4, 16, 32), (1, 0, 1), (8, 8, 64)])
+def test_batch_shapes_give_the_same_gradients(cpl, target, maxr):
+    """Every per-problem shape (chunks per lane, replica width) gives each
+    problem the oracle's gradient on the same draws (only the summation order
+    changes), and the lanes and replicas follow the rule gcp_batch_set_shape
+    states."""
+    from paper_1906_01687_gb300.batch import GcpAdamBatch
+    specs = make_specs(20_000)
+    run = GcpAdamBatch(specs, tau=5, alpha=0.01)
+    run.set_shape(chunks_per_lane=cpl, replica_target=target, max_replicas=maxr)
+    run.batch.grad()
+    torch.cuda.synchronize()
+    for i, (sp, p) in enumerate(zip(specs, run.problems)):
+        dims, rank = sp["X"].shape, sp["A0"][0].shape[1]
+        shape = run.batch.get_shape(i)
+        chunks = (rank + 3) // 4
+        per = -(-chunks // cpl)
+        L = 1
+        while L < per and L < 32:
+            L *= 2
+        assert shape["lanes"] == L and shape["chunks"] == -(-chunks // L)
+        t, m = (target or 64), (maxr or 32)
+        want = [max(1, min(math.ceil(sp["s"] / n / t), m)) for n in dims]
+        assert shape["replicas"] == want
+        XO = oracle.Tensor(dims, dense=sp["X"].astype(np.float64))
+        SO = oracle.sample(XO, oracle.UNIFORM, 0, sp["s"], sp["seed"], 0, problem=i)
+        assert_grad_close(grad_to_numpy(p["G"], rank), oracle.grad(dims, f64(sp["A0"]), sp["loss"], SO),
+                          oracle.grad_abs(dims, f64(sp["A0"]), sp["loss"], SO))
 
 
 def test_batch_rejects_sparse_and_wide_problems():
