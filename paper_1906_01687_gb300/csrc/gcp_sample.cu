@@ -176,8 +176,9 @@ cudaError_t launch_materialise(const DrawArgs& dr, int32_t* const idx[GCP_MAX_MO
 //   - a block takes the next tile in launch order from a counter, so every
 //     tile it waits on belongs to a block that is already running or done;
 //   - the block counts its accepted candidates and publishes the count, then
-//     looks back over the earlier tiles (adding their counts) until it meets
-//     a published prefix, and publishes its own inclusive prefix;
+//     looks back over the earlier tiles, a window of 32 per round trip
+//     (adding their counts), until it meets a published prefix, and
+//     publishes its own inclusive prefix;
 //   - accepted candidates whose slot (prefix + rank in the tile) is below q
 //     are written;
 //   - the block of the last tile, once it knows the batch's total, continues
@@ -285,37 +286,55 @@ __global__ void __launch_bounds__(kZeroBlock) zero_pass_kernel(const ZeroArgs a)
     const bool acc = zero_candidate<D>(a, stream, tile * kZeroTile + threadIdx.x, ix);
     int64_t total;
     const int64_t rank = block_exclusive_scan_1024(acc ? 1 : 0, sh_warp, &total);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // warp 0 publishes this tile's count and looks back over the earlier
+        // tiles 32 at a time: one round trip reads a window of 32 tile words;
+        // the nearest published prefix in the window ends the look-back once
+        // every tile between it and this one has published its count
+        const int lane = threadIdx.x;
         unsigned long long* words = a.tile_status;
         int64_t excl = 0;
         int ok = 1;
         if (tile == 0) {
-            atomicExch(words, kTilePrefix | static_cast<unsigned long long>(total));
+            if (lane == 0) atomicExch(words, kTilePrefix | static_cast<unsigned long long>(total));
         } else {
-            atomicExch(words + tile, kTileCount | static_cast<unsigned long long>(total));
-            int64_t j = tile - 1;
+            if (lane == 0) atomicExch(words + tile, kTileCount | static_cast<unsigned long long>(total));
+            int64_t hi = tile - 1;  // the window is tiles hi, hi - 1, ..., hi - 31 (lane i: tile hi - i)
             int spins = 0;
             while (true) {
-                const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(words + j);
+                const int64_t j = hi - lane;
+                unsigned long long w = kTilePrefix | 0ull;  // before tile 0: an empty prefix
+                if (j >= 0) w = *reinterpret_cast<volatile unsigned long long*>(words + j);
                 const unsigned long long flag = w & ~kTileValue;
-                if (flag == 0ull) {
+                const unsigned not_ready = __ballot_sync(0xFFFFFFFFu, flag == 0ull);
+                const unsigned prefix = __ballot_sync(0xFFFFFFFFu, flag == kTilePrefix);
+                const int nearest = prefix ? __ffs(prefix) - 1 : 32;  // lowest lane: the nearest tile
+                const unsigned needed = nearest >= 31 ? 0xFFFFFFFFu : (2u << nearest) - 1u;
+                if (not_ready & needed) {
                     if (++spins > kSpinLimit) {
                         ok = 0;
                         break;
                     }
                     continue;
                 }
-                excl += static_cast<int64_t>(w & kTileValue);
-                if (flag == kTilePrefix) break;
-                --j;  // stops at tile 0 at the latest: it publishes a prefix
+                int64_t v = (lane <= nearest && j >= 0) ? static_cast<int64_t>(w & kTileValue) : 0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+                excl += v;
+                if (nearest < 32) break;
+                hi -= 32;
             }
-            if (ok)
-                atomicExch(words + tile, kTilePrefix | static_cast<unsigned long long>(excl + total));
-            else
-                set_status(a.status, GCP_ERR_TIMEOUT);
+            if (lane == 0) {
+                if (ok)
+                    atomicExch(words + tile, kTilePrefix | static_cast<unsigned long long>(excl + total));
+                else
+                    set_status(a.status, GCP_ERR_TIMEOUT);
+            }
         }
-        s_excl = excl;
-        s_ok = ok;
+        if (lane == 0) {
+            s_excl = excl;
+            s_ok = ok;
+        }
     }
     __syncthreads();
     const int64_t excl = s_excl;
