@@ -558,6 +558,12 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    prefetch = 1 (one chunk per lane, 2 or 4 lanes, at most 4 modes): a group
    issues the row loads of all its draws before consuming any (one round
    trip to L2 per group walk instead of one per draw; more registers).
+   prefetch = 2 (one chunk per lane, 1 to 8 lanes, 3 or 4 modes, group_draws
+   = 0): the staged walk -- every lane copies its chunk of every row of its
+   group's draws into shared memory (cp.async) and the group walks them from
+   there (one round trip per batch, no registers held; block / 32 x lanes x
+   modes x 32 x 16 bytes of shared memory, 8 with BF16 rows; shared-memory
+   accumulation of G is off with it).
    early_draws = 1: where the draws read nothing but the data tensor (uniform
    sampling, semi-stratified sampling, the nonzero draws of stratified
    sampling, or uniform over a sparse tensor whose nonzero table was built by

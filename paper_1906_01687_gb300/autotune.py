@@ -3,8 +3,8 @@
 For one handle, factor layout and sampling spec, times ``gcp_grad`` for a set
 of candidate shapes -- lanes per draw x float4 chunks per lane (rows per
 warp), threads per block, replica slabs per mode (the pre-reduction width of
-the L2 accumulation), the draw layout (group walk or prefetch) and
-optional shared-memory accumulation -- with CUDA
+the L2 accumulation), the draw layout (group walk, prefetch or staged
+walk) and optional shared-memory accumulation -- with CUDA
 events around back-to-back launches, and keeps the fastest through
 ``gcp_set_tuning``.  A shape changes only the summation order of the
 gradient, never the draws.
@@ -41,6 +41,8 @@ def candidates(rank: int) -> list:
             layouts.append(dict(group_draws=1))
         if NC == 1 and L in (2, 4):
             layouts.append(dict(prefetch=1))
+        if NC == 1 and L <= 8:
+            layouts.append(dict(prefetch=2))
         for layout in layouts:
             for block in (128, 256):
                 for reps, target in ((0, 0), (-1, 0), (8, 128), (32, 16)):

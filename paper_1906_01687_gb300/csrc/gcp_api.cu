@@ -325,7 +325,7 @@ struct Shape {
     uint32_t reps[GCP_MAX_MODES] = {};
     int64_t rep_floats = 0;  // replica workspace the shape needs
     int group = 0;           // group_draws layout
-    int pf = 0;              // prefetch layout
+    int pf = 0;              // 1: prefetch layout, 2: staged walk
     int early = 0;           // early descriptors (where the draw source allows)
     int layout() const { return pf; }
 };
@@ -394,15 +394,19 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     if (sh->block % 32 != 0 || sh->block > 256) return GCP_ERR_INVALID_ARG;  // kernels are built for <= 256
     sh->group = (t.group_draws == 1 && sh->L > 1) ? 1 : 0;
     sh->early = t.early_draws == 1 ? 1 : 0;
-    sh->pf = (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 1) &&
-              h->X.d == sh->D) ? 1 : 0;
+    sh->pf = 0;
+    if (t.prefetch == 2 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 2) && h->X.d == sh->D)
+        sh->pf = 2;  // the staged walk
+    else if (t.prefetch == 1 && !sh->group && grad_has_config(sh->D, sh->L, sh->NC, 1) && h->X.d == sh->D)
+        sh->pf = 1;  // the prefetch layout
     const int64_t per_warp = sh->group ? 32 / sh->L : 32;
     const int64_t warps = (n_total + per_warp - 1) / per_warp;
     const int64_t blocks_needed = std::max<int64_t>(1, (warps + sh->block / 32 - 1) / (sh->block / 32));
 
     // shared-memory accumulation of small, often-hit G_k (off unless tuned on:
     // shared-memory float atomics are slower than L2 vector reductions here)
-    const int64_t budget = t.smem_bytes > 0 ? t.smem_bytes : 0;
+    // (the staged walk's shared memory holds the row stage instead)
+    const int64_t budget = (t.smem_bytes > 0 && sh->pf != 2) ? t.smem_bytes : 0;
     const double min_hits = t.smem_min_hits >= 0 ? t.smem_min_hits / 10.0 : 2.0;
     const int64_t grid0 = std::min<int64_t>(blocks_needed, static_cast<int64_t>(h->num_sms) * 4);
     const double draws_per_cta = static_cast<double>(n_total) / static_cast<double>(std::max<int64_t>(grid0, 1));
@@ -418,6 +422,8 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     }
     sh->smem = static_cast<size_t>(used);
     if (sh->pf == 1 && sh->smem > 0) sh->pf = 0;  // the prefetch layout accumulates through L2 only
+    if (sh->pf == 2)  // the staged walk: each warp stages L draws x d rows x 32 lanes of 16 (BF16: 8) bytes
+        sh->smem = static_cast<size_t>(sh->block / 32) * sh->L * sh->D * 32 * (F->bf16 ? 8 : 16);
     const int bps = occupancy(sh->D, sh->L, sh->NC, F->bf16 != 0, sh->layout(), sh->block, sh->smem, h->device);
     const int64_t resident = static_cast<int64_t>(h->num_sms) * bps;
     // one resident wave; the kernel deals batches across all of its blocks
@@ -678,7 +684,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, 0)) return GCP_ERR_INVALID_ARG;
-    if (t->prefetch < 0 || t->prefetch > 1) return GCP_ERR_INVALID_ARG;
+    if (t->prefetch < 0 || t->prefetch > 2) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
         t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1)
@@ -827,7 +833,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     a.ld = F->ld;
     a.rank = F->rank;
     a.loss = loss;
-    a.smem_floats = static_cast<int32_t>(sh.smem / 4);
+    a.smem_floats = sh.pf == 2 ? 0 : static_cast<int32_t>(sh.smem / 4);  // accumulators to zero (not the stage)
     a.smem_mask = sh.mask;
     a.group_draws = sh.group;
     a.early = (sh.early && early_ok) ? 1 : 0;

@@ -168,6 +168,36 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16* __restrict__ p)
     return out;
 }
 
+// Asynchronous global -> shared copies (cp.async): a thread's own copies are
+// complete and visible to it after cp_async_wait_all().
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src)
+{
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
+// 4 factor entries staged in shared memory: float4 (FP32 rows) or 4 BF16 (8 bytes).
+__device__ __forceinline__ float4 staged4(const float4* p) { return *p; }
+__device__ __forceinline__ float4 staged4(const uint2* p)
+{
+    const uint2 raw = *p;
+    float4 out;
+    out.x = __uint_as_float(raw.x << 16);
+    out.y = __uint_as_float(raw.x & 0xFFFF0000u);
+    out.z = __uint_as_float(raw.y << 16);
+    out.w = __uint_as_float(raw.y & 0xFFFF0000u);
+    return out;
+}
+
 __device__ __forceinline__ float4 mul4(float4 a, float4 b)
 {
     return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);

@@ -35,11 +35,12 @@
 
 namespace gcpk {
 
-// LAYOUT 0: the group walk; 1: the prefetch layout.
+// LAYOUT 0: the group walk; 1: the prefetch layout; 2: the staged walk.
 template <int D, int L, int NC, bool BF16, int LAYOUT>
 __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_kernel(const GradArgs a)
 {
     constexpr bool PF = LAYOUT == 1;
+    constexpr bool STAGED = LAYOUT == 2;
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     bool verify = false;
     if (a.dr.stream_dev) {
         actual = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev));
-        if (early && !PF) {
+        if (early && !PF && !STAGED) {
             verify = true;
         } else {
             if (early && actual != stream) make_draw<D>(a.dr, wb0 + sub, actual, my);  // mispredicted: redraw
@@ -119,6 +120,74 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
     // warp-uniform loop over this warp's batches
     for (int64_t wb = wb0; wb < a.dr.n_total; wb += nwarps * per_warp) {
         if (wb != wb0) make_draw<D>(a.dr, wb + sub, stream, my);
+        if constexpr (STAGED) {
+            // staged walk (one chunk per lane): every lane copies its own chunk of
+            // every row of its group's L draws into shared memory (cp.async), waits
+            // once, and the group then walks its draws from shared memory: one
+            // round trip to L2 per batch instead of one per draw, and no registers
+            // held for the rows.  Layout [draw b][mode k][lane]: conflict-free.
+            static_assert(NC == 1 && D <= 4, "staged walk: one chunk per lane, at most 4 modes");
+            using C = std::conditional_t<BF16, uint2, float4>;
+            C* stage = reinterpret_cast<C*>(smem4) + static_cast<size_t>(threadIdx.x >> 5) * (L * D * 32);
+            const int col = gl * 4;
+            const bool colok = col < rank;
+#pragma unroll
+            for (int b = 0; b < L; ++b) {
+                const int src = gbase + b;
+                const bool v = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const uint32_t i = __shfl_sync(kFull, my.ix[k], src);
+                    if (v && colok) {
+                        const T* g = static_cast<const T*>(a.A[k]) + static_cast<size_t>(i) * ld + col;
+                        if constexpr (BF16)
+                            cp_async8(stage + (b * D + k) * 32 + lane, g);
+                        else
+                            cp_async16(stage + (b * D + k) * 32 + lane, g);
+                    }
+                }
+            }
+            cp_async_wait_all();
+#pragma unroll 1
+            for (int b = 0; b < L; ++b) {
+                const int src = gbase + b;
+                uint32_t ix[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) ix[k] = __shfl_sync(kFull, my.ix[k], src);
+                const float x = __shfl_sync(kFull, my.x, src);
+                const float w = __shfl_sync(kFull, my.w, src);
+                const int cls = __shfl_sync(kFull, my.cls, src);
+                const bool valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
+                float4 r[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    r[k] = (valid && colok) ? staged4(stage + (b * D + k) * 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 p01 = mul4(r[0], r[1]);
+                const float4 p23 = D == 4 ? mul4(r[2], r[3]) : r[D - 1];
+                float part = sum4(mul4(p01, p23));
+#pragma unroll
+                for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+                if (!valid || !colok) continue;  // no shuffles below this point in the iteration
+                const float y = entry_y(a.loss, cls, x, part, w);
+                float4 upd[D];
+                if constexpr (D == 4) {
+                    const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
+                    upd[0] = mul4(yp23, r[1]);
+                    upd[1] = mul4(yp23, r[0]);
+                    upd[2] = mul4(yp01, r[3]);
+                    upd[3] = mul4(yp01, r[2]);
+                } else {
+                    const float4 yr2 = scale4(y, r[2]);
+                    upd[0] = mul4(yr2, r[1]);
+                    upd[1] = mul4(yr2, r[0]);
+                    upd[2] = scale4(y, p01);
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd[k]);
+            }
+            continue;
+        }
         if constexpr (PF) {
             // prefetch layout (one chunk per lane): the descriptors and row loads
             // of all L draws of the group are issued before any is consumed, so
@@ -318,6 +387,15 @@ __global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_ker
 template <int D, bool BF16>
 const void* grad_kernel_ptr(int L, int NC, int layout)
 {
+    if (layout == 2) {  // the staged walk: one chunk per lane, at most 8 lanes, at most 4 modes
+        if constexpr (D <= 4) {
+            if (NC == 1 && L == 1) return reinterpret_cast<const void*>(&grad_kernel<D, 1, 1, BF16, 2>);
+            if (NC == 1 && L == 2) return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, 2>);
+            if (NC == 1 && L == 4) return reinterpret_cast<const void*>(&grad_kernel<D, 4, 1, BF16, 2>);
+            if (NC == 1 && L == 8) return reinterpret_cast<const void*>(&grad_kernel<D, 8, 1, BF16, 2>);
+        }
+        return nullptr;
+    }
     if (layout == 1) {
         if constexpr (D <= 4) {
             if (NC == 1 && L == 2) return reinterpret_cast<const void*>(&grad_kernel<D, 2, 1, BF16, 1>);

@@ -36,5 +36,7 @@ def test_every_rank_has_covering_candidates(autotune):
         cands = autotune.candidates(rank)
         assert all((c["lanes"], c["chunks"]) in shapes for c in cands)
         # the prefetch layout only where it is compiled: one chunk per lane, 2 or 4 lanes
-        assert all(c["lanes"] in (2, 4) and c["chunks"] == 1 for c in cands if c.get("prefetch"))
+        assert all(c["lanes"] in (2, 4) and c["chunks"] == 1 for c in cands if c.get("prefetch") == 1)
+        # the staged walk where it is compiled: one chunk per lane, at most 8 lanes
+        assert all(c["lanes"] <= 8 and c["chunks"] == 1 for c in cands if c.get("prefetch") == 2)
         assert all(c["block"] % 32 == 0 and c["block"] <= 256 for c in cands)

@@ -40,7 +40,8 @@ def test_dense_uniform_early_matches_oracle(dims, rank):
     S = g.Sampling(g.SAMPLER_UNIFORM, 0, 4099, seed=5, stream=9)
     SO = oracle.sample(XO, oracle.UNIFORM, 0, 4099, 5, 9)
     ref, ref_abs = oracle.grad(dims, f64(A), 0, SO), oracle.grad_abs(dims, f64(A), 0, SO)
-    for extra in (dict(), dict(group_draws=1), dict(prefetch=1), dict(grid_blocks=3)):
+    for extra in (dict(), dict(group_draws=1), dict(prefetch=1), dict(grid_blocks=3), dict(prefetch=2),
+                  dict(prefetch=2, grid_blocks=3)):
         g.gcp_set_tuning(h, early_draws=1, **extra)
         assert g.gcp_get_launch(h, F, 4099)["early_draws"] == 1
         assert_grad_close(grad_to_numpy(grad(h, F, 0, S), rank), ref, ref_abs)
@@ -59,7 +60,7 @@ def test_sparse_sources_early_match_oracle(kind):
     A = rng_factors(dims, rank, 4, scale=(0.5 / rank) ** 0.25)
     F = g.Factors(A)
     p, q = (0, 5000) if kind == "uniform" else (2000, 2500)
-    for layout in (0, 1):  # the group walk and the prefetch layout
+    for layout in (0, 1, 2):  # the group walk, the prefetch layout and the staged walk
         g.gcp_set_tuning(h, early_draws=1, prefetch=layout)
         for stream in (1, 2):  # the first uniform call builds the table and waits; the second draws early
             S = g.Sampling(g.SAMPLERS[kind], p, q, seed=7, stream=stream)
@@ -80,7 +81,7 @@ def test_device_stream_word_prediction_hits_and_misses():
     A = rng_factors(dims, rank, 7, scale=(0.5 / rank) ** 0.25)
     F = g.Factors(A)
     word = torch.zeros(1, dtype=torch.int64, device="cuda")
-    for early, layout in ((0, 0), (1, 0), (1, 1)):
+    for early, layout in ((0, 0), (1, 0), (1, 1), (1, 2)):
         g.gcp_set_tuning(h, early_draws=early, prefetch=layout)
         for v in (5, 6, 7, 7, 100, 3, 2**40, 2**40 + 1):
             word.fill_(v)
@@ -108,7 +109,7 @@ def test_iterations_with_early_draws_follow_waiting_run(sampler):
         S = g.Sampling(g.SAMPLERS[sampler], 6000, 6000, seed=3)
     A0 = rng_factors(dims, rank, 10, scale=0.5)
     out = {}
-    for early, layout in ((0, 0), (1, 0), (1, 1)):
+    for early, layout in ((0, 0), (1, 0), (1, 1), (1, 2)):
         h = g.Handle(T)
         g.gcp_set_tuning(h, early_draws=early, prefetch=layout)
         F = g.Factors(A0)
@@ -122,7 +123,7 @@ def test_iterations_with_early_draws_follow_waiting_run(sampler):
         out[(early, layout)] = (np.concatenate([a[:, :rank].double().cpu().numpy().ravel() for a in F.A]),
                                 g.read_state(st))
     a0, s0 = out[(0, 0)]
-    for key in ((1, 0), (1, 1)):
+    for key in ((1, 0), (1, 1), (1, 2)):
         a1, s1 = out[key]
         assert s0["iter"] == s1["iter"] == 30 and s0["t"] == s1["t"] == 30
         assert np.linalg.norm(a1 - a0) <= 1e-5 * np.linalg.norm(a0), key

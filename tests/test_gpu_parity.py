@@ -215,7 +215,8 @@ def test_every_launch_shape_agrees():
         for (lanes, chunks) in shapes:
             for acc in (dict(max_replicas=0), dict(), dict(max_replicas=8, replica_target=1),
                         dict(max_replicas=0, smem_bytes=65536, smem_min_hits=0), dict(group_draws=1),
-                        dict(group_draws=1, max_replicas=0), dict(prefetch=1), dict(prefetch=1, max_replicas=0)):
+                        dict(group_draws=1, max_replicas=0), dict(prefetch=1), dict(prefetch=1, max_replicas=0),
+                        dict(prefetch=2), dict(prefetch=2, max_replicas=0)):
                 for grid in (0, 3):
                     g.gcp_set_tuning(h, lanes=lanes, chunks=chunks, grid_blocks=grid, **acc)
                     G = run_grad(h, F, 0, S=S)
