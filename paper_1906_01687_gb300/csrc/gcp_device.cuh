@@ -133,19 +133,38 @@ __device__ __forceinline__ float loss_f(int loss, float x, float m)
     }
 }
 
-// y of a drawn entry: the semi-stratified nonzero subtracts the x = 0 term.
+// y of a drawn entry: the semi-stratified nonzero subtracts the x = 0 term
+// (Alg. 3).  For the log-link losses the m-dependent parts of g(x,m) and
+// g(0,m) are identical and cancel exactly: g(x,m) - g(0,m) = -2x (Gaussian)
+// or -x (Bernoulli-logit, Poisson-log); that difference is taken in closed
+// form, without evaluating the link twice and subtracting in FP32.
 __device__ __forceinline__ float entry_y(int loss, int cls, float x, float m, float w)
 {
-    float g = loss_g(loss, x, m);
-    if (cls == GCP_CLS_SEMI_NZ) g -= loss_g(loss, 0.0f, m);
-    return w * g;
+    if (cls == GCP_CLS_SEMI_NZ) {
+        switch (loss) {
+        case GCP_LOSS_GAUSSIAN: return w * (-2.0f * x);
+        case GCP_LOSS_BERNOULLI_LOGIT:
+        case GCP_LOSS_POISSON_LOG: return w * -x;
+        default: return w * (loss_g(loss, x, m) - loss_g(loss, 0.0f, m));
+        }
+    }
+    return w * loss_g(loss, x, m);
 }
 
+// The F-hat term of a drawn entry, with the same closed forms for the
+// semi-stratified nonzero: f(x,m) - f(0,m) = x^2 - 2xm (Gaussian) or -xm
+// (Bernoulli-logit, Poisson-log).
 __device__ __forceinline__ float entry_f(int loss, int cls, float x, float m, float w)
 {
-    float f = loss_f(loss, x, m);
-    if (cls == GCP_CLS_SEMI_NZ) f -= loss_f(loss, 0.0f, m);
-    return w * f;
+    if (cls == GCP_CLS_SEMI_NZ) {
+        switch (loss) {
+        case GCP_LOSS_GAUSSIAN: return w * (x * x - 2.0f * x * m);
+        case GCP_LOSS_BERNOULLI_LOGIT:
+        case GCP_LOSS_POISSON_LOG: return w * -(x * m);
+        default: return w * (loss_f(loss, x, m) - loss_f(loss, 0.0f, m));
+        }
+    }
+    return w * loss_f(loss, x, m);
 }
 
 // ---------------------------------------------------------------------------
