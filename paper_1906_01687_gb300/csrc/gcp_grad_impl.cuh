@@ -36,8 +36,18 @@
 namespace gcpk {
 
 // LAYOUT 0: the group walk; 1: the prefetch layout; 2: the staged walk.
+// Blocks of 256 per SM the registers must allow: four (64 registers) for the
+// group walk with one chunk per lane and 2 or more lanes, which fits without
+// spilling; three for the other group and staged walks of at most 4 modes;
+// two otherwise.
+template <int D, int L, int NC>
+constexpr int grad_min_blocks(int layout)
+{
+    return (D <= 4 && layout == 0 && NC == 1 && L >= 2) ? 4 : ((D <= 4 && layout != 1) ? 3 : 2);
+}
+
 template <int D, int L, int NC, bool BF16, int LAYOUT>
-__global__ void __launch_bounds__(256, (D <= 4 && LAYOUT != 1 ? 3 : 2)) grad_kernel(const GradArgs a)
+__global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_kernel(const GradArgs a)
 {
     constexpr bool PF = LAYOUT == 1;
     constexpr bool STAGED = LAYOUT == 2;
