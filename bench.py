@@ -744,7 +744,7 @@ def form_count(torch, gcp, stream, peak):
     the FP32 factors) on the same draws."""
     import oracle
     from paper_1906_01687_gb300 import synth
-    from paper_1906_01687_gb300.autotune import autotune, candidates
+    from paper_1906_01687_gb300.autotune import autotune, candidates, with_grids
     dims, rank, p, q = (6186, 24, 77, 32), 10, 100_000, 100_000
     idx, vals, _ = synth.count_tensor()
     h = gcp.Handle(gcp.DataTensor.coo(dims, idx, vals))
@@ -769,7 +769,7 @@ def form_count(torch, gcp, stream, peak):
     for name, bf16 in (("fp32", False), ("bf16", True)):
         F = gcp.Factors(A, bf16=bf16)
         tuned = autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream,
-                         configs=[dict(c, early_draws=1) for c in candidates(rank)])
+                         configs=with_grids([dict(c, early_draws=1) for c in candidates(rank)], p + q))
         G = F.like()
         t = _time_calls(torch, lambda: gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream), stream, 50)
         for x in G:

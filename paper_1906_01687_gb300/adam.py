@@ -108,7 +108,8 @@ class GcpAdam:
         def call(spec, stream):
             gcp.gcp_iteration(self.h, F, self.loss, spec, G, B, C, st, stream_dev=st[3:4], stream=stream,
                               **self.adam)
-        configs = [dict(c, early_draws=int(self.early_draws)) for c in candidates(F.rank)]
+        from .autotune import with_grids
+        configs = with_grids([dict(c, early_draws=int(self.early_draws)) for c in candidates(F.rank)], self.spec.count())
         return _autotune(self.h, F, self.loss, self.spec, configs=configs, launches=launches, stream=self.stream,
                          call=call, graph=True)
 

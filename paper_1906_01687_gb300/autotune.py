@@ -52,6 +52,22 @@ def candidates(rank: int) -> list:
     return out
 
 
+def with_grids(configs, n_draws: int) -> list:
+    """Each candidate twice: with the automatic grid (one resident wave when
+    the draws fill at least half of it) and with the grid that gives every
+    warp exactly one batch of draws (no idle warps in a small launch)."""
+    out = []
+    for cfg in configs:
+        out.append(dict(cfg))
+        block = cfg.get("block", 0) or 256
+        lanes = cfg.get("lanes", 0) or 1
+        per_warp = 32 // lanes if cfg.get("group_draws") else 32
+        warps = -(-int(n_draws) // per_warp)
+        fit = max(1, -(-warps // (block // 32)))
+        out.append(dict(cfg, grid_blocks=fit))
+    return out
+
+
 def side_stream(stream):
     """A stream other than `stream` (torch hands streams out round-robin from
     a small pool, so a new one can be `stream` itself)."""

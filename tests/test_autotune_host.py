@@ -40,3 +40,11 @@ def test_every_rank_has_covering_candidates(autotune):
         # the staged walk where it is compiled: one chunk per lane, at most 8 lanes
         assert all(c["lanes"] <= 8 and c["chunks"] == 1 for c in cands if c.get("prefetch") == 2)
         assert all(c["block"] % 32 == 0 and c["block"] <= 256 for c in cands)
+
+
+def test_grid_variants_fit_the_draws(autotune):
+    cands = autotune.with_grids([dict(lanes=4, chunks=1, block=128), dict(lanes=4, chunks=1, block=256, group_draws=1)],
+                                100_000)
+    assert len(cands) == 4 and "grid_blocks" not in cands[0]
+    assert cands[1]["grid_blocks"] == -(-(-(-100_000 // 32)) // 4)   # 3125 warps, 4 per block
+    assert cands[3]["grid_blocks"] == -(-(-(-100_000 // 8)) // 8)    # group draws: 8 per warp, 8 warps per block
