@@ -871,7 +871,7 @@ def form_batched(torch, gcp, stream, peak, tau=20, epochs=3):
             "bytes_per_iteration": it_bytes,
             "batched": {"value": entries / t_batch, "ms_per_epoch": t_batch * 1e3,
                         "frac_of_measured_hbm": tau * it_bytes / t_batch / 1e9 / peak,
-                        "launches_per_iteration": 2, "tuning": batch.tuned,
+                        "launches_per_iteration": 1 if batch.fused else 2, "tuning": batch.tuned,
                         "adam_us_per_iteration": t_adam * 1e6,
                         "adam_share_of_iteration": t_adam * tau / t_batch},
             "sequential": {"value": entries / t_seq, "ms_per_epoch": t_seq * 1e3,

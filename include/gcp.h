@@ -528,6 +528,19 @@ gcp_status gcp_batch_adam_step(gcp_batch *b, gcp_stream_t stream);
 /* gcp_batch_grad then gcp_batch_adam_step. */
 gcp_status gcp_batch_iteration(gcp_batch *b, gcp_stream_t stream);
 
+/* gcp_batch_iteration in one persistent launch: warps take every problem's
+   gradient batches and then every problem's Adam chunks from one queue, in
+   that order; a warp holding an Adam chunk of a problem waits until all of
+   that problem's gradient batches are done (they were taken earlier by warps
+   that never wait, so the wait ends; it is bounded all the same, and a wait
+   that runs out records GCP_ERR_TIMEOUT in that problem's state->status and
+   skips the chunk).  The problem's last Adam chunk advances its t and iter.
+   Same results as gcp_batch_iteration up to the summation order (the
+   replica slabs are folded in order).  Uses library-owned counters that
+   every launch leaves zero: launches on one batch must not overlap on the
+   GPU.  Errors: GCP_ERR_INVALID_ARG (NULL batch), GCP_ERR_CUDA. */
+gcp_status gcp_batch_iteration_fused(gcp_batch *b, gcp_stream_t stream);
+
 /* Every problem's F-hat on its fixed list into its state->F (FP64), one launch. */
 gcp_status gcp_batch_loss_est(gcp_batch *b, gcp_stream_t stream);
 

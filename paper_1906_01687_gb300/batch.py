@@ -21,7 +21,8 @@ from . import gcp
 class GcpAdamBatch:
     def __init__(self, specs: Sequence[dict], tau: int = 1000, kappa: int = 1, nu: float = 0.1,
                  alpha: float = 0.01, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
-                 lower: float = -math.inf, bf16: bool = False, stream=None, autotune: bool = False):
+                 lower: float = -math.inf, bf16: bool = False, stream=None, autotune: bool = False,
+                 fused: bool = False):
         """specs: dicts with X (dense numpy array or DataTensor), A0 (factor
         list), loss (int), s (draws per iteration), est (loss-estimate draws),
         seed, est_seed, and optional problem (key word; default its index)."""
@@ -52,17 +53,21 @@ class GcpAdamBatch:
         self.batch.loss_est(stream=self.stream)
         self.batch.epoch_begin(stream=self.stream)
         self.graph = None
+        self.fused = bool(fused)  # one launch per iteration (gradient and Adam fused) instead of two
         self.tuned = None
         if autotune:
             self.tuned = self.autotune()
 
     # -- launches ---------------------------------------------------------------
     def iteration(self):
-        self.batch.iteration(stream=self.stream)
+        if self.fused:
+            self.batch.iteration_fused(stream=self.stream)
+        else:
+            self.batch.iteration(stream=self.stream)
 
     def enqueue_epoch(self):
         for _ in range(self.tau):
-            self.batch.iteration(stream=self.stream)
+            self.iteration()
         self.batch.loss_est(stream=self.stream)
         self.batch.epoch_end(stream=self.stream)
 
@@ -112,13 +117,13 @@ class GcpAdamBatch:
     SHAPES = [(cpl, target, maxr) for cpl in (1, 2, 4) for target, maxr in ((64, 32), (16, 32), (0, 1))]
 
     def autotune(self, iterations: int = 10, shapes=None):
-        """Chooses the batched gradient's shape -- threads per block and blocks
-        (grid waves), chunks per lane (the rows per warp step) and the replica
-        width (the pre-reduction of heavily hit rows) -- by timing whole
-        iterations (gradient + Adam with the fold) on a throwaway copy of the
-        batch (same draws and shapes), captured in a CUDA graph as an epoch
-        is; keeps the fastest.  Returns it with its time per iteration and the
-        per-problem shapes it gives."""
+        """Chooses the batched iteration's form and shape -- one persistent
+        launch (gradient and Adam fused) or two launches, threads per block and
+        blocks (grid waves), chunks per lane (the rows per warp step) and the
+        replica width (the pre-reduction of heavily hit rows) -- by timing whole
+        iterations on a throwaway copy of the batch (same draws and shapes),
+        captured in a CUDA graph as an epoch is; keeps the fastest.  Returns it
+        with its time per iteration and the per-problem shapes it gives."""
         from .autotune import side_stream
         shadow = []
         with torch.cuda.stream(self.stream):
@@ -132,39 +137,53 @@ class GcpAdamBatch:
         tb = gcp.Batch(shadow, stream=self.stream)
         cap = side_stream(self.stream)
         sms = torch.cuda.get_device_properties(self.stream.device).multi_processor_count
-        best, best_t, tried = None, float("inf"), 0
+
+        def timed(step):
+            with torch.cuda.stream(self.stream):
+                step(self.stream)
+            self.stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                for _ in range(iterations):
+                    step(cap)
+            with torch.cuda.stream(self.stream):
+                g.replay()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(self.stream)
+                g.replay()
+                g.replay()
+                b.record(self.stream)
+            self.stream.synchronize()
+            del g
+            return a.elapsed_time(b) * 1e-3 / (2 * iterations)
+
+        best, best_t, tried, best_fused_t = None, float("inf"), 0, float("inf")
         for cpl, target, maxr in (shapes or self.SHAPES):
             tb.set_shape(cpl, target, maxr, stream=self.stream)
+            # the one-launch iteration (its grid is one resident wave of 256-thread blocks)
+            t = timed(lambda st: tb.iteration_fused(stream=st))
+            tried += 1
+            best_fused_t = min(best_fused_t, t)
+            if t < best_t:
+                best_t = t
+                best = dict(fused=True, block=0, grid_blocks=0, chunks_per_lane=cpl, replica_target=target,
+                            max_replicas=maxr)
             for block in (128, 256):
                 for waves in (0, 1, 2, 4):
                     grid = 0 if waves == 0 else sms * waves * (256 // block)
                     tb.set_tuning(block, grid)
-                    with torch.cuda.stream(self.stream):
-                        tb.iteration(stream=self.stream)
-                    self.stream.synchronize()
-                    g = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(g, stream=cap):
-                        for _ in range(iterations):
-                            tb.iteration(stream=cap)
-                    with torch.cuda.stream(self.stream):
-                        g.replay()
-                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        a.record(self.stream)
-                        g.replay()
-                        g.replay()
-                        b.record(self.stream)
-                    self.stream.synchronize()
-                    t = a.elapsed_time(b) * 1e-3 / (2 * iterations)
-                    del g
+                    t = timed(lambda st: tb.iteration(stream=st))
                     tried += 1
                     if t < best_t:
                         best_t = t
-                        best = dict(block=block, grid_blocks=grid, chunks_per_lane=cpl, replica_target=target,
-                                    max_replicas=maxr)
+                        best = dict(fused=False, block=block, grid_blocks=grid, chunks_per_lane=cpl,
+                                    replica_target=target, max_replicas=maxr)
         tb.close()
-        self.set_shape(**best)
+        self.fused = best["fused"]
+        self.set_shape(**{k: v for k, v in best.items() if k != "fused"})
         shapes = [self.batch.get_shape(i) for i in range(len(self.problems))]
-        return dict(best=best, seconds_per_iteration=best_t, tried=tried, shapes=shapes)
+        return dict(best=best, seconds_per_iteration=best_t, best_fused_seconds_per_iteration=best_fused_t,
+                    tried=tried, shapes=shapes)
 
     def set_shape(self, block=0, grid_blocks=0, chunks_per_lane=0, replica_target=0, max_replicas=0):
         """Sets the batched gradient's launch and per-problem shape (before capture)."""

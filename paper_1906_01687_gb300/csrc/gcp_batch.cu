@@ -1,5 +1,7 @@
 // Batched form: many independent GCP-Adam problems (uneven shapes, ranks and
 // losses) advanced together.  Each step is one launch for all problems:
+//   batch_fused_kernel -- a whole iteration (gradient and Adam step) of every
+//                         problem in one persistent launch, or, in two:
 //   batch_grad_kernel  -- the fused sampled gradient (Alg. 1) of every problem;
 //                         warps take 32 consecutive draws of one problem at a
 //                         time from the flattened table of all problems' draws;
@@ -68,6 +70,12 @@ struct BatchArgs {
     const int64_t* est_block_begin; // prefix of loss-estimate blocks, count + 1
     double* partials;
     unsigned int* ticket;
+    // the one-launch iteration (batch_fused_kernel): every problem's gradient
+    // batches, then every problem's Adam chunks, taken in that order from one queue
+    const int64_t* adam_begin;      // prefix of Adam chunks, count + 1
+    unsigned int* grad_done;        // per problem: gradient batches finished (zero between launches)
+    unsigned int* adam_done;        // per problem: Adam chunks finished (zero between launches)
+    unsigned long long* queue;      // [0] next item, [1] warps finished (zero between launches)
 };
 
 __device__ __forceinline__ int find_problem(const int64_t* prefix, int count, int64_t u)
@@ -101,6 +109,85 @@ __device__ __forceinline__ float4 brow(const BatchDesc& P, int k, uint32_t row, 
     return load4(static_cast<const float*>(P.Ag[k]) + off);
 }
 
+// One batch of 32 consecutive draws of one problem (warp item u of the
+// flattened table of all problems' draws): Alg. 1's draws, the model values,
+// y, and the sampled MTTKRP into G (or the replica slabs).  The whole warp calls it.
+__device__ __forceinline__ void batch_grad_item(const BatchArgs& a, const int64_t* s_work, int64_t u, int lane)
+{
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    const int pb = find_problem(s_work, a.count, u);
+    const BatchDesc& P = a.desc[pb];
+    const int d = P.d, L = P.L, NC = P.NC, rank = P.rank, ld = P.ld;
+    const int64_t j = (u - s_work[pb]) * 32 + lane;
+    const uint64_t stream = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(&P.st->iter));
+    // this lane's draw (Alg. 1): i_k = randi(n_k), x = X(i), weight omega / s
+    const bool mine = j < P.s;
+    uint32_t ix[kBatchMaxD] = {0u, 0u, 0u, 0u};
+    float x = 0.0f;
+    if (mine) {
+        const U64x4 blk = philox4x64_10(static_cast<uint64_t>(j), stream, kTagUniform, 0, P.seed, P.problem);
+        uint64_t lin = 0;
+#pragma unroll
+        for (int k = 0; k < kBatchMaxD; ++k) {
+            if (k < d) {
+                ix[k] = randi32(blk.w[k], P.dims[k]);
+                lin += static_cast<uint64_t>(ix[k]) * P.strides[k];
+            }
+        }
+        x = __ldg(P.X + lin);
+    }
+    const int gl = lane & (L - 1), gbase = lane & ~(L - 1);
+    // this batch's destination of each mode: G_k, or replica u mod R of its slabs
+    float* dst[kBatchMaxD];
+#pragma unroll
+    for (int k = 0; k < kBatchMaxD; ++k)
+        dst[k] = (k < d && P.reps[k] > 1)
+                     ? P.R[k] + static_cast<size_t>(static_cast<uint32_t>(u) % P.reps[k]) * P.rep_stride[k]
+                     : P.G[k];
+    for (int b = 0; b < L; ++b) {
+        const int src = gbase + b;
+        uint32_t jx[kBatchMaxD];
+#pragma unroll
+        for (int k = 0; k < kBatchMaxD; ++k) jx[k] = __shfl_sync(kFull, ix[k], src);
+        const float xb = __shfl_sync(kFull, x, src);
+        const bool vb = __shfl_sync(kFull, static_cast<int>(mine), src) != 0;
+        float part = 0.0f;
+        for (int c = 0; c < NC; ++c) {
+            const int col = (gl * NC + c) * 4;
+            if (!vb || col >= rank) continue;
+            float4 prod = brow(P, 0, jx[0], col);
+#pragma unroll
+            for (int k = 1; k < kBatchMaxD; ++k)
+                if (k < d) prod = mul4(prod, brow(P, k, jx[k], col));
+            part += sum4(prod);
+        }
+        for (int off = L >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+        if (!vb) continue;  // no shuffles below this point
+        const float y = P.w * loss_g(P.loss, xb, part);
+        for (int c = 0; c < NC; ++c) {
+            const int col = (gl * NC + c) * 4;
+            if (col >= rank) continue;
+            float4 rc[kBatchMaxD];
+#pragma unroll
+            for (int k = 0; k < kBatchMaxD; ++k)
+                rc[k] = k < d ? brow(P, k, jx[k], col) : make_float4(1.f, 1.f, 1.f, 1.f);
+            float4 pre[kBatchMaxD], suf[kBatchMaxD];
+            pre[0] = make_float4(y, y, y, y);
+#pragma unroll
+            for (int k = 1; k < kBatchMaxD; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
+            suf[kBatchMaxD - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+            for (int k = kBatchMaxD - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
+#pragma unroll
+            for (int k = 0; k < kBatchMaxD; ++k) {
+                if (k >= d) continue;
+                atomicAdd(reinterpret_cast<float4*>(dst[k] + static_cast<size_t>(jx[k]) * ld + col),
+                          mul4(pre[k], suf[k]));
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) batch_grad_kernel(const BatchArgs a)
 {
     pdl_wait();
@@ -108,84 +195,11 @@ __global__ void __launch_bounds__(256) batch_grad_kernel(const BatchArgs a)
     extern __shared__ int64_t s_work[];
     for (int i = threadIdx.x; i <= a.count; i += blockDim.x) s_work[i] = a.work_begin[i];
     __syncthreads();
-    constexpr unsigned kFull = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int64_t W = s_work[a.count];
     const int64_t warp_global = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t u = warp_global; u < W; u += nwarps) {
-        const int pb = find_problem(s_work, a.count, u);
-        const BatchDesc& P = a.desc[pb];
-        const int d = P.d, L = P.L, NC = P.NC, rank = P.rank, ld = P.ld;
-        const int64_t j = (u - s_work[pb]) * 32 + lane;
-        const uint64_t stream = static_cast<uint64_t>(*reinterpret_cast<const volatile int64_t*>(&P.st->iter));
-        // this lane's draw (Alg. 1): i_k = randi(n_k), x = X(i), weight omega / s
-        const bool mine = j < P.s;
-        uint32_t ix[kBatchMaxD] = {0u, 0u, 0u, 0u};
-        float x = 0.0f;
-        if (mine) {
-            const U64x4 blk = philox4x64_10(static_cast<uint64_t>(j), stream, kTagUniform, 0, P.seed, P.problem);
-            uint64_t lin = 0;
-#pragma unroll
-            for (int k = 0; k < kBatchMaxD; ++k) {
-                if (k < d) {
-                    ix[k] = randi32(blk.w[k], P.dims[k]);
-                    lin += static_cast<uint64_t>(ix[k]) * P.strides[k];
-                }
-            }
-            x = __ldg(P.X + lin);
-        }
-        const int gl = lane & (L - 1), gbase = lane & ~(L - 1);
-        // this batch's destination of each mode: G_k, or replica u mod R of its slabs
-        float* dst[kBatchMaxD];
-#pragma unroll
-        for (int k = 0; k < kBatchMaxD; ++k)
-            dst[k] = (k < d && P.reps[k] > 1)
-                         ? P.R[k] + static_cast<size_t>(static_cast<uint32_t>(u) % P.reps[k]) * P.rep_stride[k]
-                         : P.G[k];
-        for (int b = 0; b < L; ++b) {
-            const int src = gbase + b;
-            uint32_t jx[kBatchMaxD];
-#pragma unroll
-            for (int k = 0; k < kBatchMaxD; ++k) jx[k] = __shfl_sync(kFull, ix[k], src);
-            const float xb = __shfl_sync(kFull, x, src);
-            const bool vb = __shfl_sync(kFull, static_cast<int>(mine), src) != 0;
-            float part = 0.0f;
-            for (int c = 0; c < NC; ++c) {
-                const int col = (gl * NC + c) * 4;
-                if (!vb || col >= rank) continue;
-                float4 prod = brow(P, 0, jx[0], col);
-#pragma unroll
-                for (int k = 1; k < kBatchMaxD; ++k)
-                    if (k < d) prod = mul4(prod, brow(P, k, jx[k], col));
-                part += sum4(prod);
-            }
-            for (int off = L >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
-            if (!vb) continue;  // no shuffles below this point
-            const float y = P.w * loss_g(P.loss, xb, part);
-            for (int c = 0; c < NC; ++c) {
-                const int col = (gl * NC + c) * 4;
-                if (col >= rank) continue;
-                float4 rc[kBatchMaxD];
-#pragma unroll
-                for (int k = 0; k < kBatchMaxD; ++k)
-                    rc[k] = k < d ? brow(P, k, jx[k], col) : make_float4(1.f, 1.f, 1.f, 1.f);
-                float4 pre[kBatchMaxD], suf[kBatchMaxD];
-                pre[0] = make_float4(y, y, y, y);
-#pragma unroll
-                for (int k = 1; k < kBatchMaxD; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
-                suf[kBatchMaxD - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
-#pragma unroll
-                for (int k = kBatchMaxD - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
-#pragma unroll
-                for (int k = 0; k < kBatchMaxD; ++k) {
-                    if (k >= d) continue;
-                    atomicAdd(reinterpret_cast<float4*>(dst[k] + static_cast<size_t>(jx[k]) * ld + col),
-                              mul4(pre[k], suf[k]));
-                }
-            }
-        }
-    }
+    for (int64_t u = warp_global; u < W; u += nwarps) batch_grad_item(a, s_work, u, lane);
 }
 
 __device__ __forceinline__ void bstore_bf16x4(uint16_t* dst, float4 v)
@@ -205,6 +219,46 @@ __device__ __forceinline__ int mode_in_problem(const BatchDesc& P, int64_t loc4)
     for (int l = 1; l < kBatchMaxD; ++l)
         if (l < P.d && loc4 >= P.off4[l]) k = l;
     return k;
+}
+
+// The Adam step (Alg. 4) of float4 element p4 of problem P's parameters:
+// its gradient (with the replica slabs folded in, in order, and cleared),
+// moments, update, projection and BF16 copy, then G = 0.  G and the slabs
+// are read past L1 (they were written at L2 by reductions of this launch or
+// the one before).
+__device__ __forceinline__ void batch_adam_element(const BatchDesc& P, int64_t p4, float ic1, float ic2, float alpha,
+                                                   bool done)
+{
+    const int k = mode_in_problem(P, p4);
+    const int64_t loc = p4 - P.off4[k];
+    const int col = static_cast<int>((loc * 4) % P.ld);
+    float4* g4 = reinterpret_cast<float4*>(P.G[k]) + loc;
+    float4 g = __ldcg(g4);
+    if (P.reps[k] > 1) {  // fold the replica slabs of this mode, leaving them zero
+        float4* r = reinterpret_cast<float4*>(P.R[k]) + loc;
+        const uint64_t rs = P.rep_stride[k] / 4;
+        for (uint32_t q = 0; q < P.reps[k]; ++q) {
+            g = add4(g, __ldcg(r + q * rs));
+            r[q * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    if (!done && col < P.rank) {
+        float4* a4p = reinterpret_cast<float4*>(P.A[k]) + loc;
+        float4* b4p = reinterpret_cast<float4*>(P.B[k]) + loc;
+        float4* c4p = reinterpret_cast<float4*>(P.C[k]) + loc;
+        float4 A4 = *a4p, B4 = *b4p, C4 = *c4p;
+        const bool inside = P.eps_inside != 0;
+        const int ncol = P.rank - col;
+        adam_one(A4.x, B4.x, C4.x, g.x, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+        if (ncol > 1) adam_one(A4.y, B4.y, C4.y, g.y, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+        if (ncol > 2) adam_one(A4.z, B4.z, C4.z, g.z, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+        if (ncol > 3) adam_one(A4.w, B4.w, C4.w, g.w, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
+        *a4p = A4;
+        *b4p = B4;
+        *c4p = C4;
+        if (P.Abf[k]) bstore_bf16x4(P.Abf[k] + loc * 4, A4);
+    }
+    *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Adam of every problem: per-problem bias corrections, learning rate and
@@ -229,33 +283,8 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i4 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i4 < total4; i4 += stride) {
         const int pb = find_problem(s_param, a.count, i4);
-        const BatchDesc& P = a.desc[pb];
-        const int64_t p4 = i4 - s_param[pb];
-        const int k = mode_in_problem(P, p4);
-        const int64_t loc = p4 - P.off4[k];
-        const int col = static_cast<int>((loc * 4) % P.ld);
-        float4* g4 = reinterpret_cast<float4*>(P.G[k]) + loc;
-        float4 g = *g4;
-        if (P.reps[k] > 1)  // fold the replica slabs of this mode, leaving them zero
-            g = add4(g, fold_replicas(reinterpret_cast<float4*>(P.R[k]) + loc, P.reps[k], P.rep_stride[k] / 4));
-        if (s_prob[4 * pb + 3] == 0.0f && col < P.rank) {
-            const float ic1 = s_prob[4 * pb], ic2 = s_prob[4 * pb + 1], alpha = s_prob[4 * pb + 2];
-            float4* a4p = reinterpret_cast<float4*>(P.A[k]) + loc;
-            float4* b4p = reinterpret_cast<float4*>(P.B[k]) + loc;
-            float4* c4p = reinterpret_cast<float4*>(P.C[k]) + loc;
-            float4 A4 = *a4p, B4 = *b4p, C4 = *c4p;
-            const bool inside = P.eps_inside != 0;
-            const int ncol = P.rank - col;
-            adam_one(A4.x, B4.x, C4.x, g.x, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
-            if (ncol > 1) adam_one(A4.y, B4.y, C4.y, g.y, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
-            if (ncol > 2) adam_one(A4.z, B4.z, C4.z, g.z, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
-            if (ncol > 3) adam_one(A4.w, B4.w, C4.w, g.w, P.beta1, P.beta2, ic1, ic2, P.eps, alpha, P.lower, inside);
-            *a4p = A4;
-            *b4p = B4;
-            *c4p = C4;
-            if (P.Abf[k]) bstore_bf16x4(P.Abf[k] + loc * 4, A4);
-        }
-        *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        batch_adam_element(a.desc[pb], i4 - s_param[pb], s_prob[4 * pb], s_prob[4 * pb + 1], s_prob[4 * pb + 2],
+                           s_prob[4 * pb + 3] != 0.0f);
     }
     if (batch_last_block(a.ticket)) {  // every problem's step count, one thread per problem
         for (int b = threadIdx.x; b < a.count; b += blockDim.x) {
@@ -266,6 +295,105 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
         __syncthreads();
         if (threadIdx.x == 0) {
             *a.ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// One launch for a whole iteration of every problem (gradient and Adam step).
+// Warps take items from one queue in order: first every problem's gradient
+// batches (as batch_grad_kernel), then every problem's Adam chunks of
+// kAdamChunk float4 elements (4 per lane).  A warp holding an Adam chunk of
+// problem b waits until all of b's gradient batches are done; those were all
+// taken before any Adam chunk by warps that never wait, so the wait ends.
+// The wait is bounded: after kBatchSpinLimit polls the warp records
+// GCP_ERR_TIMEOUT in the problem's state and skips the chunk.  The problem's
+// last Adam chunk advances its t and iter and clears its counters; the last
+// warp to leave clears the queue.
+constexpr int kAdamChunk = 128;
+constexpr int kBatchSpinLimit = 1 << 21;
+
+__global__ void __launch_bounds__(256) batch_fused_kernel(const BatchArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    extern __shared__ int64_t s_pre[];  // gradient batch prefix (count + 1), then Adam chunk prefix (count + 1)
+    int64_t* s_work = s_pre;
+    int64_t* s_adam = s_pre + a.count + 1;
+    for (int i = threadIdx.x; i <= a.count; i += blockDim.x) {
+        s_work[i] = a.work_begin[i];
+        s_adam[i] = a.adam_begin[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t W = s_work[a.count];
+    const int64_t total = W + s_adam[a.count];
+    while (true) {
+        unsigned long long got = 0ull;
+        if (lane == 0) got = atomicAdd(&a.queue[0], 1ull);
+        const int64_t item = static_cast<int64_t>(__shfl_sync(kFull, got, 0));
+        if (item >= total) break;
+        if (item < W) {
+            batch_grad_item(a, s_work, item, lane);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicAdd(&a.grad_done[find_problem(s_work, a.count, item)], 1u);
+            }
+            continue;
+        }
+        const int64_t ai = item - W;
+        const int pb = find_problem(s_adam, a.count, ai);
+        const BatchDesc& P = a.desc[pb];
+        int ok = 1;
+        if (lane == 0) {
+            const unsigned need = static_cast<unsigned>(s_work[pb + 1] - s_work[pb]);
+            int spins = 0;
+            while (*reinterpret_cast<volatile unsigned*>(&a.grad_done[pb]) < need) {
+                if (++spins > kBatchSpinLimit) {
+                    ok = 0;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        ok = __shfl_sync(kFull, ok, 0);
+        __syncwarp();
+        if (ok) {
+            const float n = static_cast<float>(P.st->t + 1);
+            const float ic1 = inv_bias_correction(P.beta1, n), ic2 = inv_bias_correction(P.beta2, n);
+            const float alpha = P.st->alpha;
+            const bool done = P.st->done != 0;
+            const int64_t c0 = (ai - s_adam[pb]) * kAdamChunk;
+            const int64_t n4 = P.off4[P.d];
+#pragma unroll
+            for (int i = 0; i < kAdamChunk / 32; ++i) {
+                const int64_t p4 = c0 + i * 32 + lane;
+                if (p4 < n4) batch_adam_element(P, p4, ic1, ic2, alpha, done);
+            }
+        } else if (lane == 0) {
+            atomicCAS(&P.st->status, 0, static_cast<int32_t>(GCP_ERR_TIMEOUT));
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            const unsigned chunks = static_cast<unsigned>(s_adam[pb + 1] - s_adam[pb]);
+            if (atomicAdd(&a.adam_done[pb], 1u) + 1u == chunks) {  // the problem's last Adam chunk
+                gcp_adam_state* st = P.st;
+                if (!st->done) st->t += 1;
+                st->iter += 1;
+                a.grad_done[pb] = 0u;
+                a.adam_done[pb] = 0u;
+                __threadfence();
+            }
+        }
+    }
+    if (lane == 0) {  // the last warp to leave clears the queue for the next launch
+        const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+        if (atomicAdd(&a.queue[1], 1ull) + 1ull == warps) {
+            a.queue[0] = 0ull;
+            a.queue[1] = 0ull;
             __threadfence();
         }
     }
@@ -427,6 +555,10 @@ struct gcp_batch {
     int64_t total_work = 0, total_param4 = 0, est_blocks = 0;
     int num_sms = 1;
     int block = 0, grid = 0;
+    int64_t* d_adam = nullptr;            // prefix of Adam chunks (the one-launch iteration)
+    unsigned int* d_done = nullptr;       // per problem: gradient batches done, then Adam chunks done
+    unsigned long long* d_queue = nullptr;  // the one-launch iteration's queue: next item, warps finished
+    int64_t total_adam = 0;
     std::vector<BatchDesc> host_desc;  // the uploaded table, for reshaping
     int chunks_per_lane = 1, replica_target = 64, max_replicas = 32;
 };
@@ -548,6 +680,10 @@ BatchArgs batch_args(const gcp_batch* b, int begin)
     a.est_block_begin = b->d_est;
     a.partials = b->d_partials;
     a.ticket = b->d_ticket;
+    a.adam_begin = b->d_adam;
+    a.grad_done = b->d_done;
+    a.adam_done = b->d_done + b->count;
+    a.queue = b->d_queue;
     return a;
 }
 
@@ -565,12 +701,13 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
     if (!out || !problems || count < 1 || count > kBatchMaxProblems) return GCP_ERR_INVALID_ARG;
     *out = nullptr;
     std::vector<BatchDesc> desc(count);
-    std::vector<int64_t> work(count + 1, 0), param(count + 1, 0), est(count + 1, 0);
+    std::vector<int64_t> work(count + 1, 0), param(count + 1, 0), est(count + 1, 0), adam(count + 1, 0);
     for (int i = 0; i < count; ++i) {
         gcp_status st = fill_desc(problems[i], &desc[i]);
         if (st != GCP_OK) return st;
         work[i + 1] = work[i] + (desc[i].s + 31) / 32;
         param[i + 1] = param[i] + desc[i].off4[desc[i].d];
+        adam[i + 1] = adam[i] + (desc[i].off4[desc[i].d] + kAdamChunk - 1) / kAdamChunk;
         const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((desc[i].n_est + 255) / 256, kBatchEstBlocksPerProblem));
         est[i + 1] = est[i] + nb;
     }
@@ -610,6 +747,10 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_est), sizeof(int64_t) * (count + 1))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_partials), sizeof(double) * b->est_blocks)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_ticket), sizeof(unsigned int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_adam), sizeof(int64_t) * (count + 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_done), sizeof(unsigned int) * 2 * count)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_queue), sizeof(unsigned long long) * 2)) != cudaSuccess) return fail(e);
+    b->total_adam = adam[count];
     if (rep_floats > 0) {
         if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_rep), sizeof(float) * rep_floats)) != cudaSuccess) return fail(e);
         if ((e = cudaMemsetAsync(b->d_rep, 0, sizeof(float) * rep_floats, s)) != cudaSuccess) return fail(e);
@@ -628,6 +769,10 @@ gcp_status gcp_batch_create(gcp_batch** out, const gcp_batch_problem* problems, 
     if ((e = cudaMemcpyAsync(b->d_est, est.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(e);
     if ((e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(b->d_adam, adam.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * 2 * count, s)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 2, s)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
     b->host_desc = desc;
     *out = b;
@@ -711,6 +856,9 @@ gcp_status gcp_batch_destroy(gcp_batch* b)
     cudaFree(b->d_partials);
     cudaFree(b->d_ticket);
     cudaFree(b->d_rep);
+    cudaFree(b->d_adam);
+    cudaFree(b->d_done);
+    cudaFree(b->d_queue);
     delete b;
     return GCP_OK;
 }
@@ -762,6 +910,20 @@ gcp_status gcp_batch_iteration(gcp_batch* b, gcp_stream_t stream)
     gcp_status st = batch_grad_launch(b, stream);  // the Adam kernel folds the replica slabs
     if (st != GCP_OK) return st;
     return gcp_batch_adam_step(b, stream);
+}
+
+gcp_status gcp_batch_iteration_fused(gcp_batch* b, gcp_stream_t stream)
+{
+    if (!b) return GCP_ERR_INVALID_ARG;
+    const int block = 256;
+    const size_t smem = sizeof(int64_t) * 2 * (b->count + 1);
+    int bps = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_fused_kernel, block, smem);
+    const int64_t items = b->total_work + b->total_adam;
+    const int64_t want = std::max<int64_t>(1, (items + block / 32 - 1) / (block / 32));
+    const int grid = static_cast<int>(std::min<int64_t>(want, int64_t(b->num_sms) * std::max(bps, 1)));
+    return to_status(launch_pdl(batch_fused_kernel, dim3(grid), dim3(block), smem,
+                                reinterpret_cast<cudaStream_t>(stream), batch_args(b, 0)));
 }
 
 gcp_status gcp_batch_loss_est(gcp_batch* b, gcp_stream_t stream)

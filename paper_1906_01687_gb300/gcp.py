@@ -130,6 +130,7 @@ _SIGS = {
     "gcp_batch_grad": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_adam_step": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_iteration": ([_vp, _vp], ctypes.c_int),
+    "gcp_batch_iteration_fused": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_loss_est": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_epoch_begin": ([_vp, _vp], ctypes.c_int),
     "gcp_batch_epoch_end": ([_vp, _vp], ctypes.c_int),
@@ -600,6 +601,10 @@ class Batch:
 
     def iteration(self, stream=None):
         self._call("gcp_batch_iteration", stream)
+
+    def iteration_fused(self, stream=None):
+        """One iteration of every problem in one persistent launch."""
+        self._call("gcp_batch_iteration_fused", stream)
 
     def loss_est(self, stream=None):
         self._call("gcp_batch_loss_est", stream)

@@ -120,7 +120,8 @@ def test_batch_autotune_and_graph_replay():
     specs = make_specs(5000)
     run = GcpAdamBatch(specs, tau=4, alpha=0.01, autotune=True)
     assert run.tuned["seconds_per_iteration"] > 0 and run.tuned["tried"] >= 8
-    assert set(run.tuned["best"]) == {"block", "grid_blocks", "chunks_per_lane", "replica_target", "max_replicas"}
+    assert set(run.tuned["best"]) == {"fused", "block", "grid_blocks", "chunks_per_lane", "replica_target",
+                                      "max_replicas"}
     assert len(run.tuned["shapes"]) == len(specs)
     sts = run.fit(max_epochs=3)
     assert all(st["iter"] == 12 for st in sts)
@@ -167,3 +168,39 @@ def test_batch_rejects_sparse_and_wide_problems():
              G=F.like(), B=F.like(), C=F.like(), SA=F.like(), SB=F.like(), SC=F.like(), state=st)
     with pytest.raises(g.GcpError):
         g.Batch([p])  # d = 5 > 4
+
+
+@pytest.mark.parametrize("cpl,target,maxr", [(1, 0, 0), (2, 16, 32), (1, 0, 1)])
+def test_fused_iteration_follows_two_launches(cpl, target, maxr):
+    """The one-launch batched iteration (gradient batches, then Adam chunks that
+    wait for their problem's gradient) gives every problem the factors, moments
+    and counters of the two-launch iteration (summation order aside), and
+    leaves its queue ready for the next launch (repeated iterations)."""
+    from paper_1906_01687_gb300.batch import GcpAdamBatch
+    g = gcp()
+    specs = make_specs(20_000)
+    runs = []
+    for fused in (False, True):
+        run = GcpAdamBatch(specs, tau=5, alpha=0.01, fused=fused)
+        run.set_shape(chunks_per_lane=cpl, replica_target=target, max_replicas=maxr)
+        for _ in range(6):
+            run.iteration()
+        torch.cuda.synchronize()
+        runs.append(run)
+    for i in range(len(specs)):
+        a, b = runs[0].factors(i), runs[1].factors(i)
+        num = math.sqrt(sum(np.linalg.norm(x - y) ** 2 for x, y in zip(a, b)))
+        den = math.sqrt(sum(np.linalg.norm(y) ** 2 for y in a))
+        assert num <= 1e-4 * den, (i, num / den)
+        s0, s1 = runs[0].states()[i], runs[1].states()[i]
+        assert (s0["t"], s0["iter"], s1["status"]) == (s1["t"], s1["iter"], 0) == (6, 6, 0)
+        assert all(torch.count_nonzero(x).item() == 0 for x in runs[1].problems[i]["G"])
+
+
+def test_fused_epochs_in_a_graph():
+    from paper_1906_01687_gb300.batch import GcpAdamBatch
+    specs = make_specs(5000)
+    run = GcpAdamBatch(specs, tau=4, alpha=0.01, fused=True)
+    sts = run.fit(max_epochs=3)
+    assert all(st["iter"] == 12 and st["status"] == 0 for st in sts)
+    assert all(math.isfinite(st["F"]) for st in sts)
