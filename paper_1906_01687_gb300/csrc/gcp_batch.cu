@@ -301,17 +301,20 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
 }
 
 // One launch for a whole iteration of every problem (gradient and Adam step).
-// Warps take items from one queue in order: first every problem's gradient
-// batches (as batch_grad_kernel), then every problem's Adam chunks of
-// kAdamChunk float4 elements (4 per lane).  A warp holding an Adam chunk of
-// problem b waits until all of b's gradient batches are done; those were all
-// taken before any Adam chunk by warps that never wait, so the wait ends.
+// Warps take items from one queue in order, kClaim at a time: first every
+// problem's gradient batches (as batch_grad_kernel), then every problem's
+// Adam chunks of kAdamChunk float4 elements (4 per lane).  A warp holding an
+// Adam chunk of problem b waits until all of b's gradient batches are done;
+// those were all claimed before any Adam chunk, by warps that work their
+// gradient batches without waiting (a warp's later claims only ever hold later
+// items), so the wait ends.
 // The wait is bounded: after kBatchSpinLimit polls the warp records
 // GCP_ERR_TIMEOUT in the problem's state and skips the chunk.  The problem's
 // last Adam chunk advances its t and iter and clears its counters; the last
 // warp to leave clears the queue.
 constexpr int kAdamChunk = 128;
 constexpr int kBatchSpinLimit = 1 << 21;
+constexpr int kClaim = 4;  // queue items a warp claims at a time
 
 __global__ void __launch_bounds__(256) batch_fused_kernel(const BatchArgs a)
 {
@@ -329,65 +332,71 @@ __global__ void __launch_bounds__(256) batch_fused_kernel(const BatchArgs a)
     const int lane = threadIdx.x & 31;
     const int64_t W = s_work[a.count];
     const int64_t total = W + s_adam[a.count];
-    while (true) {
-        unsigned long long got = 0ull;
-        if (lane == 0) got = atomicAdd(&a.queue[0], 1ull);
-        const int64_t item = static_cast<int64_t>(__shfl_sync(kFull, got, 0));
-        if (item >= total) break;
-        if (item < W) {
-            batch_grad_item(a, s_work, item, lane);
+    // items are claimed kClaim at a time, the next claim in flight while this one is worked
+    unsigned long long got = 0ull;
+    if (lane == 0) got = atomicAdd(&a.queue[0], static_cast<unsigned long long>(kClaim));
+    int64_t claim = static_cast<int64_t>(__shfl_sync(kFull, got, 0));
+    while (claim < total) {
+        unsigned long long next = 0ull;
+        if (lane == 0) next = atomicAdd(&a.queue[0], static_cast<unsigned long long>(kClaim));
+        for (int64_t item = claim; item < claim + kClaim && item < total; ++item) {
+            if (item < W) {
+                batch_grad_item(a, s_work, item, lane);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    atomicAdd(&a.grad_done[find_problem(s_work, a.count, item)], 1u);
+                }
+                continue;
+            }
+            const int64_t ai = item - W;
+            const int pb = find_problem(s_adam, a.count, ai);
+            const BatchDesc& P = a.desc[pb];
+            int ok = 1;
+            if (lane == 0) {
+                const unsigned need = static_cast<unsigned>(s_work[pb + 1] - s_work[pb]);
+                int spins = 0;
+                while (*reinterpret_cast<volatile unsigned*>(&a.grad_done[pb]) < need) {
+                    if (++spins > kBatchSpinLimit) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();
+            }
+            ok = __shfl_sync(kFull, ok, 0);
+            __syncwarp();
+            if (ok) {
+                const float n = static_cast<float>(P.st->t + 1);
+                const float ic1 = inv_bias_correction(P.beta1, n), ic2 = inv_bias_correction(P.beta2, n);
+                const float alpha = P.st->alpha;
+                const bool done = P.st->done != 0;
+                const int64_t c0 = (ai - s_adam[pb]) * kAdamChunk;
+                const int64_t n4 = P.off4[P.d];
+#pragma unroll
+                for (int i = 0; i < kAdamChunk / 32; ++i) {
+                    const int64_t p4 = c0 + i * 32 + lane;
+                    if (p4 < n4) batch_adam_element(P, p4, ic1, ic2, alpha, done);
+                }
+            } else if (lane == 0) {
+                atomicCAS(&P.st->status, 0, static_cast<int32_t>(GCP_ERR_TIMEOUT));
+            }
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
-                atomicAdd(&a.grad_done[find_problem(s_work, a.count, item)], 1u);
-            }
-            continue;
-        }
-        const int64_t ai = item - W;
-        const int pb = find_problem(s_adam, a.count, ai);
-        const BatchDesc& P = a.desc[pb];
-        int ok = 1;
-        if (lane == 0) {
-            const unsigned need = static_cast<unsigned>(s_work[pb + 1] - s_work[pb]);
-            int spins = 0;
-            while (*reinterpret_cast<volatile unsigned*>(&a.grad_done[pb]) < need) {
-                if (++spins > kBatchSpinLimit) {
-                    ok = 0;
-                    break;
+                const unsigned chunks = static_cast<unsigned>(s_adam[pb + 1] - s_adam[pb]);
+                if (atomicAdd(&a.adam_done[pb], 1u) + 1u == chunks) {  // the problem's last Adam chunk
+                    gcp_adam_state* st = P.st;
+                    if (!st->done) st->t += 1;
+                    st->iter += 1;
+                    a.grad_done[pb] = 0u;
+                    a.adam_done[pb] = 0u;
+                    __threadfence();
                 }
             }
-            __threadfence();
         }
-        ok = __shfl_sync(kFull, ok, 0);
-        __syncwarp();
-        if (ok) {
-            const float n = static_cast<float>(P.st->t + 1);
-            const float ic1 = inv_bias_correction(P.beta1, n), ic2 = inv_bias_correction(P.beta2, n);
-            const float alpha = P.st->alpha;
-            const bool done = P.st->done != 0;
-            const int64_t c0 = (ai - s_adam[pb]) * kAdamChunk;
-            const int64_t n4 = P.off4[P.d];
-#pragma unroll
-            for (int i = 0; i < kAdamChunk / 32; ++i) {
-                const int64_t p4 = c0 + i * 32 + lane;
-                if (p4 < n4) batch_adam_element(P, p4, ic1, ic2, alpha, done);
-            }
-        } else if (lane == 0) {
-            atomicCAS(&P.st->status, 0, static_cast<int32_t>(GCP_ERR_TIMEOUT));
-        }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            const unsigned chunks = static_cast<unsigned>(s_adam[pb + 1] - s_adam[pb]);
-            if (atomicAdd(&a.adam_done[pb], 1u) + 1u == chunks) {  // the problem's last Adam chunk
-                gcp_adam_state* st = P.st;
-                if (!st->done) st->t += 1;
-                st->iter += 1;
-                a.grad_done[pb] = 0u;
-                a.adam_done[pb] = 0u;
-                __threadfence();
-            }
-        }
+        claim = static_cast<int64_t>(__shfl_sync(kFull, next, 0));
     }
     if (lane == 0) {  // the last warp to leave clears the queue for the next launch
         const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
