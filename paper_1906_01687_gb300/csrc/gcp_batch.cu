@@ -234,13 +234,27 @@ __device__ __forceinline__ void batch_adam_element(const BatchDesc& P, int64_t p
     const int col = static_cast<int>((loc * 4) % P.ld);
     float4* g4 = reinterpret_cast<float4*>(P.G[k]) + loc;
     float4 g = __ldcg(g4);
-    if (P.reps[k] > 1) {  // fold the replica slabs of this mode, leaving them zero
+    if (P.reps[k] > 1) {  // fold the replica slabs of this mode in order, leaving them zero
+        // the first kWide loads are all issued before any is added or cleared
+        constexpr int kWide = 16;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         float4* r = reinterpret_cast<float4*>(P.R[k]) + loc;
         const uint64_t rs = P.rep_stride[k] / 4;
-        for (uint32_t q = 0; q < P.reps[k]; ++q) {
-            g = add4(g, __ldcg(r + q * rs));
-            r[q * rs] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t reps = P.reps[k];
+        float4 v[kWide];
+#pragma unroll
+        for (int q = 0; q < kWide; ++q) v[q] = static_cast<uint32_t>(q) < reps ? __ldcg(r + q * rs) : zero;
+        float4 acc = zero;
+#pragma unroll
+        for (int q = 0; q < kWide; ++q) acc = add4(acc, v[q]);
+#pragma unroll
+        for (int q = 0; q < kWide; ++q)
+            if (static_cast<uint32_t>(q) < reps) r[q * rs] = zero;
+        for (uint32_t q = kWide; q < reps; ++q) {
+            acc = add4(acc, __ldcg(r + q * rs));
+            r[q * rs] = zero;
         }
+        g = add4(g, acc);
     }
     if (!done && col < P.rank) {
         float4* a4p = reinterpret_cast<float4*>(P.A[k]) + loc;
@@ -316,7 +330,7 @@ constexpr int kAdamChunk = 128;
 constexpr int kBatchSpinLimit = 1 << 21;
 constexpr int kClaim = 1;  // queue items a warp claims at a time (more made the tail longer: measured)
 
-__global__ void __launch_bounds__(256) batch_fused_kernel(const BatchArgs a)
+__global__ void __launch_bounds__(256, 3) batch_fused_kernel(const BatchArgs a)
 {
     pdl_wait();
     pdl_trigger();
@@ -374,7 +388,7 @@ __global__ void __launch_bounds__(256) batch_fused_kernel(const BatchArgs a)
                 const bool done = P.st->done != 0;
                 const int64_t c0 = (ai - s_adam[pb]) * kAdamChunk;
                 const int64_t n4 = P.off4[P.d];
-#pragma unroll
+#pragma unroll 1
                 for (int i = 0; i < kAdamChunk / 32; ++i) {
                     const int64_t p4 = c0 + i * 32 + lane;
                     if (p4 < n4) batch_adam_element(P, p4, ic1, ic2, alpha, done);
