@@ -326,6 +326,11 @@ __global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
 // GCP_ERR_TIMEOUT in the problem's state and skips the chunk.  The problem's
 // last Adam chunk advances its t and iter and clears its counters; the last
 // warp to leave clears the queue.
+// Release / acquire ordering at device scope: a warp's reductions are made
+// visible before its count of finished batches (release), and a waiting warp
+// sees them after reading the count (acquire).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 constexpr int kAdamChunk = 128;
 constexpr int kBatchSpinLimit = 1 << 21;
 constexpr int kClaim = 1;  // queue items a warp claims at a time (more made the tail longer: measured)
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(256, 3) batch_fused_kernel(const BatchArgs a)
                 batch_grad_item(a, s_work, item, lane);
                 __syncwarp();
                 if (lane == 0) {
-                    __threadfence();
+                    fence_acq_rel_gpu();
                     atomicAdd(&a.grad_done[find_problem(s_work, a.count, item)], 1u);
                 }
                 continue;
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(256, 3) batch_fused_kernel(const BatchArgs a)
                     }
                     __nanosleep(64);
                 }
-                __threadfence();
+                fence_acq_rel_gpu();
             }
             ok = __shfl_sync(kFull, ok, 0);
             __syncwarp();
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(256, 3) batch_fused_kernel(const BatchArgs a)
             }
             __syncwarp();
             if (lane == 0) {
-                __threadfence();
+                fence_acq_rel_gpu();
                 const unsigned chunks = static_cast<unsigned>(s_adam[pb + 1] - s_adam[pb]);
                 if (atomicAdd(&a.adam_done[pb], 1u) + 1u == chunks) {  // the problem's last Adam chunk
                     gcp_adam_state* st = P.st;
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(256, 3) batch_fused_kernel(const BatchArgs a)
                     st->iter += 1;
                     a.grad_done[pb] = 0u;
                     a.adam_done[pb] = 0u;
-                    __threadfence();
+                    fence_acq_rel_gpu();
                 }
             }
         }
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(256, 3) batch_fused_kernel(const BatchArgs a)
         if (atomicAdd(&a.queue[1], 1ull) + 1ull == warps) {
             a.queue[0] = 0ull;
             a.queue[1] = 0ull;
-            __threadfence();
+            fence_acq_rel_gpu();
         }
     }
 }
