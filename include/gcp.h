@@ -47,8 +47,11 @@ typedef enum gcp_status {
     GCP_ERR_CUDA = 2,             /* a CUDA runtime call failed */
     GCP_ERR_NO_MEMORY = 3,        /* a library-owned allocation failed */
     GCP_ERR_SAMPLE_SHORTFALL = 4, /* stratified zeros: fewer than q accepted */
-    GCP_ERR_TIMEOUT = 5,          /* reserved for a bounded device-side wait that gives up;
-                                     no kernel of this version waits on another */
+    GCP_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up: the stratified zero
+                                     pass's look-back over earlier tiles (device status of
+                                     the handle) or a fused batched iteration's wait for a
+                                     problem's gradient (that problem's state->status);
+                                     neither can run out while the kernel's own blocks run */
     GCP_ERR_NONFINITE = 6,        /* a non-finite loss estimate was seen */
     GCP_ERR_UNSUPPORTED = 7       /* valid but not supported (e.g. prod(dims) >= 2^64 for stratified) */
 } gcp_status;
