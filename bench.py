@@ -382,6 +382,35 @@ def time_iterations(torch, gcp, h, F, loss, spec, stream, iters=10, replays=3):
     return a.elapsed_time(b) * 1e-3 / (replays * iters)
 
 
+def adam_only_time(torch, gcp, F, stream, iters=50, replays=3):
+    """Device time (s) per Adam step (gcp_adam_step) of a captured sequence of
+    steps on throwaway state: subtracted from a captured whole iteration it
+    bounds the gradient kernel's time inside the iteration from above (the
+    standalone step folds no replica slabs, so it is the cheaper Adam)."""
+    from paper_1906_01687_gb300.autotune import side_stream
+    with torch.cuda.stream(stream):
+        Ft = gcp.Factors([a[:, :F.rank] for a in F.A])
+        G, B, C = Ft.like(), Ft.like(), Ft.like()
+        st = gcp.new_state(Ft.A[0].device)
+        gcp.gcp_state_init(st, 1e-4, stream=stream)
+        gcp.gcp_adam_step(Ft, G, B, C, st, stream=stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side_stream(stream)):
+        for _ in range(iters):
+            gcp.gcp_adam_step(Ft, G, B, C, st, stream=torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(replays):
+            g.replay()
+        b.record(stream)
+    stream.synchronize()
+    del g
+    return a.elapsed_time(b) * 1e-3 / (replays * iters)
+
+
 def grad_launch_time(torch, gcp, h, F, loss, spec, stream, launches=50):
     """Per-launch device time of the gradient kernel inside GCP-Adam
     iterations on throwaway state (events around each gradient launch)."""
@@ -706,6 +735,8 @@ def form_dense100(torch, gcp, stream, peak, args, tau=100, epochs=5):
     t_epoch = _time_calls(torch, run.run_epoch, stream, epochs)
     mean_s, n, adam_s = time_grad_kernel(torch, gcp, run.h, run.iteration, stream)
     iter_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
+    adam_s = adam_only_time(torch, gcp, run.F, stream)
+    grad_in_graph = iter_s - adam_s
     gb = s * (4 + row_bytes(4, rank, 4))
     out = {"workload": "dense-100x100x100x100-r10-gaussian-uniform-s1e5", "tau": tau,
            "entries_per_s": tau * s / t_epoch, "ms_per_epoch": t_epoch * 1e3,
@@ -713,6 +744,9 @@ def form_dense100(torch, gcp, stream, peak, args, tau=100, epochs=5):
            "grad_frac_of_measured_hbm": gb / mean_s / 1e9 / peak,
            "iteration_us_in_graph": iter_s * 1e6,
            "iteration_frac_of_measured_hbm": (gb + adam_bytes(dims, rank)) / iter_s / 1e9 / peak,
+           "adam_only_us_in_graph": adam_s * 1e6,
+           "grad_us_in_graph_at_most": grad_in_graph * 1e6,
+           "grad_frac_in_graph_at_least": gb / grad_in_graph / 1e9 / peak,
            "launch": gcp.gcp_get_launch(run.h, run.F, s), "autotuned": run.tuned,
            "traffic_note": "factors and G are 16 KB: rows and updates are L2 hits; DRAM traffic is the X gathers"}
     if not args.no_sweep:
