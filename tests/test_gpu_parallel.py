@@ -183,3 +183,26 @@ def test_refresh_takes_up_new_tensor_contents():
     A = f64([a[:, :5].cpu().numpy() for a in F.A])
     assert_grad_close(grad_to_numpy(G, 5), oracle.grad(dims, A, oracle.POISSON_LOG, SO),
                       oracle.grad_abs(dims, A, oracle.POISSON_LOG, SO))
+
+
+def test_refresh_recounts_the_observed_entries():
+    """Entry weights rewritten in place (more entries missing) and refreshed:
+    the observed-entry sampler counts |Omega_obs| again and draws the
+    oracle's list for the new weights (weights (|Omega_obs| / q) v_i)."""
+    g = gcp()
+    dims = (20, 15, 12)
+    r = np.random.default_rng(40)
+    X = r.standard_normal(dims).astype(np.float32)
+    v1 = (r.random(dims) >= 0.2).astype(np.float32)
+    v2 = np.where(r.random(dims) >= 0.5, v1, 0.0).astype(np.float32)
+    XT = g.DataTensor.dense(X, weights=v1)
+    h = g.Handle(XT)
+    S = g.Sampling(g.SAMPLER_OBSERVED, 0, 3001, seed=8, stream=2)
+    g.gcp_sample(h, S)  # counts the entries of nonzero weight of v1
+    XT.weights.copy_(torch.as_tensor(v2.reshape(-1)))
+    g.gcp_refresh(h)
+    L = g.gcp_sample(h, S)
+    torch.cuda.synchronize()
+    assert g.gcp_get_device_status(h) == 0
+    XO = oracle.Tensor(dims, dense=X.astype(np.float64), weights=v2.astype(np.float64))
+    assert_lists_equal(L, oracle.sample(XO, oracle.OBSERVED, 0, 3001, 8, 2))
