@@ -7,9 +7,9 @@ in COO (int32 indices), drawn from a planted rank-32 logistic model;
 Bernoulli-logit loss; semi-stratified sampling (Alg. 3) with 1e6 nonzero and
 1e6 "zero" draws per iteration; rank 32; FP32 factors; the loss estimate on a
 fixed semi-stratified set of 1e5 + 1e5 entries.  One step is one GCP-Adam
-epoch (Alg. 4): tau = 100 iterations of (fused sample + gradient, Adam
-step), the loss estimate and the accept-or-revert decision, captured once as
-a CUDA graph and replayed.  Metric: sampled-gradient entries processed per
+epoch (Alg. 4): tau = 1000 iterations of (fused sample + gradient, Adam
+step; Section 5.1's epoch length), the loss estimate and the accept-or-revert
+decision, captured once as a CUDA graph and replayed.  Metric: sampled-gradient entries processed per
 second (tau (p + q) per step).
 
 The same line carries the other workloads as forms, each beside the plain
@@ -43,7 +43,7 @@ METRIC = "sampled-gradient entries/s"
 UNIT = "entries/s"
 WORKLOAD = "coo-1e5x1e5x1e4-nnz1e8-r32-bernoullilogit-semistratified-1e6+1e6"
 DIMS, NNZ, RANK = (100_000, 100_000, 10_000), 100_000_000, 32
-P_DRAWS, Q_DRAWS, EST_P, EST_Q, TAU = 1_000_000, 1_000_000, 100_000, 100_000, 100
+P_DRAWS, Q_DRAWS, EST_P, EST_Q, TAU = 1_000_000, 1_000_000, 100_000, 100_000, 1000  # tau: Section 5.1's default
 ALPHA = 0.01  # Adam's learning rate, Section 5.1's default
 RECORD_BYTES = 16  # packed record of a nonzero of a 3-way tensor: three indices and the value's bits
 
