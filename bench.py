@@ -770,6 +770,18 @@ def sweep_draws(torch, gcp, run, stream, peak, rank, sizes=(100_000, 1_000_000, 
     return out
 
 
+def count_problem(gcp):
+    """The count tensor's gcp_grad workload: (dims, rank, p, q, idx, vals,
+    handle, initial factors, stratified spec)."""
+    from paper_1906_01687_gb300 import synth
+    dims, rank, p, q = (6186, 24, 77, 32), 10, 100_000, 100_000
+    idx, vals, _ = synth.count_tensor()
+    h = gcp.Handle(gcp.DataTensor.coo(dims, idx, vals))
+    A = [(a * 0.3).astype(np.float32) for a in synth.initial_guess(dims, rank, 4, positive=True)]
+    spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, p, q, 1687, 0)
+    return dims, rank, p, q, idx, vals, h, A, spec
+
+
 def form_count(torch, gcp, stream, peak):
     """FP32 vs BF16 factor storage on the count tensor (6186x24x77x32, 5.33M
     nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): the whole
@@ -777,13 +789,8 @@ def form_count(torch, gcp, stream, peak):
     the gradient's and the loss estimate's errors against the FP64 oracle (at
     the FP32 factors) on the same draws."""
     import oracle
-    from paper_1906_01687_gb300 import synth
     from paper_1906_01687_gb300.autotune import autotune, candidates, with_grids
-    dims, rank, p, q = (6186, 24, 77, 32), 10, 100_000, 100_000
-    idx, vals, _ = synth.count_tensor()
-    h = gcp.Handle(gcp.DataTensor.coo(dims, idx, vals))
-    A = [(a * 0.3).astype(np.float32) for a in synth.initial_guess(dims, rank, 4, positive=True)]
-    spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, p, q, 1687, 0)
+    dims, rank, p, q, idx, vals, h, A, spec = count_problem(gcp)
     XO = oracle.Tensor(dims, coo=np.stack([i.astype(np.int64) for i in idx], axis=1), vals=vals.astype(np.float64))
     SO = oracle.sample(XO, oracle.STRATIFIED, p, q, 1687, 0)
     ref = oracle.grad(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SO)
@@ -934,7 +941,8 @@ def main():
                          "profiled for that workload's kernel breakdown)")
     ap.add_argument("--profile", type=int, default=0, metavar="ITERS",
                     help="only set up the benchmark's run and take ITERS eager GCP-Adam iterations, then exit "
-                         "(the command profiled with ncu; prints one line of timing)")
+                         "(the command profiled with ncu; prints one line of timing); with --form count, ITERS "
+                         "gcp_grad calls on the count tensor instead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -967,11 +975,16 @@ def form_arm(args):
 def profile_arm(args):
     """The benchmark's run set up as in ours_arm (no autotuning: the shape
     given by --tuning, else the automatic one), then --profile eager
-    iterations: a short, bounded command for ncu."""
+    iterations: a short, bounded command for ncu.  With --form count, the
+    count tensor's gcp_grad call instead (--profile calls)."""
     import torch
     from paper_1906_01687_gb300 import gcp
     from paper_1906_01687_gb300.adam import GcpAdam
     stream = torch.cuda.Stream()
+    if args.form == "count":
+        return profile_count(args, torch, gcp, stream)
+    if args.form:
+        raise SystemExit("--profile takes no --form but count")
     idx, A0, _ = large_input()
     XT = gcp.DataTensor.coo(DIMS, idx, None)
     with torch.cuda.stream(stream):
@@ -993,6 +1006,31 @@ def profile_arm(args):
                       "us_per_iteration": a.elapsed_time(b) * 1e3 / args.profile,
                       "grad_kernel_us": ms * 1e3 / max(n, 1),
                       "launch": gcp.gcp_get_launch(run.h, run.F, P_DRAWS + Q_DRAWS)}), flush=True)
+    return 0
+
+
+def profile_count(args, torch, gcp, stream):
+    """--profile calls of gcp_grad on the count tensor (ordered zero pass,
+    gradient, replica fold) in the shape --tuning gives, with the gradient
+    kernel's own event time beside the call's."""
+    dims, rank, p, q, idx, vals, h, A, spec = count_problem(gcp)
+    F = gcp.Factors(A)
+    G = F.like()
+    if args.tuning:
+        gcp.gcp_set_tuning(h, **json.loads(args.tuning))
+    call = lambda: gcp.gcp_grad(h, F, gcp.LOSS_POISSON_LOG, G, S=spec, stream=stream)
+    call()
+    stream.synchronize()
+    t_call = _time_calls(torch, call, stream, args.profile)
+    gcp.gcp_profile(h, True, args.profile)
+    for _ in range(args.profile):
+        call()
+    stream.synchronize()
+    ms, n = gcp.gcp_profile_read(h, 0)
+    gcp.gcp_profile(h, False)
+    print(json.dumps({"profile": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
+                      "calls": args.profile, "us_per_call": t_call * 1e6, "grad_kernel_us": ms * 1e3 / max(n, 1),
+                      "launch": gcp.gcp_get_launch(h, F, p + q)}), flush=True)
     return 0
 
 
