@@ -593,6 +593,13 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    (the previous such launch's stream + 1), checks it against *stream_dev
    after the wait and redoes the batch when it differs, so the draws are
    always those of *stream_dev.  Default 0 (wait first).
+   zero_pass (stratified and observed-entry sampling, Alg. 2 and Section
+   4.4): 0 (automatic) makes the zeros inside the gradient launch where the
+   walk is the group walk of 3 or 4 modes -- the grid's first blocks each
+   take a tile of block-size consecutive candidates, rank the accepted ones,
+   learn the count accepted before their tile by decoupled look-back (bounded
+   waits, GCP_ERR_TIMEOUT) and walk the kept ones as draws, with no list
+   written; 1 runs the separate ordered pass that lists the zeros first.
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -606,6 +613,7 @@ typedef struct gcp_tuning {
     int32_t group_draws;
     int32_t prefetch;
     int32_t early_draws;
+    int32_t zero_pass;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */
@@ -620,6 +628,7 @@ typedef struct gcp_launch_info {
     int32_t group_draws;
     int32_t prefetch;
     int32_t early_draws;
+    int32_t zero_tiles;  /* 1: stratified zeros are made inside the gradient launch */
 } gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch

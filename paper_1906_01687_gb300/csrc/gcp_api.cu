@@ -21,8 +21,8 @@ static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
 static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
-static_assert(sizeof(gcp_tuning) == 44, "gcp_tuning layout");
-static_assert(sizeof(gcp_launch_info) == 68, "gcp_launch_info layout");
+static_assert(sizeof(gcp_tuning) == 48, "gcp_tuning layout");
+static_assert(sizeof(gcp_launch_info) == 72, "gcp_launch_info layout");
 
 struct gcp_handle {
     gcp_tensor X{};
@@ -55,7 +55,7 @@ struct gcp_handle {
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
     int partials_cap = 0;
-    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0};
+    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0};
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
@@ -448,6 +448,14 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
     return GCP_OK;
 }
 
+// Whether a stratified or observed-entry launch of this shape makes its zeros
+// inside the gradient kernel (layout 3: the group walk of 3 or 4 modes).
+bool zero_tiles_apply(const gcp_handle* h, const Shape& sh)
+{
+    return h->tune.zero_pass == 0 && sh.layout() == 0 && h->X.d == sh.D &&
+           grad_has_config(sh.D, sh.L, sh.NC, 3);
+}
+
 ModeTable mode_table(const gcp_factors* F, int32_t d, const int64_t* dims)
 {
     ModeTable mt{};
@@ -680,14 +688,15 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     if (!t) {
-        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0};
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0};
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, 0)) return GCP_ERR_INVALID_ARG;
     if (t->prefetch < 0 || t->prefetch > 2) return GCP_ERR_INVALID_ARG;
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
-        t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1)
+        t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1 || t->zero_pass < 0 ||
+        t->zero_pass > 1)
         return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
@@ -711,6 +720,7 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     out->group_draws = sh.group;
     out->prefetch = sh.pf;
     out->early_draws = sh.early;
+    out->zero_tiles = zero_tiles_apply(h, sh) ? 1 : 0;
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
@@ -761,7 +771,9 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
     if ((S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
         st = S->kind == GCP_SAMPLER_OBSERVED ? ensure_observed(h, s) : ensure_hash(h, s);
         if (st != GCP_OK) return st;
-        if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 1023) / 1024, s)) != GCP_OK) return st;
+        // tile words for tiles of 1024 candidates (the separate pass) or of one
+        // block (zeros made in the gradient launch: blocks of at least 32 threads)
+        if ((st = ensure_zero_scratch(h, (zero_batch(h, S) + 31) / 32, s)) != GCP_OK) return st;
         if ((st = ensure_zero_list(h, S->q)) != GCP_OK) return st;
     }
     GCP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -809,19 +821,54 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     const bool early_ok = (a.dr.src == kSrcUniformDense || (a.dr.src == kSrcUniformSparse && table_ready) ||
                            a.dr.src == kSrcSparse) && !h->fresh_data;
     if (n_draws == 0) return GCP_OK;
-    if (S && (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
-        st = ensure_zero_list(h, S->q);
-        if (st != GCP_OK) return st;
-        int32_t* zdst[GCP_MAX_MODES] = {};
-        for (int k = 0; k < h->X.d; ++k) zdst[k] = h->zidx_base + static_cast<size_t>(k) * h->zq_cap;
-        st = run_zero_pass(h, S, stream_dev, zdst, nullptr, nullptr, nullptr, 0.0f, s);
-        if (st != GCP_OK) return st;
-        for (int k = 0; k < h->X.d; ++k) a.dr.zidx[k] = zdst[k];
-        a.dr.zcount = h->zcount;
-    }
     Shape sh;
     st = choose_shape(h, F, n_draws, &sh);
     if (st != GCP_OK) return st;
+    int layout = sh.layout();
+    int grid = sh.grid;
+    if (S && (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
+        // the zero draws of this launch: ranks [z_begin, z_end) of the kept candidates
+        const int64_t z_begin = std::max<int64_t>(a.dr.j_begin - a.dr.p, 0);
+        const int64_t z_end = std::max<int64_t>(a.dr.n_total - a.dr.p, 0);
+        if (zero_tiles_apply(h, sh) && z_end > z_begin) {
+            // made inside the gradient launch (layout 3): the first `tiles` blocks
+            if (S->kind == GCP_SAMPLER_STRATIFIED && (st = ensure_hash(h, s)) != GCP_OK) return st;
+            const int64_t batch = zero_batch(h, S);
+            const int64_t tiles = (batch + sh.block - 1) / sh.block;
+            if ((st = ensure_zero_scratch(h, tiles, s)) != GCP_OK) return st;
+            ZeroTileArgs& z = a.zt;
+            z.tiles = tiles;
+            z.cap = 64 * batch;
+            z.q = S->q;
+            z.z_begin = z_begin;
+            z.z_end = z_end;
+            z.observed = S->kind == GCP_SAMPLER_OBSERVED ? 1 : 0;
+            z.tag = static_cast<uint32_t>(z.observed ? kTagObserved : kTagZeroCandidate);
+            z.tile_status = h->tile_status;
+            z.tile_ctr = h->zero_ctrs;
+            z.done_ctr = h->zero_ctrs + 1;
+            z.count_out = h->zcount;
+            z.status = h->d_status;
+            a.dr.table = h->table;
+            a.dr.table_mask = h->table_mask;
+            // the other blocks walk the nonzero draws [j_begin, min(end, p))
+            a.dr.n_total = std::min(a.dr.n_total, a.dr.p);
+            const int64_t nz = std::max<int64_t>(a.dr.n_total - a.dr.j_begin, 0);
+            const int64_t per_warp = sh.group ? 32 / sh.L : 32;
+            const int64_t blocks_nz = (((nz + per_warp - 1) / per_warp) + sh.block / 32 - 1) / (sh.block / 32);
+            grid = static_cast<int>(tiles + std::min<int64_t>(sh.grid, blocks_nz));
+            layout = 3;
+        } else {
+            st = ensure_zero_list(h, S->q);
+            if (st != GCP_OK) return st;
+            int32_t* zdst[GCP_MAX_MODES] = {};
+            for (int k = 0; k < h->X.d; ++k) zdst[k] = h->zidx_base + static_cast<size_t>(k) * h->zq_cap;
+            st = run_zero_pass(h, S, stream_dev, zdst, nullptr, nullptr, nullptr, 0.0f, s);
+            if (st != GCP_OK) return st;
+            for (int k = 0; k < h->X.d; ++k) a.dr.zidx[k] = zdst[k];
+            a.dr.zcount = h->zcount;
+        }
+    }
     if (sh.rep_floats > h->rep_ws_cap) {
         cudaFree(h->rep_ws);
         h->rep_ws = nullptr;
@@ -874,7 +921,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     }
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));
-    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, sh.layout(), sh.grid, sh.block, sh.smem, s));
+    GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, layout, grid, sh.block, sh.smem, s));
     h->fresh_data = false;
     if (launched) *launched = true;
     if (timed) {

@@ -7,9 +7,16 @@ namespace gcpk {
 const void* grad_kernel_ptr_d3(int L, int NC, bool bf16, int layout);
 const void* grad_kernel_ptr_d4(int L, int NC, bool bf16, int layout);
 const void* grad_kernel_ptr_d8(int L, int NC, bool bf16, int layout);
+const void* grad_kernel_ptr_d3z(int L, int NC, bool bf16);
+const void* grad_kernel_ptr_d4z(int L, int NC, bool bf16);
 
 static const void* grad_ptr(int D, int L, int NC, bool bf16, int layout)
 {
+    if (layout == 3) {  // the zeros made in the launch: 3 or 4 modes
+        if (D == 3) return grad_kernel_ptr_d3z(L, NC, bf16);
+        if (D == 4) return grad_kernel_ptr_d4z(L, NC, bf16);
+        return nullptr;
+    }
     switch (D) {
     case 3: return grad_kernel_ptr_d3(L, NC, bf16, layout);
     case 4: return grad_kernel_ptr_d4(L, NC, bf16, layout);

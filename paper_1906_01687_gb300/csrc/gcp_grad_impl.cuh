@@ -32,10 +32,254 @@
 #include <type_traits>
 
 #include "gcp_draw.cuh"
+#include "gcp_lookback.cuh"
 
 namespace gcpk {
 
-// LAYOUT 0: the group walk; 1: the prefetch layout; 2: the staged walk.
+// One batch of the group walk.  Groups of L lanes take the batch's draws in
+// turn (step b: the descriptor of lane gbase + b), or with `group` each group
+// takes its own draw in one step.  m_i is reduced across the group with
+// shuffles, then y_i and the d row updates follow.  verify: the batch was
+// drawn from a predicted stream word, checked against `actual` before the
+// first update; on a miss the batch is redrawn (jfirst: this lane's draw).
+template <int D, int L, int NC, bool BF16>
+__device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float* (&gdst)[D], float* sG, int steps,
+                                           bool group, bool& verify, uint64_t& stream, uint64_t actual,
+                                           int64_t jfirst)
+{
+    using T = std::conditional_t<BF16, __nv_bfloat16, float>;
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const int d = D <= 4 ? D : a.dr.d;
+    const int ld = a.ld, rank = a.rank;
+    auto row4 = [&](int k, uint32_t i, int col) -> float4 {
+        return load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(i) * ld + col);
+    };
+#pragma unroll 1
+    for (int b = 0; b < steps; ++b) {
+        const int src = group ? lane : gbase + b;
+        uint32_t ix[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) ix[k] = __shfl_sync(kFull, my.ix[k], src);
+        const float x = __shfl_sync(kFull, my.x, src);
+        const float w = __shfl_sync(kFull, my.w, src);
+        const int cls = __shfl_sync(kFull, my.cls, src);
+        const bool valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
+
+        // m_i = sum_j prod_k A_k(i_k, j) over this lane's chunks of the d rows.
+        // With one chunk per lane the rows stay in registers for the scatter;
+        // with several they are re-read there (L1 hits) to keep registers low.
+        // For 3 and 4 modes with one chunk, the pairwise products of the rows
+        // serve both m and the leave-one-out products of the scatter.
+        constexpr bool kKeep = NC == 1;
+        constexpr bool kPairs = kKeep && (D == 3 || D == 4);
+        float4 r[D];
+        float4 p01 = make_float4(0.f, 0.f, 0.f, 0.f), p23 = p01;
+        float part = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int col = (gl * NC + c) * 4;
+            float4 v[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (k >= d) {
+                    v[k] = make_float4(1.f, 1.f, 1.f, 1.f);
+                } else if (valid && col < rank) {
+                    v[k] = row4(k, ix[k], col);
+                } else {
+                    v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (kKeep) r[k] = v[k];
+            }
+            float4 prod;
+            if constexpr (kPairs) {
+                p01 = mul4(v[0], v[1]);
+                if constexpr (D == 4) {
+                    p23 = mul4(v[2], v[3]);
+                    prod = mul4(p01, p23);
+                } else {
+                    prod = mul4(p01, v[2]);
+                }
+            } else {
+                prod = v[0];
+#pragma unroll
+                for (int k = 1; k < D; ++k) prod = mul4(prod, v[k]);
+            }
+            part += sum4(prod);
+        }
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+        if (verify) {  // warp-uniform; first batch only
+            verify = false;
+            if (actual != stream) {  // mispredicted: redraw the batch and start it again
+                stream = actual;
+                make_draw<D>(a.dr, jfirst, stream, my);
+                b = -1;
+                continue;
+            }
+        }
+        if (!valid) continue;  // no shuffles below this point
+        const float y = entry_y(a.loss, cls, x, part, w);
+
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int col = (gl * NC + c) * 4;
+            if (col >= rank) continue;
+            // upd[k] = y prod_{l != k} A_l(i_l, cols)
+            float4 upd[D];
+            if constexpr (kPairs) {
+                if constexpr (D == 4) {
+                    const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
+                    upd[0] = mul4(yp23, r[1]);
+                    upd[1] = mul4(yp23, r[0]);
+                    upd[2] = mul4(yp01, r[3]);
+                    upd[3] = mul4(yp01, r[2]);
+                } else {
+                    const float4 yr2 = scale4(y, r[2]);
+                    upd[0] = mul4(yr2, r[1]);
+                    upd[1] = mul4(yr2, r[0]);
+                    upd[2] = scale4(y, p01);
+                }
+            } else {
+                float4 rc[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if (kKeep) rc[k] = r[k];
+                    else rc[k] = k < d ? row4(k, ix[k], col) : make_float4(1.f, 1.f, 1.f, 1.f);
+                }
+                // prefix and suffix products
+                float4 pre[D], suf[D];
+                pre[0] = make_float4(y, y, y, y);
+#pragma unroll
+                for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
+                suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+                for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
+#pragma unroll
+                for (int k = 0; k < D; ++k) upd[k] = mul4(pre[k], suf[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (k >= d) continue;
+                if ((a.smem_mask >> k) & 1u) {
+                    float* s = sG + a.smem_off[k] + static_cast<size_t>(ix[k]) * ld + col;
+                    atomicAdd(s + 0, upd[k].x);
+                    atomicAdd(s + 1, upd[k].y);
+                    atomicAdd(s + 2, upd[k].z);
+                    atomicAdd(s + 3, upd[k].w);
+                } else {
+                    atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd[k]);
+                }
+            }
+        }
+    }
+}
+
+// Candidate c of the zero stream (Alg. 2), or of the observed-entry stream
+// (Section 4.4), as a draw descriptor; returns whether it is accepted: c is
+// below the cap and its linear key is not a nonzero's (observed: its weight
+// v_i is nonzero).
+template <int D>
+__device__ __forceinline__ bool zt_candidate(const GradArgs& a, uint64_t stream, int64_t c, Draw<D>& o)
+{
+    const DrawArgs& dr = a.dr;
+    draw_index<D>(dr.dims, dr.seed, dr.problem, stream, a.zt.tag, static_cast<uint64_t>(c), dr.d, o.ix);
+    o.valid = false;
+    o.x = 0.0f;
+    o.w = dr.w_second;
+    o.cls = GCP_CLS_STRAT_ZERO;
+    if (c >= a.zt.cap) return false;
+    uint64_t key = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        if (k < dr.d) key += static_cast<uint64_t>(o.ix[k]) * dr.strides[k];
+    if (a.zt.observed) {
+        const float v = __ldg(dr.W + key);
+        o.cls = GCP_CLS_UNIFORM;
+        o.x = v != 0.0f ? __ldg(dr.X + key) : 0.0f;
+        o.w = dr.w_first * v;
+        return v != 0.0f;
+    }
+    return !hash_contains(dr.table, dr.table_mask, key);
+}
+
+// A block of the first a.zt.tiles (layout 3): claims the next tile of
+// blockDim.x candidates, one per thread (every hash probe in flight at once),
+// ranks its accepted candidates, looks back for the count accepted by the
+// earlier tiles, and walks the accepted candidates whose rank in candidate
+// order falls in [z_begin, z_end) as zero draws (x = 0, w = zeta / q).  The
+// block of the last tile continues in candidate order up to the cap while
+// fewer than q were accepted, and reports a shortfall.  The last tile to
+// finish clears the tile words and counters for the next launch.
+template <int D, int L, int NC, bool BF16>
+__device__ __forceinline__ void zero_tiles_block(const GradArgs& a, float* (&gdst)[D], float* sG, uint64_t stream)
+{
+    __shared__ int zt_warp[32];
+    __shared__ int64_t zt_tile, zt_excl;
+    __shared__ int zt_ok, zt_last;
+    const ZeroTileArgs& z = a.zt;
+    const int64_t B = blockDim.x;
+    if (threadIdx.x == 0) zt_tile = static_cast<int64_t>(atomicAdd(z.tile_ctr, 1u));
+    __syncthreads();
+    const int64_t tile = zt_tile;
+    Draw<D> my;
+    const bool acc = zt_candidate<D>(a, stream, tile * B + threadIdx.x, my);
+    int total = 0;
+    const int rank = block_flag_rank(acc, zt_warp, total);
+    if (threadIdx.x < 32) {
+        int64_t excl = 0;
+        const bool ok = tile_lookback(z.tile_status, tile, total, excl);
+        if (threadIdx.x == 0) {
+            if (!ok) set_status(z.status, GCP_ERR_TIMEOUT);
+            zt_excl = excl;
+            zt_ok = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    const bool ok = zt_ok != 0;
+    int64_t count = zt_excl;  // accepted before this thread's batch of candidates
+    int ntot = total, nrank = rank;
+    bool nacc = acc;
+    bool verify = false;
+    uint64_t st = stream;
+    // the tile, then (the last tile's block only, block-uniform) continuation
+    // batches of blockDim.x candidates in order while fewer than q were accepted
+#pragma unroll 1
+    for (int64_t c0 = z.tiles * B;; c0 += B) {
+        my.valid = ok && nacc && count + nrank >= z.z_begin && count + nrank < z.z_end;
+        walk_batch<D, L, NC, BF16>(a, my, gdst, sG, L, false, verify, st, stream, 0);
+        if (tile != z.tiles - 1) break;
+        count = ok ? count + ntot : 0;
+        if (!(ok && count < z.q && c0 < z.cap)) {
+            if (threadIdx.x == 0) {
+                const int64_t kept = count < z.q ? count : z.q;
+                if (z.count_out) *z.count_out = kept;
+                if (kept < z.q) set_status(z.status, ok ? GCP_ERR_SAMPLE_SHORTFALL : GCP_ERR_TIMEOUT);
+            }
+            break;
+        }
+        nacc = zt_candidate<D>(a, stream, c0 + threadIdx.x, my);
+        nrank = block_flag_rank(nacc, zt_warp, ntot);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        zt_last = atomicAdd(z.done_ctr, 1u) == static_cast<unsigned int>(z.tiles - 1);
+    }
+    __syncthreads();
+    if (zt_last) {
+        for (int64_t t = threadIdx.x; t < z.tiles; t += B) z.tile_status[t] = 0ull;
+        if (threadIdx.x == 0) {
+            *z.tile_ctr = 0u;
+            *z.done_ctr = 0u;
+        }
+    }
+}
+
+// LAYOUT 0: the group walk; 1: the prefetch layout; 2: the staged walk; 3: the
+// group walk with the stratified zeros made in the launch (zero_tiles_block).
 // Blocks of 256 per SM the registers must allow: four (64 registers) for the
 // group walk with one chunk per lane and 2 or more lanes, which fits without
 // spilling; three for the other group and staged walks of at most 4 modes;
@@ -43,7 +287,7 @@ namespace gcpk {
 template <int D, int L, int NC>
 constexpr int grad_min_blocks(int layout)
 {
-    return (D <= 4 && layout == 0 && NC == 1 && L >= 2) ? 4 : ((D <= 4 && layout != 1) ? 3 : 2);
+    return (D <= 4 && (layout == 0 || layout == 3) && NC == 1 && L >= 2) ? 4 : ((D <= 4 && layout != 1) ? 3 : 2);
 }
 
 template <int D, int L, int NC, bool BF16, int LAYOUT>
@@ -51,6 +295,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
 {
     constexpr bool PF = LAYOUT == 1;
     constexpr bool STAGED = LAYOUT == 2;
+    constexpr bool ZT = LAYOUT == 3;
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
@@ -60,7 +305,12 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     const int lane = threadIdx.x & 31;
     const int gl = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    // layout 3: the first a.zt.tiles blocks make and walk the zeros; the
+    // others walk the nonzero draws as blocks 0, 1, ... of the rest of the grid
+    const bool zblock = ZT && static_cast<int64_t>(blockIdx.x) < a.zt.tiles;
+    const int64_t vblock = ZT ? static_cast<int64_t>(blockIdx.x) - a.zt.tiles : static_cast<int64_t>(blockIdx.x);
+    const int64_t vgrid = ZT ? static_cast<int64_t>(gridDim.x) - a.zt.tiles : static_cast<int64_t>(gridDim.x);
+    const int64_t nwarps = (vgrid * blockDim.x) >> 5;
     const int d = D <= 4 ? D : a.dr.d;
     const int ld = a.ld, rank = a.rank;
 
@@ -75,14 +325,13 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     const int steps = a.group_draws ? 1 : L;
     const int sub = a.group_draws ? lane / L : lane;
     // (draws j_begin .. n_total - 1: a draw range of the spec when j_begin > 0)
-    const int64_t wb0 =
-        a.dr.j_begin + (static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * per_warp;
+    const int64_t wb0 = a.dr.j_begin + (static_cast<int64_t>(threadIdx.x >> 5) * vgrid + vblock) * per_warp;
     // early descriptors for this warp: every draw of its first batch reads only
     // data written before the preceding kernel (with stratified sampling, the
     // nonzero draws j < p; the zeros come from the zero pass just before)
     // (a warp vote, so that the condition is warp-uniform by construction)
-    const bool early =
-        a.early != 0 && __all_sync(0xFFFFFFFFu, a.dr.src != kSrcSparse || a.dr.semi || wb0 + per_warp <= a.dr.p);
+    const bool early = a.early != 0 && !zblock &&
+                       __all_sync(0xFFFFFFFFu, a.dr.src != kSrcSparse || a.dr.semi || wb0 + per_warp <= a.dr.p);
 
     // The first batch's descriptors: before the dependency wait when early
     // (from the predicted stream word when it lives in device memory).
@@ -115,11 +364,8 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     } else if (!early) {
         stream = a.dr.stream;
     }
-    if (!early) make_draw<D>(a.dr, wb0 + sub, stream, my);
+    if (!early && !zblock) make_draw<D>(a.dr, wb0 + sub, stream, my);
     if (a.smem_floats > 0) __syncthreads();  // the shared accumulators are zero
-    auto row4 = [&](int k, uint32_t i, int col) -> float4 {
-        return load4(static_cast<const T*>(a.A[k]) + static_cast<size_t>(i) * ld + col);
-    };
 
     // this CTA's destination of each mode (its replica slab, or G_k itself)
     float* gdst[D];
@@ -127,8 +373,11 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     for (int k = 0; k < D; ++k)
         gdst[k] = k < d ? a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k] : nullptr;
 
-    // warp-uniform loop over this warp's batches
-    for (int64_t wb = wb0; wb < a.dr.n_total; wb += nwarps * per_warp) {
+    if constexpr (ZT) {
+        if (zblock) zero_tiles_block<D, L, NC, BF16>(a, gdst, sG, stream);
+    }
+    // warp-uniform loop over this warp's batches (none in a zero-tile block)
+    for (int64_t wb = zblock ? a.dr.n_total : wb0; wb < a.dr.n_total; wb += nwarps * per_warp) {
         if (wb != wb0) make_draw<D>(a.dr, wb + sub, stream, my);
         if constexpr (STAGED) {
             // staged walk (one chunk per lane): every lane copies its own chunk of
@@ -252,124 +501,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
             }
             continue;
         }
-#pragma unroll 1
-        for (int b = 0; b < steps; ++b) {
-            const int src = a.group_draws ? lane : gbase + b;
-            uint32_t ix[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) ix[k] = __shfl_sync(kFull, my.ix[k], src);
-            const float x = __shfl_sync(kFull, my.x, src);
-            const float w = __shfl_sync(kFull, my.w, src);
-            const int cls = __shfl_sync(kFull, my.cls, src);
-            const bool valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
-
-            // m_i = sum_j prod_k A_k(i_k, j) over this lane's chunks of the d rows.
-            // With one chunk per lane the rows stay in registers for the scatter;
-            // with several they are re-read there (L1 hits) to keep registers low.
-            // For 3 and 4 modes with one chunk, the pairwise products of the rows
-            // serve both m and the leave-one-out products of the scatter.
-            constexpr bool kKeep = NC == 1;
-            constexpr bool kPairs = kKeep && (D == 3 || D == 4);
-            float4 r[D];
-            float4 p01 = make_float4(0.f, 0.f, 0.f, 0.f), p23 = p01;
-            float part = 0.0f;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int col = (gl * NC + c) * 4;
-                float4 v[D];
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if (k >= d) {
-                        v[k] = make_float4(1.f, 1.f, 1.f, 1.f);
-                    } else if (valid && col < rank) {
-                        v[k] = row4(k, ix[k], col);
-                    } else {
-                        v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    if (kKeep) r[k] = v[k];
-                }
-                float4 prod;
-                if constexpr (kPairs) {
-                    p01 = mul4(v[0], v[1]);
-                    if constexpr (D == 4) {
-                        p23 = mul4(v[2], v[3]);
-                        prod = mul4(p01, p23);
-                    } else {
-                        prod = mul4(p01, v[2]);
-                    }
-                } else {
-                    prod = v[0];
-#pragma unroll
-                    for (int k = 1; k < D; ++k) prod = mul4(prod, v[k]);
-                }
-                part += sum4(prod);
-            }
-#pragma unroll
-            for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
-            if (verify) {  // warp-uniform; first batch only
-                verify = false;
-                if (actual != stream) {  // mispredicted: redraw the batch and start it again
-                    stream = actual;
-                    make_draw<D>(a.dr, wb + sub, stream, my);
-                    b = -1;
-                    continue;
-                }
-            }
-            if (!valid) continue;  // no shuffles below this point
-            const float y = entry_y(a.loss, cls, x, part, w);
-
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int col = (gl * NC + c) * 4;
-                if (col >= rank) continue;
-                // upd[k] = y prod_{l != k} A_l(i_l, cols)
-                float4 upd[D];
-                if constexpr (kPairs) {
-                    if constexpr (D == 4) {
-                        const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
-                        upd[0] = mul4(yp23, r[1]);
-                        upd[1] = mul4(yp23, r[0]);
-                        upd[2] = mul4(yp01, r[3]);
-                        upd[3] = mul4(yp01, r[2]);
-                    } else {
-                        const float4 yr2 = scale4(y, r[2]);
-                        upd[0] = mul4(yr2, r[1]);
-                        upd[1] = mul4(yr2, r[0]);
-                        upd[2] = scale4(y, p01);
-                    }
-                } else {
-                    float4 rc[D];
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        if (kKeep) rc[k] = r[k];
-                        else rc[k] = k < d ? row4(k, ix[k], col) : make_float4(1.f, 1.f, 1.f, 1.f);
-                    }
-                    // prefix and suffix products
-                    float4 pre[D], suf[D];
-                    pre[0] = make_float4(y, y, y, y);
-#pragma unroll
-                    for (int k = 1; k < D; ++k) pre[k] = mul4(pre[k - 1], rc[k - 1]);
-                    suf[D - 1] = make_float4(1.f, 1.f, 1.f, 1.f);
-#pragma unroll
-                    for (int k = D - 2; k >= 0; --k) suf[k] = mul4(suf[k + 1], rc[k + 1]);
-#pragma unroll
-                    for (int k = 0; k < D; ++k) upd[k] = mul4(pre[k], suf[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if (k >= d) continue;
-                    if ((a.smem_mask >> k) & 1u) {
-                        float* s = sG + a.smem_off[k] + static_cast<size_t>(ix[k]) * ld + col;
-                        atomicAdd(s + 0, upd[k].x);
-                        atomicAdd(s + 1, upd[k].y);
-                        atomicAdd(s + 2, upd[k].z);
-                        atomicAdd(s + 3, upd[k].w);
-                    } else {
-                        atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd[k]);
-                    }
-                }
-            }
-        }
+        walk_batch<D, L, NC, BF16>(a, my, gdst, sG, steps, a.group_draws != 0, verify, stream, actual, wb + sub);
     }
 
     // the prediction for the next launch that reads its stream word from memory
@@ -416,6 +548,19 @@ const void* grad_kernel_ptr(int L, int NC, int layout)
     if (layout != 0) return nullptr;
 #define GCP_CASE(LL, CC) \
     if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, 0>);
+    GCP_GRAD_CONFIGS(GCP_CASE)
+#undef GCP_CASE
+    return nullptr;
+}
+
+// The group walk with the zeros made in the launch (layout 3), at most 4
+// modes: instantiated in translation units of their own.
+template <int D, bool BF16>
+const void* grad_kernel_ptr_zt(int L, int NC)
+{
+    static_assert(D <= 4, "layout 3: at most 4 modes");
+#define GCP_CASE(LL, CC) \
+    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, 3>);
     GCP_GRAD_CONFIGS(GCP_CASE)
 #undef GCP_CASE
     return nullptr;

@@ -49,6 +49,28 @@ struct DrawArgs {
     const int8_t* lcls;
 };
 
+// Stratified zeros (Alg. 2) or observed entries (Section 4.4) made inside the
+// gradient launch instead of listed by a separate pass: the grid's first
+// `tiles` blocks each take a tile of blockDim.x consecutive candidates (tiles
+// numbered in the order the blocks claim them), count the accepted ones,
+// learn how many earlier tiles accepted by decoupled look-back, and walk the
+// accepted candidates whose rank in candidate order is in [z_begin, z_end)
+// as zero draws; the block of the last tile continues in candidate order
+// when the tiles accepted fewer than q.
+struct ZeroTileArgs {
+    int64_t tiles;            // 0: off (zeros come from a separate pass's list)
+    int64_t cap;              // candidates allowed in total (64 batches)
+    int64_t q;                // zeros (entries) kept
+    int64_t z_begin, z_end;   // ranks of the kept candidates that are this launch's draws
+    uint32_t tag;             // candidate stream: zero candidates, or observed-entry candidates
+    int32_t observed;         // 1: accept v_i != 0 (dr.W); x = X(i), w = dr.w_first v_i
+    unsigned long long* tile_status;  // per tile: flag and count or inclusive prefix (zero between launches)
+    unsigned int* tile_ctr;   // next tile to claim (zero between launches)
+    unsigned int* done_ctr;   // tiles finished (zero between launches)
+    int64_t* count_out;       // accepted candidates kept (<= q)
+    int32_t* status;
+};
+
 struct GradArgs {
     DrawArgs dr;
     int32_t ld, rank, loss, smem_floats;
@@ -62,6 +84,7 @@ struct GradArgs {
     int32_t early;                 // 1: each warp's first descriptors are made before the dependency wait
     int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
     gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
+    ZeroTileArgs zt;               // layout 3: the zeros made in this launch (dr.n_total then ends the nonzeros)
 };
 
 // Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).
@@ -184,7 +207,8 @@ inline cudaError_t launch_pdl_ptr(const void* kernel, dim3 grid, dim3 block, siz
 }
 
 // Launchers (defined in the kernel translation units).
-// layout: 0 the group walk, 1 the prefetch layout
+// layout: 0 the group walk, 1 the prefetch layout, 2 the staged walk, 3 the group walk with
+// the stratified zeros made in the launch (ZeroTileArgs)
 cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int layout, int grid, int block,
                         size_t smem, cudaStream_t s);
 cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int layout, int block, size_t smem, int* blocks_per_sm);

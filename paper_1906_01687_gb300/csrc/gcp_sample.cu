@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "gcp_draw.cuh"
+#include "gcp_lookback.cuh"
 
 namespace gcpk {
 
@@ -192,10 +193,6 @@ cudaError_t launch_materialise(const DrawArgs& dr, int32_t* const idx[GCP_MAX_MO
 // ---------------------------------------------------------------------------
 constexpr int kZeroTile = 1024;
 constexpr int kZeroBlock = 1024;  // one candidate per thread
-constexpr unsigned long long kTileCount = 1ull << 62;   // tile word: this tile's count is published
-constexpr unsigned long long kTilePrefix = 2ull << 62;  // tile word: its inclusive prefix is published
-constexpr unsigned long long kTileValue = (1ull << 62) - 1ull;
-constexpr int kSpinLimit = 1 << 21;
 
 template <int D>
 __device__ __forceinline__ bool zero_candidate(const ZeroArgs& a, uint64_t stream, int64_t c, uint32_t (&ix)[D])
@@ -287,53 +284,13 @@ __global__ void __launch_bounds__(kZeroBlock) zero_pass_kernel(const ZeroArgs a)
     int64_t total;
     const int64_t rank = block_exclusive_scan_1024(acc ? 1 : 0, sh_warp, &total);
     if (threadIdx.x < 32) {
-        // warp 0 publishes this tile's count and looks back over the earlier
-        // tiles 32 at a time: one round trip reads a window of 32 tile words;
-        // the nearest published prefix in the window ends the look-back once
-        // every tile between it and this one has published its count
-        const int lane = threadIdx.x;
-        unsigned long long* words = a.tile_status;
+        // warp 0 publishes this tile's count and looks back over the earlier tiles
         int64_t excl = 0;
-        int ok = 1;
-        if (tile == 0) {
-            if (lane == 0) atomicExch(words, kTilePrefix | static_cast<unsigned long long>(total));
-        } else {
-            if (lane == 0) atomicExch(words + tile, kTileCount | static_cast<unsigned long long>(total));
-            int64_t hi = tile - 1;  // the window is tiles hi, hi - 1, ..., hi - 31 (lane i: tile hi - i)
-            int spins = 0;
-            while (true) {
-                const int64_t j = hi - lane;
-                unsigned long long w = kTilePrefix | 0ull;  // before tile 0: an empty prefix
-                if (j >= 0) w = *reinterpret_cast<volatile unsigned long long*>(words + j);
-                const unsigned long long flag = w & ~kTileValue;
-                const unsigned not_ready = __ballot_sync(0xFFFFFFFFu, flag == 0ull);
-                const unsigned prefix = __ballot_sync(0xFFFFFFFFu, flag == kTilePrefix);
-                const int nearest = prefix ? __ffs(prefix) - 1 : 32;  // lowest lane: the nearest tile
-                const unsigned needed = nearest >= 31 ? 0xFFFFFFFFu : (2u << nearest) - 1u;
-                if (not_ready & needed) {
-                    if (++spins > kSpinLimit) {
-                        ok = 0;
-                        break;
-                    }
-                    continue;
-                }
-                int64_t v = (lane <= nearest && j >= 0) ? static_cast<int64_t>(w & kTileValue) : 0;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
-                excl += v;
-                if (nearest < 32) break;
-                hi -= 32;
-            }
-            if (lane == 0) {
-                if (ok)
-                    atomicExch(words + tile, kTilePrefix | static_cast<unsigned long long>(excl + total));
-                else
-                    set_status(a.status, GCP_ERR_TIMEOUT);
-            }
-        }
-        if (lane == 0) {
+        const bool ok = tile_lookback(a.tile_status, tile, total, excl);
+        if (threadIdx.x == 0) {
+            if (!ok) set_status(a.status, GCP_ERR_TIMEOUT);
             s_excl = excl;
-            s_ok = ok;
+            s_ok = ok ? 1 : 0;
         }
     }
     __syncthreads();
