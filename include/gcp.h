@@ -600,6 +600,10 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    learn the count accepted before their tile by decoupled look-back (bounded
    waits, GCP_ERR_TIMEOUT) and walk the kept ones as draws, with no list
    written; 1 runs the separate ordered pass that lists the zeros first.
+   warp_combine (group walk, 3 or 4 modes): modes of at most this many rows
+   sum the updates that the groups of one warp step make to the same 16
+   bytes of G_k (a match on the row and column chunk, then shuffles) before
+   one lane issues the L2 reduction (0 = off).
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -614,6 +618,7 @@ typedef struct gcp_tuning {
     int32_t prefetch;
     int32_t early_draws;
     int32_t zero_pass;
+    int32_t warp_combine;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */
@@ -629,6 +634,7 @@ typedef struct gcp_launch_info {
     int32_t prefetch;
     int32_t early_draws;
     int32_t zero_tiles;  /* 1: stratified zeros are made inside the gradient launch */
+    uint32_t combine_mode_mask;  /* bit k: mode k's updates are combined within a warp step */
 } gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch

@@ -3,8 +3,9 @@
 For one handle, factor layout and sampling spec, times ``gcp_grad`` for a set
 of candidate shapes -- lanes per draw x float4 chunks per lane (rows per
 warp), threads per block, replica slabs per mode (the pre-reduction width of
-the L2 accumulation), the draw layout (group walk, prefetch or staged
-walk) and optional shared-memory accumulation -- with CUDA
+the L2 accumulation), warp-level pre-reduction of same-address updates, the
+draw layout (group walk, prefetch or staged walk) and optional
+shared-memory accumulation -- with CUDA
 events around back-to-back launches, and keeps the fastest through
 ``gcp_set_tuning``.  A shape changes only the summation order of the
 gradient, never the draws.
@@ -19,6 +20,11 @@ import torch
 from . import gcp
 
 COMPILED = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (16, 1), (32, 1), (32, 2)]
+
+
+# modes of at most this many rows get the warp-level pre-reduction in the
+# candidates that try it (short modes, where a warp step's draws share rows)
+COMBINE_ROWS = 4096
 
 
 def candidate_shapes(rank: int) -> list:
@@ -36,9 +42,9 @@ def candidate_shapes(rank: int) -> list:
 def candidates(rank: int) -> list:
     out = []
     for L, NC in candidate_shapes(rank):
-        layouts = [dict(group_draws=0)]
+        layouts = [dict(group_draws=0), dict(group_draws=0, warp_combine=COMBINE_ROWS)]
         if L > 1:
-            layouts.append(dict(group_draws=1))
+            layouts += [dict(group_draws=1), dict(group_draws=1, warp_combine=COMBINE_ROWS)]
         if NC == 1 and L in (2, 4):
             layouts.append(dict(prefetch=1))
         if NC == 1 and L <= 8:

@@ -21,8 +21,8 @@ static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
 static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
-static_assert(sizeof(gcp_tuning) == 48, "gcp_tuning layout");
-static_assert(sizeof(gcp_launch_info) == 72, "gcp_launch_info layout");
+static_assert(sizeof(gcp_tuning) == 52, "gcp_tuning layout");
+static_assert(sizeof(gcp_launch_info) == 76, "gcp_launch_info layout");
 
 struct gcp_handle {
     gcp_tensor X{};
@@ -55,7 +55,7 @@ struct gcp_handle {
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
     int partials_cap = 0;
-    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0};
+    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0};
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
@@ -321,6 +321,7 @@ struct Shape {
     int D = 3, L = 1, NC = 1, block = 256, grid = 1;
     size_t smem = 0;
     uint32_t mask = 0;
+    uint32_t comb = 0;  // modes whose updates are combined within a warp step
     uint32_t off[GCP_MAX_MODES] = {};
     uint32_t reps[GCP_MAX_MODES] = {};
     int64_t rep_floats = 0;  // replica workspace the shape needs
@@ -421,6 +422,13 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
         }
     }
     sh->smem = static_cast<size_t>(used);
+    // warp-level pre-reduction (the group walk's variant, 3 or 4 modes)
+    sh->comb = 0;
+    if (t.warp_combine > 0 && sh->pf == 0 && grad_has_config(sh->D, sh->L, sh->NC, 4) && h->X.d == sh->D)
+        for (int k = 0; k < d; ++k)
+            if (!((sh->mask >> k) & 1u) && h->X.dims[k] <= t.warp_combine &&
+                h->X.dims[k] * (F->ld / 4) < (int64_t(1) << 31))
+                sh->comb |= 1u << k;
     if (sh->pf == 1 && sh->smem > 0) sh->pf = 0;  // the prefetch layout accumulates through L2 only
     if (sh->pf == 2)  // the staged walk: each warp stages L draws x d rows x 32 lanes of 16 (BF16: 8) bytes
         sh->smem = static_cast<size_t>(sh->block / 32) * sh->L * sh->D * 32 * (F->bf16 ? 8 : 16);
@@ -453,7 +461,7 @@ gcp_status choose_shape(const gcp_handle* h, const gcp_factors* F, int64_t n_tot
 bool zero_tiles_apply(const gcp_handle* h, const Shape& sh)
 {
     return h->tune.zero_pass == 0 && sh.layout() == 0 && h->X.d == sh.D &&
-           grad_has_config(sh.D, sh.L, sh.NC, 3);
+           grad_has_config(sh.D, sh.L, sh.NC, sh.comb ? 5 : 3);
 }
 
 ModeTable mode_table(const gcp_factors* F, int32_t d, const int64_t* dims)
@@ -688,7 +696,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     if (!t) {
-        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0};
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0};
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, 0)) return GCP_ERR_INVALID_ARG;
@@ -696,7 +704,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
         t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1 || t->zero_pass < 0 ||
-        t->zero_pass > 1)
+        t->zero_pass > 1 || t->warp_combine < 0)
         return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
@@ -721,6 +729,7 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     out->prefetch = sh.pf;
     out->early_draws = sh.early;
     out->zero_tiles = zero_tiles_apply(h, sh) ? 1 : 0;
+    out->combine_mode_mask = sh.comb;
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
@@ -824,7 +833,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     Shape sh;
     st = choose_shape(h, F, n_draws, &sh);
     if (st != GCP_OK) return st;
-    int layout = sh.layout();
+    int layout = (sh.layout() == 0 && sh.comb) ? 4 : sh.layout();
     int grid = sh.grid;
     if (S && (S->kind == GCP_SAMPLER_STRATIFIED || S->kind == GCP_SAMPLER_OBSERVED) && S->q > 0) {
         // the zero draws of this launch: ranks [z_begin, z_end) of the kept candidates
@@ -857,7 +866,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
             const int64_t per_warp = sh.group ? 32 / sh.L : 32;
             const int64_t blocks_nz = (((nz + per_warp - 1) / per_warp) + sh.block / 32 - 1) / (sh.block / 32);
             grid = static_cast<int>(tiles + std::min<int64_t>(sh.grid, blocks_nz));
-            layout = 3;
+            layout = sh.comb ? 5 : 3;
         } else {
             st = ensure_zero_list(h, S->q);
             if (st != GCP_OK) return st;
@@ -882,6 +891,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     a.loss = loss;
     a.smem_floats = sh.pf == 2 ? 0 : static_cast<int32_t>(sh.smem / 4);  // accumulators to zero (not the stage)
     a.smem_mask = sh.mask;
+    a.comb_mask = sh.comb;
     a.group_draws = sh.group;
     a.early = (sh.early && early_ok) ? 1 : 0;
     a.stream_pred = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(h->d_status) + 8);
@@ -948,6 +958,7 @@ static gcp_status grad_from_args(gcp_handle* h, const gcp_factors* F, gcp_loss l
     a.loss = loss;
     a.smem_floats = 0;
     a.smem_mask = 0;
+    a.comb_mask = 0;
     a.group_draws = sh.group;
     a.early = 0;
     a.stream_pred = nullptr;

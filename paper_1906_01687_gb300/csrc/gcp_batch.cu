@@ -181,8 +181,7 @@ __device__ __forceinline__ void batch_grad_item(const BatchArgs& a, const int64_
 #pragma unroll
             for (int k = 0; k < kBatchMaxD; ++k) {
                 if (k >= d) continue;
-                atomicAdd(reinterpret_cast<float4*>(dst[k] + static_cast<size_t>(jx[k]) * ld + col),
-                          mul4(pre[k], suf[k]));
+                red_add4(dst[k] + static_cast<size_t>(jx[k]) * ld + col, mul4(pre[k], suf[k]));
             }
         }
     }

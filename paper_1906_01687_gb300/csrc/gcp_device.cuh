@@ -187,6 +187,14 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16* __restrict__ p)
     return out;
 }
 
+// G_k(i, cols) += v: one 16-byte reduction performed at L2 (red, no value
+// returned to the thread; relaxed, GPU scope).  Needs a 16-byte aligned address.
+__device__ __forceinline__ void red_add4(float* p, const float4 v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 // Asynchronous global -> shared copies (cp.async): a thread's own copies are
 // complete and visible to it after cp_async_wait_all().
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)

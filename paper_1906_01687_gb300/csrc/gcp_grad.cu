@@ -9,13 +9,21 @@ const void* grad_kernel_ptr_d4(int L, int NC, bool bf16, int layout);
 const void* grad_kernel_ptr_d8(int L, int NC, bool bf16, int layout);
 const void* grad_kernel_ptr_d3z(int L, int NC, bool bf16);
 const void* grad_kernel_ptr_d4z(int L, int NC, bool bf16);
+const void* grad_kernel_ptr_d3c(int L, int NC, bool bf16);
+const void* grad_kernel_ptr_d4c(int L, int NC, bool bf16);
+const void* grad_kernel_ptr_d3zc(int L, int NC, bool bf16);
+const void* grad_kernel_ptr_d4zc(int L, int NC, bool bf16);
 
 static const void* grad_ptr(int D, int L, int NC, bool bf16, int layout)
 {
-    if (layout == 3) {  // the zeros made in the launch: 3 or 4 modes
-        if (D == 3) return grad_kernel_ptr_d3z(L, NC, bf16);
-        if (D == 4) return grad_kernel_ptr_d4z(L, NC, bf16);
-        return nullptr;
+    if (layout >= 3) {  // the group-walk variants (3 or 4 modes)
+        if (D != 3 && D != 4) return nullptr;
+        switch (layout) {
+        case 3: return D == 3 ? grad_kernel_ptr_d3z(L, NC, bf16) : grad_kernel_ptr_d4z(L, NC, bf16);
+        case 4: return D == 3 ? grad_kernel_ptr_d3c(L, NC, bf16) : grad_kernel_ptr_d4c(L, NC, bf16);
+        case 5: return D == 3 ? grad_kernel_ptr_d3zc(L, NC, bf16) : grad_kernel_ptr_d4zc(L, NC, bf16);
+        default: return nullptr;
+        }
     }
     switch (D) {
     case 3: return grad_kernel_ptr_d3(L, NC, bf16, layout);

@@ -42,7 +42,7 @@ namespace gcpk {
 // shuffles, then y_i and the d row updates follow.  verify: the batch was
 // drawn from a predicted stream word, checked against `actual` before the
 // first update; on a miss the batch is redrawn (jfirst: this lane's draw).
-template <int D, int L, int NC, bool BF16>
+template <int D, int L, int NC, bool BF16, bool COMB>
 __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float* (&gdst)[D], float* sG, int steps,
                                            bool group, bool& verify, uint64_t& stream, uint64_t actual,
                                            int64_t jfirst)
@@ -169,8 +169,28 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
                     atomicAdd(s + 1, upd[k].y);
                     atomicAdd(s + 2, upd[k].z);
                     atomicAdd(s + 3, upd[k].w);
+                } else if (COMB && ((a.comb_mask >> k) & 1u)) {
+                    // warp-level pre-reduction: the lanes of this step that update
+                    // the same 16 bytes of G_k (groups whose draws share row i_k)
+                    // sum their updates and the lowest of them issues one reduction
+                    const unsigned act = __activemask();
+                    const unsigned key = ix[k] * static_cast<unsigned>(ld >> 2) + static_cast<unsigned>(col >> 2);
+                    const unsigned same = __match_any_sync(act, key);
+                    float4 sum = upd[k];
+                    unsigned rest = same & ~(1u << lane);
+                    const int rounds = static_cast<int>(__reduce_max_sync(act, static_cast<unsigned>(__popc(rest))));
+                    for (int i = 0; i < rounds; ++i) {
+                        const int src = rest ? __ffs(rest) - 1 : lane;
+                        const float4 v = make_float4(__shfl_sync(act, upd[k].x, src), __shfl_sync(act, upd[k].y, src),
+                                                     __shfl_sync(act, upd[k].z, src), __shfl_sync(act, upd[k].w, src));
+                        if (rest) {
+                            sum = add4(sum, v);
+                            rest &= rest - 1u;
+                        }
+                    }
+                    if (lane == __ffs(same) - 1) red_add4(gdst[k] + static_cast<size_t>(ix[k]) * ld + col, sum);
                 } else {
-                    atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd[k]);
+                    red_add4(gdst[k] + static_cast<size_t>(ix[k]) * ld + col, upd[k]);
                 }
             }
         }
@@ -213,7 +233,7 @@ __device__ __forceinline__ bool zt_candidate(const GradArgs& a, uint64_t stream,
 // block of the last tile continues in candidate order up to the cap while
 // fewer than q were accepted, and reports a shortfall.  The last tile to
 // finish clears the tile words and counters for the next launch.
-template <int D, int L, int NC, bool BF16>
+template <int D, int L, int NC, bool BF16, bool COMB>
 __device__ __forceinline__ void zero_tiles_block(const GradArgs& a, float* (&gdst)[D], float* sG, uint64_t stream)
 {
     __shared__ int zt_warp[32];
@@ -249,7 +269,7 @@ __device__ __forceinline__ void zero_tiles_block(const GradArgs& a, float* (&gds
 #pragma unroll 1
     for (int64_t c0 = z.tiles * B;; c0 += B) {
         my.valid = ok && nacc && count + nrank >= z.z_begin && count + nrank < z.z_end;
-        walk_batch<D, L, NC, BF16>(a, my, gdst, sG, L, false, verify, st, stream, 0);
+        walk_batch<D, L, NC, BF16, COMB>(a, my, gdst, sG, L, false, verify, st, stream, 0);
         if (tile != z.tiles - 1) break;
         count = ok ? count + ntot : 0;
         if (!(ok && count < z.q && c0 < z.cap)) {
@@ -279,7 +299,9 @@ __device__ __forceinline__ void zero_tiles_block(const GradArgs& a, float* (&gds
 }
 
 // LAYOUT 0: the group walk; 1: the prefetch layout; 2: the staged walk; 3: the
-// group walk with the stratified zeros made in the launch (zero_tiles_block).
+// group walk with the stratified zeros made in the launch (zero_tiles_block);
+// 4: the group walk with warp-level pre-reduction of same-address updates
+// (GradArgs::comb_mask); 5: both 3 and 4.
 // Blocks of 256 per SM the registers must allow: four (64 registers) for the
 // group walk with one chunk per lane and 2 or more lanes, which fits without
 // spilling; three for the other group and staged walks of at most 4 modes;
@@ -287,7 +309,7 @@ __device__ __forceinline__ void zero_tiles_block(const GradArgs& a, float* (&gds
 template <int D, int L, int NC>
 constexpr int grad_min_blocks(int layout)
 {
-    return (D <= 4 && (layout == 0 || layout == 3) && NC == 1 && L >= 2) ? 4 : ((D <= 4 && layout != 1) ? 3 : 2);
+    return (D <= 4 && layout != 1 && layout != 2 && NC == 1 && L >= 2) ? 4 : ((D <= 4 && layout != 1) ? 3 : 2);
 }
 
 template <int D, int L, int NC, bool BF16, int LAYOUT>
@@ -295,7 +317,8 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
 {
     constexpr bool PF = LAYOUT == 1;
     constexpr bool STAGED = LAYOUT == 2;
-    constexpr bool ZT = LAYOUT == 3;
+    constexpr bool ZT = LAYOUT == 3 || LAYOUT == 5;
+    constexpr bool COMB = LAYOUT == 4 || LAYOUT == 5;
     using T = std::conditional_t<BF16, __nv_bfloat16, float>;
     extern __shared__ float4 smem4[];
     float* sG = reinterpret_cast<float*>(smem4);
@@ -374,7 +397,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
         gdst[k] = k < d ? a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k] : nullptr;
 
     if constexpr (ZT) {
-        if (zblock) zero_tiles_block<D, L, NC, BF16>(a, gdst, sG, stream);
+        if (zblock) zero_tiles_block<D, L, NC, BF16, COMB>(a, gdst, sG, stream);
     }
     // warp-uniform loop over this warp's batches (none in a zero-tile block)
     for (int64_t wb = zblock ? a.dr.n_total : wb0; wb < a.dr.n_total; wb += nwarps * per_warp) {
@@ -443,7 +466,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
                 }
 #pragma unroll
                 for (int k = 0; k < D; ++k)
-                    atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(ix[k]) * ld + col), upd[k]);
+                    red_add4(gdst[k] + static_cast<size_t>(ix[k]) * ld + col, upd[k]);
             }
             continue;
         }
@@ -497,11 +520,11 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
                 }
 #pragma unroll
                 for (int k = 0; k < D; ++k)
-                    atomicAdd(reinterpret_cast<float4*>(gdst[k] + static_cast<size_t>(pix[b][k]) * ld + col), upd[k]);
+                    red_add4(gdst[k] + static_cast<size_t>(pix[b][k]) * ld + col, upd[k]);
             }
             continue;
         }
-        walk_batch<D, L, NC, BF16>(a, my, gdst, sG, steps, a.group_draws != 0, verify, stream, actual, wb + sub);
+        walk_batch<D, L, NC, BF16, COMB>(a, my, gdst, sG, steps, a.group_draws != 0, verify, stream, actual, wb + sub);
     }
 
     // the prediction for the next launch that reads its stream word from memory
@@ -517,7 +540,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
         float4* g = reinterpret_cast<float4*>(a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k]);
         for (int e = threadIdx.x; e < n4; e += blockDim.x) {
             const float4 v = s[e];
-            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(g + e, v);
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) red_add4(reinterpret_cast<float*>(g + e), v);
         }
     }
 }
@@ -553,14 +576,14 @@ const void* grad_kernel_ptr(int L, int NC, int layout)
     return nullptr;
 }
 
-// The group walk with the zeros made in the launch (layout 3), at most 4
-// modes: instantiated in translation units of their own.
-template <int D, bool BF16>
-const void* grad_kernel_ptr_zt(int L, int NC)
+// The group-walk variants of layouts 3, 4 and 5 (LAYOUT), at most 4 modes:
+// instantiated in translation units of their own.
+template <int D, bool BF16, int LAYOUT>
+const void* grad_kernel_ptr_variant(int L, int NC)
 {
-    static_assert(D <= 4, "layout 3: at most 4 modes");
+    static_assert(D <= 4 && LAYOUT >= 3 && LAYOUT <= 5, "layouts 3-5: at most 4 modes");
 #define GCP_CASE(LL, CC) \
-    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, 3>);
+    if (L == LL && NC == CC) return reinterpret_cast<const void*>(&grad_kernel<D, LL, CC, BF16, LAYOUT>);
     GCP_GRAD_CONFIGS(GCP_CASE)
 #undef GCP_CASE
     return nullptr;

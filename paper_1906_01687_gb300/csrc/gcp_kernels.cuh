@@ -79,6 +79,7 @@ struct GradArgs {
     uint32_t reps[GCP_MAX_MODES];  // replicas of mode k's destination (CTA b adds into replica b % reps)
     uint64_t rep_stride[GCP_MAX_MODES];  // floats between replicas
     uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
+    uint32_t comb_mask;            // bit k: same-address updates of a warp step are summed before the reduction
     uint32_t smem_off[GCP_MAX_MODES];
     int32_t group_draws;           // 1: each group of L lanes takes its own draw (32/L draws per warp step)
     int32_t early;                 // 1: each warp's first descriptors are made before the dependency wait
@@ -208,7 +209,8 @@ inline cudaError_t launch_pdl_ptr(const void* kernel, dim3 grid, dim3 block, siz
 
 // Launchers (defined in the kernel translation units).
 // layout: 0 the group walk, 1 the prefetch layout, 2 the staged walk, 3 the group walk with
-// the stratified zeros made in the launch (ZeroTileArgs)
+// the stratified zeros made in the launch (ZeroTileArgs), 4 the group walk with warp-level
+// pre-reduction (comb_mask), 5 both
 cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int layout, int grid, int block,
                         size_t smem, cudaStream_t s);
 cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int layout, int block, size_t smem, int* blocks_per_sm);

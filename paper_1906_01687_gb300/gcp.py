@@ -76,14 +76,15 @@ class gcp_tuning(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_min_hits", ctypes.c_int32),
                 ("max_replicas", ctypes.c_int32), ("replica_target", ctypes.c_int32),
                 ("group_draws", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("early_draws", ctypes.c_int32),
-                ("zero_pass", ctypes.c_int32)]
+                ("zero_pass", ctypes.c_int32), ("warp_combine", ctypes.c_int32)]
 
 
 class gcp_launch_info(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("chunks", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_mode_mask", ctypes.c_uint32),
                 ("replicas", ctypes.c_int32 * MAX_MODES), ("group_draws", ctypes.c_int32),
-                ("prefetch", ctypes.c_int32), ("early_draws", ctypes.c_int32), ("zero_tiles", ctypes.c_int32)]
+                ("prefetch", ctypes.c_int32), ("early_draws", ctypes.c_int32), ("zero_tiles", ctypes.c_int32),
+                ("combine_mode_mask", ctypes.c_uint32)]
 
 
 class gcp_batch_problem(ctypes.Structure):
@@ -364,9 +365,10 @@ def gcp_get_device_status(h: Handle) -> int:
 
 
 TUNING_FIELDS = ("lanes", "chunks", "block", "grid_blocks", "smem_bytes", "smem_min_hits", "max_replicas",
-                 "replica_target", "group_draws", "prefetch", "early_draws", "zero_pass")
+                 "replica_target", "group_draws", "prefetch", "early_draws", "zero_pass", "warp_combine")
 TUNING_DEFAULT = dict(lanes=0, chunks=0, block=0, grid_blocks=0, smem_bytes=-1, smem_min_hits=-1,
-                      max_replicas=-1, replica_target=0, group_draws=0, prefetch=0, early_draws=0, zero_pass=0)
+                      max_replicas=-1, replica_target=0, group_draws=0, prefetch=0, early_draws=0, zero_pass=0,
+                      warp_combine=0)
 
 
 def gcp_set_tuning(h: Handle, reset: bool = False, **kw):
@@ -388,7 +390,8 @@ def gcp_get_launch(h: Handle, F: Factors, n_draws: int) -> dict:
     _check(_lib.gcp_get_launch(h.ptr, ctypes.byref(F._c()), int(n_draws), ctypes.byref(t)), "gcp_get_launch")
     return dict(lanes=t.lanes, chunks=t.chunks, block=t.block, grid_blocks=t.grid_blocks,
                 smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_mode_mask, replicas=list(t.replicas)[: h.d],
-                group_draws=t.group_draws, prefetch=t.prefetch, early_draws=t.early_draws, zero_tiles=t.zero_tiles)
+                group_draws=t.group_draws, prefetch=t.prefetch, early_draws=t.early_draws, zero_tiles=t.zero_tiles,
+                combine_mode_mask=t.combine_mode_mask)
 
 
 def gcp_profile(h: Handle, enable: bool, capacity: int = 1024):
