@@ -660,6 +660,14 @@ gcp_status gcp_profile_read(gcp_handle *h, int32_t which, double *total_ms, int6
 /* A static string naming a status code. */
 const char *gcp_status_string(gcp_status s);
 
+/* The CUDA runtime error behind the calling thread's most recent
+   GCP_ERR_CUDA or GCP_ERR_NO_MEMORY from any entry point: its numeric code
+   (a cudaError_t; 0 when no call of this thread has failed on a CUDA error)
+   and the runtime's name for it (a static string).  For diagnostics; the
+   status codes stay the interface. */
+int32_t gcp_last_cuda_error(void);
+const char *gcp_last_cuda_error_name(void);
+
 /* Library version string. */
 const char *gcp_version(void);
 

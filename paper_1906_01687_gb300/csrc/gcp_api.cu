@@ -31,7 +31,8 @@ struct gcp_handle {
     double omega = 0.0;
     int rec_int4 = 0;
     int4* recs = nullptr;
-    int32_t* d_status = nullptr;     // 16 bytes: the status word, then the predicted stream (int64)
+    int32_t* d_status = nullptr;     // 32 bytes: the status word, the predicted stream (int64) at 8, the fold
+                                     // tail's block counter (uint32) at 16
     cudaStream_t last_stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -74,9 +75,16 @@ constexpr int kLossMaxBlocks = 2048;
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// the CUDA error behind this thread's most recent CUDA-caused status
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 gcp_status cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return GCP_OK;
+    g_last_cuda_error = e;
+    // clear the runtime's per-thread error state (a failed launch's error is
+    // not sticky), so that the caller's next CUDA call does not report it again
+    (void)cudaGetLastError();
     if (e == cudaErrorMemoryAllocation) return GCP_ERR_NO_MEMORY;
     return GCP_ERR_CUDA;
 }
@@ -514,6 +522,10 @@ extern "C" {
 
 const char* gcp_version(void) { return "gcp_gb300 0.1 (sm_103a)"; }
 
+int32_t gcp_last_cuda_error(void) { return static_cast<int32_t>(g_last_cuda_error); }
+
+const char* gcp_last_cuda_error_name(void) { return cudaGetErrorName(g_last_cuda_error); }
+
 const char* gcp_status_string(gcp_status s)
 {
     switch (s) {
@@ -584,13 +596,13 @@ gcp_status gcp_create(gcp_handle** out, const gcp_tensor* X, gcp_stream_t stream
     if (e != cudaSuccess) return fail(cuda_status(e));
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (h->num_sms < 1) h->num_sms = 1;
-    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), 16)) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), 32)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMalloc(reinterpret_cast<void**>(&h->zcount), sizeof(int64_t))) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMalloc(reinterpret_cast<void**>(&h->partials), kLossMaxBlocks * sizeof(double))) != cudaSuccess)
         return fail(cuda_status(e));
     if ((e = cudaMalloc(reinterpret_cast<void**>(&h->ticket), sizeof(unsigned int))) != cudaSuccess) return fail(cuda_status(e));
     h->partials_cap = kLossMaxBlocks;
-    if ((e = cudaMemsetAsync(h->d_status, 0, 16, s)) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMemsetAsync(h->d_status, 0, 32, s)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMemsetAsync(h->zcount, 0, sizeof(int64_t), s)) != cudaSuccess) return fail(cuda_status(e));
     if ((e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return fail(cuda_status(e));
     if (X->sparse) {
@@ -929,6 +941,13 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
             a.rep_stride[k] = 0;
         }
     }
+    // a small fold (at most kTailFold4 float4 elements of replicated modes) is done
+    // by the gradient kernel's last block instead of a launch of its own
+    constexpr int64_t kTailFold4 = 2048;
+    if (!deferred_fold && fold.nmodes > 0 && fold.off4[fold.nmodes] <= kTailFold4) {
+        a.tail = fold;
+        a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
+    }
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));
     GCP_CUDA_TRY(launch_grad(a, sh.D, sh.L, sh.NC, F->bf16 != 0, layout, grid, sh.block, sh.smem, s));
@@ -938,7 +957,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
         GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s));
         h->prof_used++;
     }
-    if (!deferred_fold && fold.nmodes > 0) {
+    if (!deferred_fold && fold.nmodes > 0 && a.tail.nmodes == 0) {
         const int64_t total4 = fold.off4[fold.nmodes];
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total4 + 255) / 256, int64_t(h->num_sms) * 8)));
         GCP_CUDA_TRY(launch_fold(fold, grid, s));

@@ -39,7 +39,9 @@ cudaError_t grad_occupancy(int D, int L, int NC, bool bf16, int layout, int bloc
 {
     const void* f = grad_ptr(D, L, NC, bf16, layout);
     if (!f) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
+    // the default dynamic allowance is 48 KB less the kernel's static shared
+    // memory, so any sizeable request raises it explicitly
+    if (smem >= 16 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
@@ -51,7 +53,9 @@ cudaError_t launch_grad(const GradArgs& a, int D, int L, int NC, bool bf16, int 
 {
     const void* f = grad_ptr(D, L, NC, bf16, layout);
     if (!f) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
+    // the default dynamic allowance is 48 KB less the kernel's static shared
+    // memory, so any sizeable request raises it explicitly
+    if (smem >= 16 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }

@@ -197,6 +197,51 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
     }
 }
 
+// gcp_grad with replica slabs and a small fold: the last block to finish sums
+// the slabs into the caller's G_k (G_k += R_k[0] + R_k[1] + ..., the order of
+// the separate fold kernel) and zeroes them, instead of a fold launch.  Every
+// thread fences its own reductions before its block counts itself done; the
+// last block reads through L2 (ld.cg).
+__device__ __forceinline__ void fold_tail(const GradArgs& a)
+{
+    __shared__ int tail_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) tail_last = atomicAdd(a.tail_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!tail_last) return;
+    __threadfence();
+    const FoldArgs& f = a.tail;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < GCP_MAX_MODES; ++m) {  // constant indices into the launch parameters
+        if (m >= f.nmodes) break;
+        const int64_t n4 = f.off4[m + 1] - f.off4[m];
+        const uint32_t reps = f.reps[m];
+        const uint64_t stride = f.rep_stride4[m];
+#pragma unroll 1
+        for (int64_t loc = threadIdx.x; loc < n4; loc += blockDim.x) {
+            float4* g = reinterpret_cast<float4*>(f.G[m]) + loc;
+            float4* r = reinterpret_cast<float4*>(f.R[m]) + loc;
+            constexpr int kWide = 4;
+            float4 acc = zero;
+#pragma unroll 1
+            for (uint32_t q0 = 0; q0 < reps; q0 += kWide) {
+                float4 v[kWide];
+#pragma unroll
+                for (int q = 0; q < kWide; ++q) v[q] = q0 + q < reps ? __ldcg(r + (q0 + q) * stride) : zero;
+#pragma unroll
+                for (int q = 0; q < kWide; ++q) {
+                    acc = add4(acc, v[q]);
+                    if (q0 + q < reps) r[(q0 + q) * stride] = zero;
+                }
+            }
+            *g = add4(__ldcg(g), acc);
+        }
+    }
+    if (threadIdx.x == 0) *a.tail_done = 0u;
+}
+
 // Candidate c of the zero stream (Alg. 2), or of the observed-entry stream
 // (Section 4.4), as a draw descriptor; returns whether it is accepted: c is
 // below the cap and its linear key is not a nonzero's (observed: its weight
@@ -530,19 +575,22 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     // the prediction for the next launch that reads its stream word from memory
     if (a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
         *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
-    if (a.smem_mask == 0) return;
-    __syncthreads();
+    if (a.smem_mask != 0) {
+        __syncthreads();
 #pragma unroll 1
-    for (int k = 0; k < d; ++k) {
-        if (!((a.smem_mask >> k) & 1u)) continue;
-        const int n4 = static_cast<int>(a.dr.dims[k]) * ld / 4;
-        const float4* s = reinterpret_cast<const float4*>(sG + a.smem_off[k]);
-        float4* g = reinterpret_cast<float4*>(a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k]);
-        for (int e = threadIdx.x; e < n4; e += blockDim.x) {
-            const float4 v = s[e];
-            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) red_add4(reinterpret_cast<float*>(g + e), v);
+        for (int k = 0; k < d; ++k) {
+            if (!((a.smem_mask >> k) & 1u)) continue;
+            const int n4 = static_cast<int>(a.dr.dims[k]) * ld / 4;
+            const float4* s = reinterpret_cast<const float4*>(sG + a.smem_off[k]);
+            float4* g =
+                reinterpret_cast<float4*>(a.G[k] + static_cast<size_t>(blockIdx.x % a.reps[k]) * a.rep_stride[k]);
+            for (int e = threadIdx.x; e < n4; e += blockDim.x) {
+                const float4 v = s[e];
+                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) red_add4(reinterpret_cast<float*>(g + e), v);
+            }
         }
     }
+    if (a.tail.nmodes > 0) fold_tail(a);
 }
 
 #define GCP_GRAD_CONFIGS(X) \

@@ -71,6 +71,17 @@ struct ZeroTileArgs {
     int32_t* status;
 };
 
+// Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).
+struct FoldArgs {
+    int32_t nmodes;
+    int32_t pad;
+    int64_t off4[GCP_MAX_MODES + 1];  // prefix of the folded modes' float4 counts
+    uint32_t reps[GCP_MAX_MODES];
+    uint64_t rep_stride4[GCP_MAX_MODES];
+    float* R[GCP_MAX_MODES];
+    float* G[GCP_MAX_MODES];
+};
+
 struct GradArgs {
     DrawArgs dr;
     int32_t ld, rank, loss, smem_floats;
@@ -86,17 +97,8 @@ struct GradArgs {
     int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
     gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
     ZeroTileArgs zt;               // layout 3: the zeros made in this launch (dr.n_total then ends the nonzeros)
-};
-
-// Folds replica slabs into G: G_k += sum_r R_k[r]; R_k[r] = 0 (fixed order r = 0, 1, ...).
-struct FoldArgs {
-    int32_t nmodes;
-    int32_t pad;
-    int64_t off4[GCP_MAX_MODES + 1];  // prefix of the folded modes' float4 counts
-    uint32_t reps[GCP_MAX_MODES];
-    uint64_t rep_stride4[GCP_MAX_MODES];
-    float* R[GCP_MAX_MODES];
-    float* G[GCP_MAX_MODES];
+    FoldArgs tail;                 // nmodes > 0: the last block to finish folds these replica slabs into G
+    unsigned int* tail_done;       //   blocks finished (zero between launches)
 };
 
 struct LossArgs {

@@ -99,6 +99,8 @@ _P = ctypes.POINTER
 _SIGS = {
     "gcp_version": ([], ctypes.c_char_p),
     "gcp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "gcp_last_cuda_error": ([], ctypes.c_int32),
+    "gcp_last_cuda_error_name": ([], ctypes.c_char_p),
     "gcp_sample_count": ([_P(gcp_sampling)], _i64),
     "gcp_create": ([_P(_vp), _P(gcp_tensor), _vp], ctypes.c_int),
     "gcp_destroy": ([_vp], ctypes.c_int),
@@ -148,7 +150,10 @@ EXPORTED = tuple(_SIGS)
 
 class GcpError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {_lib.gcp_status_string(status).decode()} (status {status})")
+        msg = f"{where}: {_lib.gcp_status_string(status).decode()} (status {status})"
+        if status in (ERR_CUDA, ERR_NO_MEMORY):
+            msg += f" [{_lib.gcp_last_cuda_error_name().decode()}]"
+        super().__init__(msg)
         self.status = status
 
 

@@ -245,7 +245,8 @@ def test_binding_signatures_follow_the_header(lib_path):
                    "uint64_t": ctypes.c_uint64}
         return {scalars[base]}
 
-    ret = {"gcp_status": {ctypes.c_int}, "int64_t": {ctypes.c_int64}, "char*": {ctypes.c_char_p}}
+    ret = {"gcp_status": {ctypes.c_int}, "int64_t": {ctypes.c_int64}, "int32_t": {ctypes.c_int32},
+           "char*": {ctypes.c_char_p}}
     for name, params in protos.items():
         args, res = gcp._SIGS[name]
         assert res in ret[RETURNS[name]], f"{name} returns {RETURNS[name]}, bound as {res}"
