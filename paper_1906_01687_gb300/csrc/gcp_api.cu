@@ -32,7 +32,7 @@ struct gcp_handle {
     int rec_int4 = 0;
     int4* recs = nullptr;
     int32_t* d_status = nullptr;     // 32 bytes: the status word, the predicted stream (int64) at 8, the fold
-                                     // tail's block counter (uint32) at 16
+                                     // tail's two block counters (uint32) at 16 and 20
     cudaStream_t last_stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -941,12 +941,19 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
             a.rep_stride[k] = 0;
         }
     }
-    // a small fold (at most kTailFold4 float4 elements of replicated modes) is done
-    // by the gradient kernel's last block instead of a launch of its own
-    constexpr int64_t kTailFold4 = 2048;
-    if (!deferred_fold && fold.nmodes > 0 && fold.off4[fold.nmodes] <= kTailFold4) {
-        a.tail = fold;
-        a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
+    // the fold is done by the gradient kernel's last blocks to finish (four lanes
+    // per float4 element, at most 64 blocks, at most four elements per lane)
+    // instead of a launch of its own
+    if (!deferred_fold && fold.nmodes > 0) {
+        const int64_t quads_per_block = sh.block / 4;
+        const int64_t passes = (fold.off4[fold.nmodes] + quads_per_block - 1) / quads_per_block;
+        const int64_t blocks = std::max<int64_t>(1, (passes + 3) / 4);
+        if (blocks <= 64 && blocks <= grid) {
+            a.tail = fold;
+            a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
+            a.tail_blocks = static_cast<int32_t>(blocks);
+            a.tail_status = h->d_status;
+        }
     }
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used], s));

@@ -197,49 +197,95 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
     }
 }
 
-// gcp_grad with replica slabs and a small fold: the last block to finish sums
-// the slabs into the caller's G_k (G_k += R_k[0] + R_k[1] + ..., the order of
-// the separate fold kernel) and zeroes them, instead of a fold launch.  Every
-// thread fences its own reductions before its block counts itself done; the
-// last block reads through L2 (ld.cg).
+// gcp_grad with replica slabs: the last a.tail_blocks blocks to finish their
+// draws fold the slabs into the caller's G_k instead of a fold launch.  Every
+// thread fences its own reductions before its block counts itself done; a
+// folding block then waits (bounded: kSpinLimit polls, then GCP_ERR_TIMEOUT
+// and no fold) until every block has counted itself, and reads through L2
+// (ld.cg).  Four lanes share a float4 element of G_k: lane s sums replicas s,
+// s + 4, s + 8, ... in order, the four partial sums are added by two
+// shuffles, and lane 0 adds the total to G_k; the slabs are left zero.  At
+// most 64 blocks wait, fewer than the blocks one wave keeps resident, so the
+// blocks still to run always find room.  The last folding block to finish
+// clears both counters for the next launch.
 __device__ __forceinline__ void fold_tail(const GradArgs& a)
 {
-    __shared__ int tail_last;
+    __shared__ int tail_rank, tail_ok;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) tail_last = atomicAdd(a.tail_done, 1u) == gridDim.x - 1;
+    const unsigned grid = gridDim.x;
+    const unsigned K = static_cast<unsigned>(a.tail_blocks);
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(a.tail_done, 1u);
+        const int rank = static_cast<int>(ticket) - static_cast<int>(grid - K);
+        int ok = 1;
+        if (rank >= 0) {
+            int spins = 0;
+            while (*reinterpret_cast<volatile unsigned int*>(a.tail_done) < grid) {
+                if (++spins > kSpinLimit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        tail_rank = rank;
+        tail_ok = ok;
+    }
     __syncthreads();
-    if (!tail_last) return;
-    __threadfence();
-    const FoldArgs& f = a.tail;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int rank = tail_rank;
+    if (rank < 0) return;
+    if (tail_ok) {
+        __threadfence();
+        const FoldArgs& f = a.tail;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int sub = threadIdx.x & 3;
+        const unsigned quad = 0xFu << (threadIdx.x & 28);
+        const int64_t first = (static_cast<int64_t>(rank) * blockDim.x + threadIdx.x) >> 2;
+        const int64_t step = (static_cast<int64_t>(K) * blockDim.x) >> 2;
 #pragma unroll
-    for (int m = 0; m < GCP_MAX_MODES; ++m) {  // constant indices into the launch parameters
-        if (m >= f.nmodes) break;
-        const int64_t n4 = f.off4[m + 1] - f.off4[m];
-        const uint32_t reps = f.reps[m];
-        const uint64_t stride = f.rep_stride4[m];
+        for (int m = 0; m < GCP_MAX_MODES; ++m) {  // constant indices into the launch parameters
+            if (m >= f.nmodes) break;
+            const int64_t n4 = f.off4[m + 1] - f.off4[m];
+            const uint32_t reps = f.reps[m];
+            const uint64_t stride = f.rep_stride4[m];
 #pragma unroll 1
-        for (int64_t loc = threadIdx.x; loc < n4; loc += blockDim.x) {
-            float4* g = reinterpret_cast<float4*>(f.G[m]) + loc;
-            float4* r = reinterpret_cast<float4*>(f.R[m]) + loc;
-            constexpr int kWide = 4;
-            float4 acc = zero;
+            for (int64_t loc = first; loc < n4; loc += step) {  // the same trip count in all four lanes
+                float4* r = reinterpret_cast<float4*>(f.R[m]) + loc;
+                constexpr int kWide = 4;
+                float4 acc = zero;
 #pragma unroll 1
-            for (uint32_t q0 = 0; q0 < reps; q0 += kWide) {
-                float4 v[kWide];
+                for (uint32_t q0 = sub; q0 < reps; q0 += 4 * kWide) {
+                    float4 v[kWide];
 #pragma unroll
-                for (int q = 0; q < kWide; ++q) v[q] = q0 + q < reps ? __ldcg(r + (q0 + q) * stride) : zero;
+                    for (int j = 0; j < kWide; ++j) v[j] = q0 + 4 * j < reps ? __ldcg(r + (q0 + 4 * j) * stride) : zero;
 #pragma unroll
-                for (int q = 0; q < kWide; ++q) {
-                    acc = add4(acc, v[q]);
-                    if (q0 + q < reps) r[(q0 + q) * stride] = zero;
+                    for (int j = 0; j < kWide; ++j) {
+                        acc = add4(acc, v[j]);
+                        if (q0 + 4 * j < reps) r[(q0 + 4 * j) * stride] = zero;
+                    }
+                }
+#pragma unroll
+                for (int off = 1; off <= 2; off <<= 1)
+                    acc = add4(acc, make_float4(__shfl_xor_sync(quad, acc.x, off), __shfl_xor_sync(quad, acc.y, off),
+                                                __shfl_xor_sync(quad, acc.z, off), __shfl_xor_sync(quad, acc.w, off)));
+                if (sub == 0) {
+                    float4* g = reinterpret_cast<float4*>(f.G[m]) + loc;
+                    *g = add4(__ldcg(g), acc);
                 }
             }
-            *g = add4(__ldcg(g), acc);
+        }
+    } else if (threadIdx.x == 0) {
+        set_status(a.tail_status, GCP_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.tail_done + 1, 1u) == K - 1) {
+            a.tail_done[0] = 0u;
+            a.tail_done[1] = 0u;
         }
     }
-    if (threadIdx.x == 0) *a.tail_done = 0u;
 }
 
 // Candidate c of the zero stream (Alg. 2), or of the observed-entry stream

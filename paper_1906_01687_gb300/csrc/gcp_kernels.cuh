@@ -97,8 +97,10 @@ struct GradArgs {
     int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
     gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
     ZeroTileArgs zt;               // layout 3: the zeros made in this launch (dr.n_total then ends the nonzeros)
-    FoldArgs tail;                 // nmodes > 0: the last block to finish folds these replica slabs into G
-    unsigned int* tail_done;       //   blocks finished (zero between launches)
+    FoldArgs tail;                 // nmodes > 0: the last tail_blocks blocks fold these replica slabs into G
+    unsigned int* tail_done;       //   [0] blocks finished, [1] folding blocks finished (zero between launches)
+    int32_t tail_blocks;           //   1..64
+    int32_t* tail_status;          //   status word (a wait that ran out)
 };
 
 struct LossArgs {
