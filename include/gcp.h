@@ -604,6 +604,11 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    sum the updates that the groups of one warp step make to the same 16
    bytes of G_k (a match on the row and column chunk, then shuffles) before
    one lane issues the L2 reduction (0 = off).
+   adam_launch (gcp_iteration): 0 (automatic) lets the last blocks of the
+   gradient kernel to finish take the Adam step where the factor set is
+   small (at most 64 blocks at four lanes per float4 element; they wait,
+   bounded, for the other blocks, then GCP_ERR_TIMEOUT) instead of a launch
+   of its own; 1 always launches the Adam kernel.
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -619,6 +624,7 @@ typedef struct gcp_tuning {
     int32_t early_draws;
     int32_t zero_pass;
     int32_t warp_combine;
+    int32_t adam_launch;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */

@@ -21,7 +21,7 @@ static_assert(sizeof(gcp_samples) == 96, "gcp_samples layout");
 static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
-static_assert(sizeof(gcp_tuning) == 52, "gcp_tuning layout");
+static_assert(sizeof(gcp_tuning) == 56, "gcp_tuning layout");
 static_assert(sizeof(gcp_launch_info) == 76, "gcp_launch_info layout");
 
 struct gcp_handle {
@@ -56,7 +56,7 @@ struct gcp_handle {
     double* partials = nullptr;
     unsigned int* ticket = nullptr;
     int partials_cap = 0;
-    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0};
+    gcp_tuning tune{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0};
     // replica slabs of the gradient accumulation (kept zero between calls)
     float* rep_ws = nullptr;
     int64_t rep_ws_cap = 0;  // floats
@@ -708,7 +708,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
 {
     if (!h) return GCP_ERR_INVALID_ARG;
     if (!t) {
-        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0};
+        h->tune = gcp_tuning{0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0};
         return GCP_OK;
     }
     if (t->lanes > 0 && !grad_has_config(3, t->lanes, t->chunks > 0 ? t->chunks : 1, 0)) return GCP_ERR_INVALID_ARG;
@@ -716,7 +716,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
         t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1 || t->zero_pass < 0 ||
-        t->zero_pass > 1 || t->warp_combine < 0)
+        t->zero_pass > 1 || t->warp_combine < 0 || t->adam_launch < 0 || t->adam_launch > 1)
         return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
@@ -804,11 +804,16 @@ gcp_status gcp_reserve(gcp_handle* h, const gcp_sampling* S, gcp_stream_t stream
 // advance_t (gcp_iteration): the gradient kernel advances advance_t->t for the
 // Adam step that follows; *launched reports whether a gradient kernel ran.
 // first / count (count >= 0): only the draws j in [first, first + count) of the spec.
+// adam (gcp_iteration, with deferred_fold and advance_t): the step that follows;
+// where the factor set is small the gradient kernel's last blocks take it
+// (*adam_fused = true) and no Adam launch is needed.
 static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, const gcp_sampling* S,
                             const gcp_samples* list, const int64_t* stream_dev, float* const G[GCP_MAX_MODES],
                             cudaStream_t s, FoldArgs* deferred_fold, gcp_adam_state* advance_t = nullptr,
-                            bool* launched = nullptr, int64_t first = 0, int64_t count = -1)
+                            bool* launched = nullptr, int64_t first = 0, int64_t count = -1,
+                            const AdamArgs* adam = nullptr, bool* adam_fused = nullptr)
 {
+    if (adam_fused) *adam_fused = false;
     if (launched) *launched = false;
     if (!h || (S == nullptr) == (list == nullptr)) return GCP_ERR_INVALID_ARG;
     if (loss < GCP_LOSS_GAUSSIAN || loss > GCP_LOSS_BETA_HALF) return GCP_ERR_INVALID_ARG;
@@ -941,18 +946,38 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
             a.rep_stride[k] = 0;
         }
     }
-    // the fold is done by the gradient kernel's last blocks to finish (four lanes
-    // per float4 element, at most 64 blocks, at most four elements per lane)
-    // instead of a launch of its own
+    // the fold is done by the gradient kernel's last blocks to finish instead of
+    // a launch of its own: enough blocks that each lane loads about eight
+    // replica chunks (one round trip), at most 64
     if (!deferred_fold && fold.nmodes > 0) {
-        const int64_t quads_per_block = sh.block / 4;
-        const int64_t passes = (fold.off4[fold.nmodes] + quads_per_block - 1) / quads_per_block;
-        const int64_t blocks = std::max<int64_t>(1, (passes + 3) / 4);
+        int64_t loads = 0;
+        for (int m = 0; m < fold.nmodes; ++m) loads += (fold.off4[m + 1] - fold.off4[m]) * fold.reps[m];
+        const int64_t blocks = std::max<int64_t>(1, (loads + 8 * sh.block - 1) / (8 * sh.block));
         if (blocks <= 64 && blocks <= grid) {
             a.tail = fold;
             a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
             a.tail_blocks = static_cast<int32_t>(blocks);
             a.tail_status = h->d_status;
+        }
+    }
+    // the Adam step of gcp_iteration by the gradient kernel's last blocks (four
+    // lanes per float4 element, at most 64 blocks) for small factor sets
+    if (adam && deferred_fold && advance_t && h->tune.adam_launch == 0) {
+        AdamArgs ad = *adam;
+        for (int k = 0; k < h->X.d; ++k) {
+            ad.reps[k] = deferred_fold->reps[k] > 1 ? deferred_fold->reps[k] : 1;
+            ad.R[k] = deferred_fold->R[k];
+            ad.rep_stride4[k] = deferred_fold->rep_stride4[k];
+        }
+        ad.t_advanced = 1;
+        const int64_t blocks = (ad.mt.off4[h->X.d] * 4 + sh.block - 1) / sh.block;
+        if (blocks <= 64 && blocks <= grid) {
+            a.adam = ad;
+            a.tail_adam = 1;
+            a.tail_blocks = static_cast<int32_t>(std::max<int64_t>(1, blocks));
+            a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
+            a.tail_status = h->d_status;
+            if (adam_fused) *adam_fused = true;
         }
     }
     const bool timed = h->prof_ev && h->prof_used < h->prof_cap;
@@ -1156,19 +1181,12 @@ gcp_status gcp_iteration(gcp_handle* h, const gcp_factors* F, gcp_loss loss, con
     if (mode_table(F, h->X.d, h->X.dims).off4[h->X.d] >= (int64_t(1) << 31))  // 32-bit element indices
         return GCP_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    FoldArgs fold{};
-    bool advanced = false;
-    st = grad_impl(h, F, loss, S, nullptr, stream_dev, G, s, &fold, state, &advanced);
-    if (st != GCP_OK) return st;
     AdamArgs a{};
     a.mt = mode_table(F, h->X.d, h->X.dims);
     for (int k = 0; k < h->X.d; ++k) {
         a.mt.G[k] = G[k];
         a.mt.B[k] = B[k];
         a.mt.C[k] = C[k];
-        a.reps[k] = fold.reps[k] > 1 ? fold.reps[k] : 1;
-        a.R[k] = fold.R[k];
-        a.rep_stride4[k] = fold.rep_stride4[k];
     }
     a.beta1 = prm->beta1;
     a.beta2 = prm->beta2;
@@ -1176,6 +1194,16 @@ gcp_status gcp_iteration(gcp_handle* h, const gcp_factors* F, gcp_loss loss, con
     a.lower = prm->lower;
     a.eps_inside_sqrt = prm->eps_inside_sqrt;
     a.st = state;
+    FoldArgs fold{};
+    bool advanced = false, fused = false;
+    st = grad_impl(h, F, loss, S, nullptr, stream_dev, G, s, &fold, state, &advanced, 0, -1, &a, &fused);
+    if (st != GCP_OK) return st;
+    if (fused) return GCP_OK;  // the gradient kernel's last blocks took the step
+    for (int k = 0; k < h->X.d; ++k) {
+        a.reps[k] = fold.reps[k] > 1 ? fold.reps[k] : 1;
+        a.R[k] = fold.R[k];
+        a.rep_stride4[k] = fold.rep_stride4[k];
+    }
     a.t_advanced = advanced ? 1 : 0;
     const bool timed = h->prof_ev2 && h->prof_used2 < h->prof_cap;
     if (timed) GCP_CUDA_TRY(cudaEventRecord(h->prof_ev2[2 * h->prof_used2], s));

@@ -31,6 +31,7 @@
 
 #include <type_traits>
 
+#include "gcp_adam_phase.cuh"
 #include "gcp_draw.cuh"
 #include "gcp_lookback.cuh"
 
@@ -197,18 +198,23 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
     }
 }
 
-// gcp_grad with replica slabs: the last a.tail_blocks blocks to finish their
-// draws fold the slabs into the caller's G_k instead of a fold launch.  Every
+// The kernel's tail work, done by the last a.tail_blocks blocks to finish
+// their draws instead of a launch of its own: the fold of gcp_grad's replica
+// slabs into the caller's G_k, or (tail_adam, gcp_iteration with a small
+// factor set) the whole Adam step of Alg. 4 with the fold inside it.  Every
 // thread fences its own reductions before its block counts itself done; a
-// folding block then waits (bounded: kSpinLimit polls, then GCP_ERR_TIMEOUT
-// and no fold) until every block has counted itself, and reads through L2
-// (ld.cg).  Four lanes share a float4 element of G_k: lane s sums replicas s,
-// s + 4, s + 8, ... in order, the four partial sums are added by two
-// shuffles, and lane 0 adds the total to G_k; the slabs are left zero.  At
-// most 64 blocks wait, fewer than the blocks one wave keeps resident, so the
-// blocks still to run always find room.  The last folding block to finish
-// clears both counters for the next launch.
-__device__ __forceinline__ void fold_tail(const GradArgs& a)
+// tail block then waits (bounded: kSpinLimit polls, then GCP_ERR_TIMEOUT and
+// no tail work) until every block has counted itself, and reads through L2
+// (ld.cg) what other blocks wrote.  Fold: four lanes share a float4 element
+// of G_k, lane s sums replicas s, s + 4, s + 8, ... in order, the four
+// partial sums are added by two shuffles and lane 0 adds the total to G_k;
+// the slabs are left zero.  Adam: the elements are dealt to the tail blocks'
+// threads as in the split Adam kernel (four lanes per element).  At most 64
+// blocks wait, fewer than the blocks one wave keeps resident, so the blocks
+// still to run always find room.  The last tail block to finish clears both
+// counters for the next launch (and, after an Adam step, advances the
+// iteration count).
+static __device__ __noinline__ void fold_tail(const GradArgs& a)
 {
     __shared__ int tail_rank, tail_ok;
     __threadfence();
@@ -235,7 +241,19 @@ __device__ __forceinline__ void fold_tail(const GradArgs& a)
     __syncthreads();
     const int rank = tail_rank;
     if (rank < 0) return;
-    if (tail_ok) {
+    if (tail_ok && a.tail_adam) {
+        __threadfence();
+        const AdamArgs& ad = a.adam;
+        const uint32_t total4 = static_cast<uint32_t>(ad.mt.off4[ad.mt.d]);
+        const uint32_t gthread = static_cast<uint32_t>(rank) * blockDim.x + threadIdx.x;
+        const volatile gcp_adam_state* st = ad.st;
+        const int64_t t = st->t;  // advanced by block 0 at the kernel's start
+        const float alpha = st->alpha;
+        const int done = st->done;
+        AdamElem e;
+        adam_prepare(ad, gthread / kParts, total4, gthread % kParts, e);
+        adam_elements(ad, gthread, K * blockDim.x, e, t, alpha, done);
+    } else if (tail_ok) {
         __threadfence();
         const FoldArgs& f = a.tail;
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -282,6 +300,7 @@ __device__ __forceinline__ void fold_tail(const GradArgs& a)
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(a.tail_done + 1, 1u) == K - 1) {
+            if (a.tail_adam) a.adam.st->iter += 1;
             a.tail_done[0] = 0u;
             a.tail_done[1] = 0u;
         }
@@ -636,7 +655,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
             }
         }
     }
-    if (a.tail.nmodes > 0) fold_tail(a);
+    if (a.tail_blocks > 0) fold_tail(a);
 }
 
 #define GCP_GRAD_CONFIGS(X) \

@@ -82,36 +82,6 @@ struct FoldArgs {
     float* G[GCP_MAX_MODES];
 };
 
-struct GradArgs {
-    DrawArgs dr;
-    int32_t ld, rank, loss, smem_floats;
-    const void* A[GCP_MAX_MODES];  // float or bf16 rows
-    float* G[GCP_MAX_MODES];       // destination of mode k: the caller's G_k or a replica slab
-    uint32_t reps[GCP_MAX_MODES];  // replicas of mode k's destination (CTA b adds into replica b % reps)
-    uint64_t rep_stride[GCP_MAX_MODES];  // floats between replicas
-    uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
-    uint32_t comb_mask;            // bit k: same-address updates of a warp step are summed before the reduction
-    uint32_t smem_off[GCP_MAX_MODES];
-    int32_t group_draws;           // 1: each group of L lanes takes its own draw (32/L draws per warp step)
-    int32_t early;                 // 1: each warp's first descriptors are made before the dependency wait
-    int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
-    gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
-    ZeroTileArgs zt;               // layout 3: the zeros made in this launch (dr.n_total then ends the nonzeros)
-    FoldArgs tail;                 // nmodes > 0: the last tail_blocks blocks fold these replica slabs into G
-    unsigned int* tail_done;       //   [0] blocks finished, [1] folding blocks finished (zero between launches)
-    int32_t tail_blocks;           //   1..64
-    int32_t* tail_status;          //   status word (a wait that ran out)
-};
-
-struct LossArgs {
-    DrawArgs dr;  // always kSrcList
-    int32_t ld, rank, loss, pad;
-    const void* A[GCP_MAX_MODES];
-    double* partials;     // one per block
-    unsigned int* ticket; // zero between launches
-    double* out;
-};
-
 struct ModeTable {
     int32_t d, ld, rank, pad;
     int64_t off4[GCP_MAX_MODES + 1];  // prefix of n_k * ld / 4
@@ -139,6 +109,39 @@ struct AdamArgs {
     // advanced st->t, so no block of this launch has to wait for the others
     int32_t t_advanced;
 };
+
+struct GradArgs {
+    DrawArgs dr;
+    int32_t ld, rank, loss, smem_floats;
+    const void* A[GCP_MAX_MODES];  // float or bf16 rows
+    float* G[GCP_MAX_MODES];       // destination of mode k: the caller's G_k or a replica slab
+    uint32_t reps[GCP_MAX_MODES];  // replicas of mode k's destination (CTA b adds into replica b % reps)
+    uint64_t rep_stride[GCP_MAX_MODES];  // floats between replicas
+    uint32_t smem_mask;            // bit k: mode k accumulates in shared memory first
+    uint32_t comb_mask;            // bit k: same-address updates of a warp step are summed before the reduction
+    uint32_t smem_off[GCP_MAX_MODES];
+    int32_t group_draws;           // 1: each group of L lanes takes its own draw (32/L draws per warp step)
+    int32_t early;                 // 1: each warp's first descriptors are made before the dependency wait
+    int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
+    gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
+    ZeroTileArgs zt;               // layout 3: the zeros made in this launch (dr.n_total then ends the nonzeros)
+    FoldArgs tail;                 // nmodes > 0: the last tail_blocks blocks fold these replica slabs into G
+    unsigned int* tail_done;       //   [0] blocks finished, [1] folding blocks finished (zero between launches)
+    int32_t tail_blocks;           //   1..64
+    int32_t* tail_status;          //   status word (a wait that ran out)
+    int32_t tail_adam;             // 1 (gcp_iteration): those blocks take the Adam step (adam) instead
+    AdamArgs adam;
+};
+
+struct LossArgs {
+    DrawArgs dr;  // always kSrcList
+    int32_t ld, rank, loss, pad;
+    const void* A[GCP_MAX_MODES];
+    double* partials;     // one per block
+    unsigned int* ticket; // zero between launches
+    double* out;
+};
+
 
 struct EpochArgs {
     ModeTable mt;

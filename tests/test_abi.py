@@ -73,7 +73,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gcp.gcp_samples) == 96
     assert ctypes.sizeof(gcp.gcp_adam_params) == 24
     assert ctypes.sizeof(gcp.gcp_epoch_params) == 16
-    assert ctypes.sizeof(gcp.gcp_tuning) == 52
+    assert ctypes.sizeof(gcp.gcp_tuning) == 56
     assert ctypes.sizeof(gcp.gcp_launch_info) == 76
 
 
