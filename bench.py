@@ -734,21 +734,33 @@ def form_dense100(torch, gcp, stream, peak, args, tau=100, epochs=5):
     stream.synchronize()
     t_epoch = _time_calls(torch, run.run_epoch, stream, epochs)
     mean_s, n, adam_s = time_grad_kernel(torch, gcp, run.h, run.iteration, stream)
+    launch = gcp.gcp_get_launch(run.h, run.F, s)
     iter_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
+    # the same iteration with the Adam step in a launch of its own, for comparison
+    best = dict((run.tuned or {}).get("best") or {"early_draws": 1})
+    best.pop("fused", None)
+    gcp.gcp_set_tuning(run.h, **dict(best, adam_launch=1))
+    iter_sep_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
+    gcp.gcp_set_tuning(run.h, **best)
     adam_s = adam_only_time(torch, gcp, run.F, stream)
-    grad_in_graph = iter_s - adam_s
+    grad_in_graph = iter_sep_s - adam_s
     gb = s * (4 + row_bytes(4, rank, 4))
+    ab = adam_bytes(dims, rank)
     out = {"workload": "dense-100x100x100x100-r10-gaussian-uniform-s1e5", "tau": tau,
            "entries_per_s": tau * s / t_epoch, "ms_per_epoch": t_epoch * 1e3,
-           "grad_bytes_per_launch": gb, "grad_kernel_us": mean_s * 1e6, "adam_us": adam_s * 1e6,
+           "grad_bytes_per_launch": gb, "adam_bytes_per_step": ab, "grad_kernel_us": mean_s * 1e6,
            "grad_frac_of_measured_hbm": gb / mean_s / 1e9 / peak,
+           "kernels_per_iteration": 1 if launch["adam_tail_blocks"] else 2,
            "iteration_us_in_graph": iter_s * 1e6,
-           "iteration_frac_of_measured_hbm": (gb + adam_bytes(dims, rank)) / iter_s / 1e9 / peak,
+           "iteration_frac_of_measured_hbm": (gb + ab) / iter_s / 1e9 / peak,
+           "iteration_us_in_graph_separate_adam_launch": iter_sep_s * 1e6,
            "adam_only_us_in_graph": adam_s * 1e6,
            "grad_us_in_graph_at_most": grad_in_graph * 1e6,
            "grad_frac_in_graph_at_least": gb / grad_in_graph / 1e9 / peak,
-           "launch": gcp.gcp_get_launch(run.h, run.F, s), "autotuned": run.tuned,
-           "traffic_note": "factors and G are 16 KB: rows and updates are L2 hits; DRAM traffic is the X gathers"}
+           "launch": launch, "autotuned": run.tuned,
+           "notes": "grad_kernel_us: CUDA events around each launch (with the Adam step when it is in the kernel); "
+                    "grad_us_in_graph_at_most: the iteration with a separate Adam launch minus a captured Adam step "
+                    "alone; factors and G are 16 KB: rows and updates are L2 hits, DRAM traffic is the X gathers"}
     if not args.no_sweep:
         out["sweep"] = sweep_draws(torch, gcp, run, stream, peak, rank)
     return out

@@ -641,6 +641,8 @@ typedef struct gcp_launch_info {
     int32_t early_draws;
     int32_t zero_tiles;  /* 1: stratified zeros are made inside the gradient launch */
     uint32_t combine_mode_mask;  /* bit k: mode k's updates are combined within a warp step */
+    int32_t adam_tail_blocks;    /* gcp_iteration: blocks of the gradient kernel that take the Adam
+                                    step (0: a separate Adam launch) */
 } gcp_launch_info;
 
 /* Sets (t != NULL) or resets to automatic (t == NULL) the handle's launch
@@ -656,7 +658,8 @@ gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, 
    outside stream capture) and records one pair on the launching stream
    around every fused-gradient kernel launch that follows (gcp_grad,
    gcp_iteration; set 0) and around every Adam kernel launch of
-   gcp_iteration (set 1), until the pairs are used up; enable = 0 destroys
+   gcp_iteration (set 1; none when the gradient kernel took the step, see
+   gcp_tuning.adam_launch), until the pairs are used up; enable = 0 destroys
    them.  gcp_profile_read synchronises the events of set `which` and returns
    the summed device time of its recorded launches in milliseconds and their
    count, then starts a new count.  host outputs. */

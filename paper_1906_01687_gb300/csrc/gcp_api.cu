@@ -22,7 +22,7 @@ static_assert(sizeof(gcp_adam_params) == 24, "gcp_adam_params layout");
 static_assert(sizeof(gcp_epoch_params) == 16, "gcp_epoch_params layout");
 static_assert(sizeof(gcp_adam_state) == 64, "gcp_adam_state layout");
 static_assert(sizeof(gcp_tuning) == 56, "gcp_tuning layout");
-static_assert(sizeof(gcp_launch_info) == 76, "gcp_launch_info layout");
+static_assert(sizeof(gcp_launch_info) == 80, "gcp_launch_info layout");
 
 struct gcp_handle {
     gcp_tensor X{};
@@ -742,6 +742,13 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
     out->early_draws = sh.early;
     out->zero_tiles = zero_tiles_apply(h, sh) ? 1 : 0;
     out->combine_mode_mask = sh.comb;
+    {
+        int64_t total4 = 0;
+        for (int k = 0; k < h->X.d; ++k) total4 += h->X.dims[k] * (F->ld / 4);
+        const int64_t blocks = std::max<int64_t>(1, (total4 * 4 + sh.block - 1) / sh.block);
+        out->adam_tail_blocks = (h->tune.adam_launch == 0 && blocks <= 64 && blocks <= sh.grid && n_draws > 0)
+                                    ? static_cast<int32_t>(blocks) : 0;
+    }
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
     return GCP_OK;
 }
@@ -970,7 +977,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
             ad.rep_stride4[k] = deferred_fold->rep_stride4[k];
         }
         ad.t_advanced = 1;
-        const int64_t blocks = (ad.mt.off4[h->X.d] * 4 + sh.block - 1) / sh.block;
+        const int64_t blocks = std::max<int64_t>(1, (ad.mt.off4[h->X.d] * 4 + sh.block - 1) / sh.block);
         if (blocks <= 64 && blocks <= grid) {
             a.adam = ad;
             a.tail_adam = 1;

@@ -85,7 +85,7 @@ class gcp_launch_info(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("smem_mode_mask", ctypes.c_uint32),
                 ("replicas", ctypes.c_int32 * MAX_MODES), ("group_draws", ctypes.c_int32),
                 ("prefetch", ctypes.c_int32), ("early_draws", ctypes.c_int32), ("zero_tiles", ctypes.c_int32),
-                ("combine_mode_mask", ctypes.c_uint32)]
+                ("combine_mode_mask", ctypes.c_uint32), ("adam_tail_blocks", ctypes.c_int32)]
 
 
 class gcp_batch_problem(ctypes.Structure):
@@ -398,7 +398,7 @@ def gcp_get_launch(h: Handle, F: Factors, n_draws: int) -> dict:
     return dict(lanes=t.lanes, chunks=t.chunks, block=t.block, grid_blocks=t.grid_blocks,
                 smem_bytes=t.smem_bytes, smem_mode_mask=t.smem_mode_mask, replicas=list(t.replicas)[: h.d],
                 group_draws=t.group_draws, prefetch=t.prefetch, early_draws=t.early_draws, zero_tiles=t.zero_tiles,
-                combine_mode_mask=t.combine_mode_mask)
+                combine_mode_mask=t.combine_mode_mask, adam_tail_blocks=t.adam_tail_blocks)
 
 
 def gcp_profile(h: Handle, enable: bool, capacity: int = 1024):

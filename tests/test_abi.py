@@ -74,7 +74,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gcp.gcp_adam_params) == 24
     assert ctypes.sizeof(gcp.gcp_epoch_params) == 16
     assert ctypes.sizeof(gcp.gcp_tuning) == 56
-    assert ctypes.sizeof(gcp.gcp_launch_info) == 76
+    assert ctypes.sizeof(gcp.gcp_launch_info) == 80
 
 
 def test_ctypes_layouts_match_the_c_compiler(tmp_path):
