@@ -736,12 +736,15 @@ def form_dense100(torch, gcp, stream, peak, args, tau=100, epochs=5):
     mean_s, n, adam_s = time_grad_kernel(torch, gcp, run.h, run.iteration, stream)
     launch = gcp.gcp_get_launch(run.h, run.F, s)
     iter_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
-    # the same iteration with the Adam step in a launch of its own, for comparison
+    # the same iteration with the Adam step in a launch of its own and as the
+    # gradient kernel's tail work, for comparison
     best = dict((run.tuned or {}).get("best") or {"early_draws": 1})
-    best.pop("fused", None)
-    gcp.gcp_set_tuning(run.h, **dict(best, adam_launch=1))
-    iter_sep_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
+    iters_by_tail = {}
+    for tw in (0, 1):
+        gcp.gcp_set_tuning(run.h, **dict(best, tail_work=tw))
+        iters_by_tail[tw] = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
     gcp.gcp_set_tuning(run.h, **best)
+    iter_sep_s = iters_by_tail[0]
     adam_s = adam_only_time(torch, gcp, run.F, stream)
     grad_in_graph = iter_sep_s - adam_s
     gb = s * (4 + row_bytes(4, rank, 4))
@@ -754,6 +757,7 @@ def form_dense100(torch, gcp, stream, peak, args, tau=100, epochs=5):
            "iteration_us_in_graph": iter_s * 1e6,
            "iteration_frac_of_measured_hbm": (gb + ab) / iter_s / 1e9 / peak,
            "iteration_us_in_graph_separate_adam_launch": iter_sep_s * 1e6,
+           "iteration_us_in_graph_adam_in_gradient_kernel": iters_by_tail[1] * 1e6,
            "adam_only_us_in_graph": adam_s * 1e6,
            "grad_us_in_graph_at_most": grad_in_graph * 1e6,
            "grad_frac_in_graph_at_least": gb / grad_in_graph / 1e9 / peak,

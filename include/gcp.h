@@ -604,11 +604,11 @@ gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *d
    sum the updates that the groups of one warp step make to the same 16
    bytes of G_k (a match on the row and column chunk, then shuffles) before
    one lane issues the L2 reduction (0 = off).
-   adam_launch (gcp_iteration): 0 (automatic) lets the last blocks of the
-   gradient kernel to finish take the Adam step where the factor set is
-   small (at most 64 blocks at four lanes per float4 element; they wait,
-   bounded, for the other blocks, then GCP_ERR_TIMEOUT) instead of a launch
-   of its own; 1 always launches the Adam kernel.
+   tail_work: 1 lets the last blocks of the gradient kernel to finish take
+   gcp_grad's replica fold and, where the factor set is small, gcp_iteration's
+   Adam step (at most 64 blocks; they wait, bounded, for the other blocks,
+   then GCP_ERR_TIMEOUT) instead of launches of their own; 0 (default)
+   launches the fold and Adam kernels.
    A tuning choice changes the summation order only, never the draws. */
 typedef struct gcp_tuning {
     int32_t lanes;
@@ -624,7 +624,7 @@ typedef struct gcp_tuning {
     int32_t early_draws;
     int32_t zero_pass;
     int32_t warp_combine;
-    int32_t adam_launch;
+    int32_t tail_work;
 } gcp_tuning;
 
 /* The launch shape gcp_grad chose (gcp_get_launch). */
@@ -659,7 +659,7 @@ gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, 
    around every fused-gradient kernel launch that follows (gcp_grad,
    gcp_iteration; set 0) and around every Adam kernel launch of
    gcp_iteration (set 1; none when the gradient kernel took the step, see
-   gcp_tuning.adam_launch), until the pairs are used up; enable = 0 destroys
+   gcp_tuning.tail_work), until the pairs are used up; enable = 0 destroys
    them.  gcp_profile_read synchronises the events of set `which` and returns
    the summed device time of its recorded launches in milliseconds and their
    count, then starts a new count.  host outputs. */

@@ -4,6 +4,7 @@ For one handle, factor layout and sampling spec, times ``gcp_grad`` for a set
 of candidate shapes -- lanes per draw x float4 chunks per lane (rows per
 warp), threads per block, replica slabs per mode (the pre-reduction width of
 the L2 accumulation), warp-level pre-reduction of same-address updates, the
+fold (and Adam step) as the kernel's own tail work, the
 draw layout (group walk, prefetch or staged walk) and optional
 shared-memory accumulation -- with CUDA
 events around back-to-back launches, and keeps the fastest through
@@ -147,6 +148,16 @@ def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launche
             gcp.gcp_set_tuning(h, **cfg)
         except gcp.GcpError:
             continue
+        t = time_grad(h, F, loss, spec, launches, stream, call, graph, cap)
+        results.append((t, cfg))
+        if log:
+            log(dict(seconds=t, **cfg))
+        if t < best_t:
+            best, best_t = cfg, t
+    # the fastest shape once more with its fold (and Adam step) as the kernel's tail work
+    if best is not None and not best.get("tail_work"):
+        cfg = dict(best, tail_work=1)
+        gcp.gcp_set_tuning(h, **cfg)
         t = time_grad(h, F, loss, spec, launches, stream, call, graph, cap)
         results.append((t, cfg))
         if log:

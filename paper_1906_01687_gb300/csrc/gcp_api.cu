@@ -716,7 +716,7 @@ gcp_status gcp_set_tuning(gcp_handle* h, const gcp_tuning* t)
     if (t->block != 0 && (t->block < 32 || t->block > 256 || t->block % 32 != 0)) return GCP_ERR_INVALID_ARG;
     if (t->grid_blocks < 0 || t->smem_bytes > 200 * 1024 || t->max_replicas > 1024 || t->replica_target < 0 ||
         t->group_draws < 0 || t->group_draws > 1 || t->early_draws < 0 || t->early_draws > 1 || t->zero_pass < 0 ||
-        t->zero_pass > 1 || t->warp_combine < 0 || t->adam_launch < 0 || t->adam_launch > 1)
+        t->zero_pass > 1 || t->warp_combine < 0 || t->tail_work < 0 || t->tail_work > 1)
         return GCP_ERR_INVALID_ARG;
     h->tune = *t;
     return GCP_OK;
@@ -746,7 +746,7 @@ gcp_status gcp_get_launch(gcp_handle* h, const gcp_factors* F, int64_t n_draws, 
         int64_t total4 = 0;
         for (int k = 0; k < h->X.d; ++k) total4 += h->X.dims[k] * (F->ld / 4);
         const int64_t blocks = std::max<int64_t>(1, (total4 * 4 + sh.block - 1) / sh.block);
-        out->adam_tail_blocks = (h->tune.adam_launch == 0 && blocks <= 64 && blocks <= sh.grid && n_draws > 0)
+        out->adam_tail_blocks = (h->tune.tail_work == 1 && blocks <= 64 && blocks <= sh.grid && n_draws > 0)
                                     ? static_cast<int32_t>(blocks) : 0;
     }
     for (int k = 0; k < h->X.d; ++k) out->replicas[k] = static_cast<int32_t>(sh.reps[k]);
@@ -956,7 +956,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     // the fold is done by the gradient kernel's last blocks to finish instead of
     // a launch of its own: enough blocks that each lane loads about eight
     // replica chunks (one round trip), at most 64
-    if (!deferred_fold && fold.nmodes > 0) {
+    if (!deferred_fold && fold.nmodes > 0 && h->tune.tail_work == 1) {
         int64_t loads = 0;
         for (int m = 0; m < fold.nmodes; ++m) loads += (fold.off4[m + 1] - fold.off4[m]) * fold.reps[m];
         const int64_t blocks = std::max<int64_t>(1, (loads + 8 * sh.block - 1) / (8 * sh.block));
@@ -969,7 +969,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
     }
     // the Adam step of gcp_iteration by the gradient kernel's last blocks (four
     // lanes per float4 element, at most 64 blocks) for small factor sets
-    if (adam && deferred_fold && advance_t && h->tune.adam_launch == 0) {
+    if (adam && deferred_fold && advance_t && h->tune.tail_work == 1) {
         AdamArgs ad = *adam;
         for (int k = 0; k < h->X.d; ++k) {
             ad.reps[k] = deferred_fold->reps[k] > 1 ? deferred_fold->reps[k] : 1;

@@ -77,7 +77,7 @@ class gcp_tuning(ctypes.Structure):
                 ("max_replicas", ctypes.c_int32), ("replica_target", ctypes.c_int32),
                 ("group_draws", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("early_draws", ctypes.c_int32),
                 ("zero_pass", ctypes.c_int32), ("warp_combine", ctypes.c_int32),
-                ("adam_launch", ctypes.c_int32)]
+                ("tail_work", ctypes.c_int32)]
 
 
 class gcp_launch_info(ctypes.Structure):
@@ -372,10 +372,10 @@ def gcp_get_device_status(h: Handle) -> int:
 
 TUNING_FIELDS = ("lanes", "chunks", "block", "grid_blocks", "smem_bytes", "smem_min_hits", "max_replicas",
                  "replica_target", "group_draws", "prefetch", "early_draws", "zero_pass", "warp_combine",
-                 "adam_launch")
+                 "tail_work")
 TUNING_DEFAULT = dict(lanes=0, chunks=0, block=0, grid_blocks=0, smem_bytes=-1, smem_min_hits=-1,
                       max_replicas=-1, replica_target=0, group_draws=0, prefetch=0, early_draws=0, zero_pass=0,
-                      warp_combine=0, adam_launch=0)
+                      warp_combine=0, tail_work=0)
 
 
 def gcp_set_tuning(h: Handle, reset: bool = False, **kw):

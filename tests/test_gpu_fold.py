@@ -1,6 +1,7 @@
-"""The fold of replica slabs in gcp_grad: a small fold is done by the
-gradient kernel's last block to finish (a completion counter), a large one
-by a launch of its own.  Either way G_k must be the FP64 oracle's sampled
+"""The fold of replica slabs in gcp_grad: by a launch of its own
+(tail_work = 0) or by the gradient kernel's last blocks to finish
+(tail_work = 1, where at most 64 blocks suffice; a completion counter and a
+bounded wait).  Either way G_k must be the FP64 oracle's sampled
 gradient (Eq. (4.3)) and the slabs must be left zero for the next call, so
 calls queued back to back give each its own gradient.
 """
@@ -22,17 +23,18 @@ def _cuda():
     build.build()
 
 
-@pytest.mark.parametrize("dims,rank", [((40, 30, 20), 8),      # 90 rows x 2 float4: the last block folds
-                                       ((3000, 40, 30), 8),    # 6140 float4 elements: a fold launch
+@pytest.mark.parametrize("tail_work", [0, 1])
+@pytest.mark.parametrize("dims,rank", [((40, 30, 20), 8),      # 90 rows x 2 float4
+                                       ((3000, 40, 30), 8),    # 6140 float4 elements
                                        ((12, 10, 9, 11), 32)])  # 42 rows x 8 float4, 4 modes
-def test_replicated_gradient_queued_back_to_back(dims, rank):
+def test_replicated_gradient_queued_back_to_back(dims, rank, tail_work):
     g = gcp()
     X = np.random.default_rng(50).standard_normal(dims).astype(np.float32)
     h = g.Handle(g.DataTensor.dense(X))
     XO = oracle.Tensor(dims, dense=X.astype(np.float64))
     A = rng_factors(dims, rank, 51, scale=0.5)
     F = g.Factors(A)
-    g.gcp_set_tuning(h, max_replicas=8, replica_target=1)
+    g.gcp_set_tuning(h, max_replicas=8, replica_target=1, tail_work=tail_work)
     assert all(r > 1 for r in g.gcp_get_launch(h, F, 7001)["replicas"])
     outs = []
     for it in range(5):
@@ -47,7 +49,8 @@ def test_replicated_gradient_queued_back_to_back(dims, rank):
                           oracle.grad_abs(dims, f64(A), oracle.GAUSSIAN, SO))
 
 
-def test_replicated_stratified_gradient_with_zero_tiles():
+@pytest.mark.parametrize("tail_work", [0, 1])
+def test_replicated_stratified_gradient_with_zero_tiles(tail_work):
     """The count-like case: short replicated modes, zeros made in the launch,
     the fold done by the last block."""
     g = gcp()
@@ -57,7 +60,7 @@ def test_replicated_stratified_gradient_with_zero_tiles():
     XO = oracle_sparse(dims, idx, vals)
     A = rng_factors(dims, 10, 53, scale=0.4, positive=True)
     F = g.Factors(A)
-    g.gcp_set_tuning(h, max_replicas=32, replica_target=16)
+    g.gcp_set_tuning(h, max_replicas=32, replica_target=16, tail_work=tail_work)
     S = g.Sampling(g.SAMPLER_STRATIFIED, 8000, 9000, seed=6, stream=3)
     G = F.like()
     g.gcp_grad(h, F, g.LOSS_POISSON_LOG, G, S=S)

@@ -307,11 +307,11 @@ def test_profile_events_count_gradient_kernels():
     for x in G:
         x.zero_()
     g.gcp_iteration(h, F, 0, g.Sampling(g.SAMPLER_UNIFORM, 0, 5000, seed=1, stream=9), G, B, C, st)
-    # this small factor set's Adam step is taken by the gradient kernel's last blocks: no Adam launch to time
-    assert g.gcp_profile_read(h, 0)[1] == 1 and g.gcp_profile_read(h, 1)[1] == 0
-    g.gcp_set_tuning(h, adam_launch=1)
-    g.gcp_iteration(h, F, 0, g.Sampling(g.SAMPLER_UNIFORM, 0, 5000, seed=1, stream=10), G, B, C, st)
     assert g.gcp_profile_read(h, 0)[1] == 1 and g.gcp_profile_read(h, 1)[1] == 1
+    # with tail_work this small factor set's Adam step is taken by the gradient kernel: no Adam launch to time
+    g.gcp_set_tuning(h, tail_work=1)
+    g.gcp_iteration(h, F, 0, g.Sampling(g.SAMPLER_UNIFORM, 0, 5000, seed=1, stream=10), G, B, C, st)
+    assert g.gcp_profile_read(h, 0)[1] == 1 and g.gcp_profile_read(h, 1)[1] == 0
     g.gcp_profile(h, False)
 
 
