@@ -776,13 +776,20 @@ def sweep_draws(torch, gcp, run, stream, peak, rank, sizes=(100_000, 1_000_000, 
     kernels."""
     out = []
     F = gcp.Factors([a[:, :rank] for a in run.F.A])
+    # the tuned shape without its grid (a grid fitted to 1e5 draws would starve larger launches)
+    best = dict((run.tuned or {}).get("best") or {"early_draws": 1})
+    best.pop("grid_blocks", None)
+    gcp.gcp_set_tuning(run.h, **best)
     for s in sizes:
         spec = gcp.Sampling(gcp.SAMPLER_UNIFORM, 0, s, 99, 0)
         iters = max(3, min(50, 5_000_000 // s))
         us = time_iterations(torch, gcp, run.h, F, gcp.LOSS_GAUSSIAN, spec, stream, iters=iters) * 1e6
         gbs = s * (4 + row_bytes(4, rank, 4)) / us / 1e3
         out.append({"draws_per_iteration": s, "us_per_iteration": us, "entries_per_s": s / us * 1e6,
-                    "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peak})
+                    "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                    "launch": gcp.gcp_get_launch(run.h, F, s)})
+    if run.tuned:
+        gcp.gcp_set_tuning(run.h, **run.tuned["best"])
     return out
 
 

@@ -476,6 +476,16 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
         make_draw<D>(a.dr, wb0 + sub, stream, my);
     }
     pdl_wait();
+    // With the Adam step in this kernel's tail the next launch (the next
+    // iteration's gradient kernel) starts as soon as every block of this one
+    // has triggered, long before this one ends: block 0 publishes the next
+    // launch's stream prediction before it triggers (fenced, so that the next
+    // launch's early reads see it).  Otherwise it is written at the end.
+    if (a.tail_adam && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0) {
+        *reinterpret_cast<volatile int64_t*>(a.stream_pred) =
+            *reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev) + 1;
+        __threadfence();
+    }
     pdl_trigger();
 
     // gcp_iteration: this iteration's Adam step count, advanced here so that the
@@ -638,7 +648,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     }
 
     // the prediction for the next launch that reads its stream word from memory
-    if (a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
+    if (!a.tail_adam && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
         *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
     if (a.smem_mask != 0) {
         __syncthreads();
