@@ -664,10 +664,17 @@ def form_large_bf16(torch, gcp, run, XO, A0, planted, stream, peak):
     G_ref = oracle_grad_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, SO, cores)
     estO = oracle.sample(XO, oracle.SEMI_STRATIFIED, EST_P, EST_Q, 7, gcp.STREAM_EST)
     F_ref = oracle_loss_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, estO, cores)
+    from paper_1906_01687_gb300.autotune import autotune, candidates, with_grids
+    fp32_tuning = (run.tuned or {}).get("best")
     for name, bf16 in (("fp32", False), ("bf16", True)):
         b_f = 2 if bf16 else 4
         with torch.cuda.stream(stream):  # the timing steps its own copy of the factors
             F_t = gcp.Factors(A0, bf16=bf16)
+        tuned = None
+        if bf16 and fp32_tuning is not None:  # BF16 rows get a launch shape of their own
+            tuned = autotune(run.h, F_t, run.loss, spec, launches=10, stream=stream,
+                             configs=with_grids([dict(c, early_draws=1) for c in candidates(RANK)],
+                                                P_DRAWS + Q_DRAWS))
         mean_s, n, adam_s = grad_launch_time(torch, gcp, run.h, F_t, run.loss, spec, stream)
         iter_s = time_iterations(torch, gcp, run.h, F_t, run.loss, spec, stream)
         del F_t
@@ -686,7 +693,10 @@ def form_large_bf16(torch, gcp, run, XO, A0, planted, stream, peak):
                "iteration_us": iter_s * 1e6, "iteration_frac_of_measured_hbm": (gb + ab) / iter_s / 1e9 / peak,
                "grad_rel_err_vs_fp64_oracle": rel_err(got, G_ref),
                "loss_rel_err_vs_fp64_oracle": abs(F_dev.item() - F_ref) / abs(F_ref),
-               "launch": gcp.gcp_get_launch(run.h, F, P_DRAWS + Q_DRAWS)}
+               "launch": gcp.gcp_get_launch(run.h, F, P_DRAWS + Q_DRAWS),
+               "tuning": tuned["best"] if tuned else fp32_tuning}
+        if tuned:
+            gcp.gcp_set_tuning(run.h, **fp32_tuning)
         if bf16:
             Ab = [a.double().cpu().numpy()[:, :RANK] for a in F.A_bf16]
             G_rb = oracle_grad_threads(DIMS, Ab, oracle.BERNOULLI_LOGIT, SO, cores)
