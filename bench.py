@@ -664,17 +664,26 @@ def form_large_bf16(torch, gcp, run, XO, A0, planted, stream, peak):
     G_ref = oracle_grad_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, SO, cores)
     estO = oracle.sample(XO, oracle.SEMI_STRATIFIED, EST_P, EST_Q, 7, gcp.STREAM_EST)
     F_ref = oracle_loss_threads(DIMS, A64, oracle.BERNOULLI_LOGIT, estO, cores)
-    from paper_1906_01687_gb300.autotune import autotune, candidates, with_grids
+    from paper_1906_01687_gb300.autotune import autotune, candidates
     fp32_tuning = (run.tuned or {}).get("best")
     for name, bf16 in (("fp32", False), ("bf16", True)):
         b_f = 2 if bf16 else 4
         with torch.cuda.stream(stream):  # the timing steps its own copy of the factors
             F_t = gcp.Factors(A0, bf16=bf16)
         tuned = None
-        if bf16 and fp32_tuning is not None:  # BF16 rows get a launch shape of their own
-            tuned = autotune(run.h, F_t, run.loss, spec, launches=10, stream=stream,
-                             configs=with_grids([dict(c, early_draws=1) for c in candidates(RANK)],
-                                                P_DRAWS + Q_DRAWS))
+        if bf16 and fp32_tuning is not None:
+            # BF16 rows get a launch shape of their own, timed as GCP-Adam times
+            # them: whole iterations captured in a CUDA graph
+            with torch.cuda.stream(stream):
+                Gt, Bt, Ct = F_t.like(), F_t.like(), F_t.like()
+                st_t = gcp.new_state(F_t.A[0].device)
+                gcp.gcp_state_init(st_t, 1e-4, stream=stream)
+
+            def call(sp, strm):
+                gcp.gcp_iteration(run.h, F_t, run.loss, sp, Gt, Bt, Ct, st_t, stream_dev=st_t[3:4], stream=strm)
+            tuned = autotune(run.h, F_t, run.loss, spec, launches=5, stream=stream, call=call, graph=True,
+                             configs=[dict(c, early_draws=1) for c in candidates(RANK)])
+            del Gt, Bt, Ct, st_t
         mean_s, n, adam_s = grad_launch_time(torch, gcp, run.h, F_t, run.loss, spec, stream)
         iter_s = time_iterations(torch, gcp, run.h, F_t, run.loss, spec, stream)
         del F_t
@@ -972,6 +981,7 @@ def main():
     ap.add_argument("--form", default=None, choices=["dense100", "count", "batched"],
                     help="run one of the other workloads alone and print its JSON object (the command "
                          "profiled for that workload's kernel breakdown)")
+    ap.add_argument("--bf16", action="store_true", help="with --profile: BF16-stored factor rows")
     ap.add_argument("--profile", type=int, default=0, metavar="ITERS",
                     help="only set up the benchmark's run and take ITERS eager GCP-Adam iterations, then exit "
                          "(the command profiled with ncu; prints one line of timing); with --form count, ITERS "
@@ -1022,7 +1032,7 @@ def profile_arm(args):
     XT = gcp.DataTensor.coo(DIMS, idx, None)
     with torch.cuda.stream(stream):
         run = GcpAdam(XT, A0, gcp.LOSS_BERNOULLI_LOGIT, gcp.SAMPLER_SEMI_STRATIFIED, P_DRAWS, Q_DRAWS, EST_P, EST_Q,
-                      seed=1687, est_seed=7, alpha=ALPHA, tau=TAU, kappa=1_000_000, stream=stream)
+                      seed=1687, est_seed=7, alpha=ALPHA, tau=TAU, kappa=1_000_000, stream=stream, bf16=args.bf16)
         if args.tuning:
             gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1035,7 +1045,7 @@ def profile_arm(args):
     stream.synchronize()
     ms, n = gcp.gcp_profile_read(run.h, 0)
     gcp.gcp_profile(run.h, False)
-    print(json.dumps({"profile": WORKLOAD, "iterations": args.profile,
+    print(json.dumps({"profile": WORKLOAD + ("-bf16" if args.bf16 else ""), "iterations": args.profile,
                       "us_per_iteration": a.elapsed_time(b) * 1e3 / args.profile,
                       "grad_kernel_us": ms * 1e3 / max(n, 1),
                       "launch": gcp.gcp_get_launch(run.h, run.F, P_DRAWS + Q_DRAWS)}), flush=True)
