@@ -187,20 +187,6 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16* __restrict__ p)
     return out;
 }
 
-// 8 consecutive BF16 entries (one 16-byte load) as two float4.
-__device__ __forceinline__ void load8(const __nv_bfloat16* __restrict__ p, float4& lo, float4& hi)
-{
-    const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
-    lo.x = __uint_as_float(raw.x << 16);
-    lo.y = __uint_as_float(raw.x & 0xFFFF0000u);
-    lo.z = __uint_as_float(raw.y << 16);
-    lo.w = __uint_as_float(raw.y & 0xFFFF0000u);
-    hi.x = __uint_as_float(raw.z << 16);
-    hi.y = __uint_as_float(raw.z & 0xFFFF0000u);
-    hi.z = __uint_as_float(raw.w << 16);
-    hi.w = __uint_as_float(raw.w & 0xFFFF0000u);
-}
-
 // G_k(i, cols) += v: one 16-byte reduction performed at L2 (red, no value
 // returned to the thread; relaxed, GPU scope).  Needs a 16-byte aligned address.
 __device__ __forceinline__ void red_add4(float* p, const float4 v)

@@ -70,36 +70,15 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
         const bool valid = __shfl_sync(kFull, static_cast<int>(my.valid), src) != 0;
 
         // m_i = sum_j prod_k A_k(i_k, j) over this lane's chunks of the d rows.
-        // With one chunk per lane, or two with 3 modes, the rows stay
-        // in registers for the scatter; otherwise they are re-read there (L1
-        // hits) to keep registers low.  For 3 and 4 modes the pairwise
-        // products of the rows serve both m and the leave-one-out products of
-        // the scatter.  BF16 rows with two chunks per lane (8 consecutive
-        // entries) are read with one 16-byte load where the rows allow it.
-        constexpr bool kKeep = NC == 1 || (NC == 2 && D == 3);
+        // With one chunk per lane the rows stay in registers for the scatter;
+        // with several they are re-read there (L1 hits) to keep registers low.
+        // For 3 and 4 modes with one chunk, the pairwise products of the rows
+        // serve both m and the leave-one-out products of the scatter.
+        constexpr bool kKeep = NC == 1;
         constexpr bool kPairs = kKeep && (D == 3 || D == 4);
-        constexpr int KC = kKeep ? NC : 1;
-        float4 r[KC][D];
-        float4 p01[KC], p23[KC];
-#pragma unroll
-        for (int c = 0; c < KC; ++c) p01[c] = p23[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 r[D];
+        float4 p01 = make_float4(0.f, 0.f, 0.f, 0.f), p23 = p01;
         float part = 0.0f;
-        bool wide = false;
-        if constexpr (BF16 && NC == 2 && kKeep) {
-            wide = (ld & 7) == 0;  // rows start on 16 bytes; a lane's 8 entries are one load
-            if (wide) {
-                const int col0 = gl * 8;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if (valid && col0 < rank) {
-                        load8(static_cast<const __nv_bfloat16*>(a.A[k]) + static_cast<size_t>(ix[k]) * ld + col0,
-                              r[0][k], r[1][k]);
-                    } else {
-                        r[0][k] = r[1][k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-            }
-        }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const int col = (gl * NC + c) * 4;
@@ -108,23 +87,21 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
             for (int k = 0; k < D; ++k) {
                 if (k >= d) {
                     v[k] = make_float4(1.f, 1.f, 1.f, 1.f);
-                } else if (wide) {
-                    v[k] = r[kKeep ? c : 0][k];
                 } else if (valid && col < rank) {
                     v[k] = row4(k, ix[k], col);
                 } else {
                     v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                if (kKeep) r[kKeep ? c : 0][k] = v[k];
+                if (kKeep) r[k] = v[k];
             }
             float4 prod;
             if constexpr (kPairs) {
-                p01[c] = mul4(v[0], v[1]);
+                p01 = mul4(v[0], v[1]);
                 if constexpr (D == 4) {
-                    p23[c] = mul4(v[2], v[3]);
-                    prod = mul4(p01[c], p23[c]);
+                    p23 = mul4(v[2], v[3]);
+                    prod = mul4(p01, p23);
                 } else {
-                    prod = mul4(p01[c], v[2]);
+                    prod = mul4(p01, v[2]);
                 }
             } else {
                 prod = v[0];
@@ -154,24 +131,23 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
             // upd[k] = y prod_{l != k} A_l(i_l, cols)
             float4 upd[D];
             if constexpr (kPairs) {
-                const float4* rr = r[c];
                 if constexpr (D == 4) {
-                    const float4 yp23 = scale4(y, p23[c]), yp01 = scale4(y, p01[c]);
-                    upd[0] = mul4(yp23, rr[1]);
-                    upd[1] = mul4(yp23, rr[0]);
-                    upd[2] = mul4(yp01, rr[3]);
-                    upd[3] = mul4(yp01, rr[2]);
+                    const float4 yp23 = scale4(y, p23), yp01 = scale4(y, p01);
+                    upd[0] = mul4(yp23, r[1]);
+                    upd[1] = mul4(yp23, r[0]);
+                    upd[2] = mul4(yp01, r[3]);
+                    upd[3] = mul4(yp01, r[2]);
                 } else {
-                    const float4 yr2 = scale4(y, rr[2]);
-                    upd[0] = mul4(yr2, rr[1]);
-                    upd[1] = mul4(yr2, rr[0]);
-                    upd[2] = scale4(y, p01[c]);
+                    const float4 yr2 = scale4(y, r[2]);
+                    upd[0] = mul4(yr2, r[1]);
+                    upd[1] = mul4(yr2, r[0]);
+                    upd[2] = scale4(y, p01);
                 }
             } else {
                 float4 rc[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    if (kKeep) rc[k] = r[kKeep ? c : 0][k];
+                    if (kKeep) rc[k] = r[k];
                     else rc[k] = k < d ? row4(k, ix[k], col) : make_float4(1.f, 1.f, 1.f, 1.f);
                 }
                 // prefix and suffix products
