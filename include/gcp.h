@@ -274,8 +274,9 @@ gcp_status gcp_sample(gcp_handle *h, const gcp_sampling *S, const gcp_samples *o
 
 /* Performs every library-owned allocation and host read that gcp_sample and
    gcp_grad would make for this spec (the stratified sampler's nonzero-key
-   hash, candidate scratch and zero list; for the observed-entry sampler the
-   count of entries of nonzero weight, read back to the host once), so that
+   hash, the tile words of its ordered compaction and the zero list; for the
+   observed-entry sampler the count of entries of nonzero weight, read back
+   to the host once), so that
    later calls with the same or a smaller spec allocate nothing, wait for
    nothing and can be captured in a CUDA graph.  Waits for the stream.
    Errors: as gcp_sample; GCP_ERR_INVALID_ARG when no entry has a nonzero
@@ -324,8 +325,8 @@ gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
    FP32 summation order): this is the sample-parallel split of one problem
    across GPUs, each GPU taking one range and a sum of G across GPUs
    following -- the parallel use of sampling that Section 6 points to.  With
-   a stratified spec each call runs the whole ordered zero pass (the zeros
-   of a range depend on every earlier candidate) and then takes its range.
+   a stratified spec each call examines every candidate tile (the zeros of
+   a range depend on every earlier candidate) and walks only its range.
    stream_dev, replica slabs, allocation and overlap rules as for gcp_grad.
    Errors: GCP_ERR_INVALID_ARG (S NULL, first < 0, count < 0, or
    first + count beyond gcp_sample_count(S)) and as gcp_grad. */
@@ -411,8 +412,11 @@ gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
 /* One GCP-Adam iteration (Alg. 4, inner loop body): the sampled gradient of
    gcp_grad for spec S (with stream_dev as there) followed by the Adam step
    of gcp_adam_step, fused so that replica slabs of the gradient are folded
-   inside the Adam kernel (two kernel launches per iteration, three with a
-   stratified spec's zero pass counted as one).  G must be zero on entry and
+   inside the Adam kernel (two kernel launches per iteration; a stratified
+   spec's zeros are made inside the gradient kernel, or by a third launch
+   with gcp_tuning.zero_pass = 1; with tail_work = 1 a small factor set's
+   Adam step is taken by the gradient kernel's last blocks and the iteration
+   is one launch).  G must be zero on entry and
    is left zero; B, C, state as for gcp_adam_step.  Same results as
    gcp_grad followed by gcp_adam_step up to the summation order.  Between
    the two kernels state->t has already advanced (the gradient kernel does
