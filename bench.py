@@ -985,7 +985,8 @@ def main():
     ap.add_argument("--profile", type=int, default=0, metavar="ITERS",
                     help="only set up the benchmark's run and take ITERS eager GCP-Adam iterations, then exit "
                          "(the command profiled with ncu; prints one line of timing); with --form count, ITERS "
-                         "gcp_grad calls on the count tensor instead")
+                         "gcp_grad calls on the count tensor instead; with --form dense100, ITERS iterations on "
+                         "the dense 100^4 tensor")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -1019,15 +1020,18 @@ def profile_arm(args):
     """The benchmark's run set up as in ours_arm (no autotuning: the shape
     given by --tuning, else the automatic one), then --profile eager
     iterations: a short, bounded command for ncu.  With --form count, the
-    count tensor's gcp_grad call instead (--profile calls)."""
+    count tensor's gcp_grad call instead (--profile calls); with --form
+    dense100, eager GCP-Adam iterations on the dense 100^4 tensor."""
     import torch
     from paper_1906_01687_gb300 import gcp
     from paper_1906_01687_gb300.adam import GcpAdam
     stream = torch.cuda.Stream()
     if args.form == "count":
         return profile_count(args, torch, gcp, stream)
+    if args.form == "dense100":
+        return profile_dense100(args, torch, gcp, stream)
     if args.form:
-        raise SystemExit("--profile takes no --form but count")
+        raise SystemExit("--profile takes no --form but count and dense100")
     idx, A0, _ = large_input()
     XT = gcp.DataTensor.coo(DIMS, idx, None)
     with torch.cuda.stream(stream):
@@ -1074,6 +1078,29 @@ def profile_count(args, torch, gcp, stream):
     print(json.dumps({"profile": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
                       "calls": args.profile, "us_per_call": t_call * 1e6, "grad_kernel_us": ms * 1e3 / max(n, 1),
                       "launch": gcp.gcp_get_launch(h, F, p + q)}), flush=True)
+    return 0
+
+
+def profile_dense100(args, torch, gcp, stream):
+    """--profile eager GCP-Adam iterations (gradient + Adam launches) on the
+    dense 100^4 tensor, rank 10, Gaussian, uniform 1e5 draws, in the shape
+    --tuning gives, with the gradient kernel's own event time."""
+    from paper_1906_01687_gb300 import synth
+    from paper_1906_01687_gb300.adam import GcpAdam
+    dims, rank, s = (100, 100, 100, 100), 10, 100_000
+    X32, _ = synth.dense_100_4()
+    A0 = synth.initial_guess(dims, rank, seed=3, target_norm=float(np.linalg.norm(X32)))
+    XT = gcp.DataTensor.dense(X32, device=stream.device)
+    with torch.cuda.stream(stream):
+        run = GcpAdam(XT, A0, gcp.LOSS_GAUSSIAN, gcp.SAMPLER_UNIFORM, 0, s, 0, 100_000, seed=1687, est_seed=7,
+                      alpha=1e-3, tau=100, kappa=1_000_000, stream=stream)
+        if args.tuning:
+            gcp.gcp_set_tuning(run.h, **json.loads(args.tuning))
+    iter_s = time_iterations(torch, gcp, run.h, run.F, run.loss, run.spec, stream, iters=50)
+    mean_s, n, adam_s = time_grad_kernel(torch, gcp, run.h, run.iteration, stream, launches=args.profile)
+    print(json.dumps({"profile": "dense-100x100x100x100-r10-gaussian-uniform-s1e5", "iterations": args.profile,
+                      "iteration_us_in_graph": iter_s * 1e6, "grad_kernel_us": mean_s * 1e6,
+                      "adam_kernel_us": adam_s * 1e6, "launch": gcp.gcp_get_launch(run.h, run.F, s)}), flush=True)
     return 0
 
 
