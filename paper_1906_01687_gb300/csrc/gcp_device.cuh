@@ -234,25 +234,23 @@ __device__ __forceinline__ float sum4(float4 a) { return (a.x + a.y) + (a.z + a.
 __device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
 // Sum of reps replica chunks r[0], r[stride], ... (each then zeroed), added
-// in replica order.  The first 16 loads are all issued before any store, so
-// a fold of up to 16 replicas costs one round trip to L2; further replicas
-// follow one at a time.
+// in replica order, in rounds of 16: every load of a round is issued before
+// any is used, so a fold costs one round trip to L2 per 16 replicas.
 __device__ __forceinline__ float4 fold_replicas(float4* r, uint32_t reps, uint64_t stride)
 {
     constexpr int kWide = 16;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 v[kWide];
-#pragma unroll
-    for (int q = 0; q < kWide; ++q) v[q] = static_cast<uint32_t>(q) < reps ? r[q * stride] : zero;
     float4 acc = zero;
+#pragma unroll 1
+    for (uint32_t q0 = 0; q0 < reps; q0 += kWide) {
+        float4 v[kWide];
 #pragma unroll
-    for (int q = 0; q < kWide; ++q) acc = add4(acc, v[q]);
+        for (int q = 0; q < kWide; ++q) v[q] = q0 + q < reps ? r[(q0 + q) * stride] : zero;
 #pragma unroll
-    for (int q = 0; q < kWide; ++q)
-        if (static_cast<uint32_t>(q) < reps) r[q * stride] = zero;
-    for (uint32_t q = kWide; q < reps; ++q) {
-        acc = add4(acc, r[q * stride]);
-        r[q * stride] = zero;
+        for (int q = 0; q < kWide; ++q) acc = add4(acc, v[q]);
+#pragma unroll
+        for (int q = 0; q < kWide; ++q)
+            if (q0 + q < reps) r[(q0 + q) * stride] = zero;
     }
     return acc;
 }
