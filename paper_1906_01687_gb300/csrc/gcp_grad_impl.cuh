@@ -201,8 +201,9 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
 // The kernel's tail work, done by the last a.tail_blocks blocks to finish
 // their draws instead of a launch of its own: the fold of gcp_grad's replica
 // slabs into the caller's G_k, or (tail_adam, gcp_iteration with a small
-// factor set) the whole Adam step of Alg. 4 with the fold inside it.  Every
-// thread fences its own reductions before its block counts itself done; a
+// factor set) the whole Adam step of Alg. 4 with the fold inside it.  After a
+// block barrier one thread fences (a release that covers the block's
+// reductions) and counts the block done; a
 // tail block then waits (bounded: kSpinLimit polls, then GCP_ERR_TIMEOUT and
 // no tail work) until every block has counted itself, and reads through L2
 // (ld.cg) what other blocks wrote.  Fold: four lanes share a float4 element
@@ -217,11 +218,11 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
 static __device__ __noinline__ void fold_tail(const GradArgs& a)
 {
     __shared__ int tail_rank, tail_ok;
-    __threadfence();
     __syncthreads();
     const unsigned grid = gridDim.x;
     const unsigned K = static_cast<unsigned>(a.tail_blocks);
     if (threadIdx.x == 0) {
+        __threadfence();  // after the barrier: releases the whole block's reductions (cumulative)
         const unsigned ticket = atomicAdd(a.tail_done, 1u);
         const int rank = static_cast<int>(ticket) - static_cast<int>(grid - K);
         int ok = 1;
