@@ -961,10 +961,10 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
         for (int m = 0; m < fold.nmodes; ++m) loads += (fold.off4[m + 1] - fold.off4[m]) * fold.reps[m];
         const int64_t blocks = std::max<int64_t>(1, (loads + 8 * sh.block - 1) / (8 * sh.block));
         if (blocks <= 64 && blocks <= grid) {
-            a.tail = fold;
-            a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
-            a.tail_blocks = static_cast<int32_t>(blocks);
-            a.tail_status = h->d_status;
+            a.tail.fold = fold;
+            a.tail.done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
+            a.tail.blocks = static_cast<int32_t>(blocks);
+            a.tail.status = h->d_status;
         }
     }
     // the Adam step of gcp_iteration by the gradient kernel's last blocks (four
@@ -979,11 +979,11 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
         ad.t_advanced = 1;
         const int64_t blocks = std::max<int64_t>(1, (ad.mt.off4[h->X.d] * 4 + sh.block - 1) / sh.block);
         if (blocks <= 64 && blocks <= grid) {
-            a.adam = ad;
-            a.tail_adam = 1;
-            a.tail_blocks = static_cast<int32_t>(std::max<int64_t>(1, blocks));
-            a.tail_done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
-            a.tail_status = h->d_status;
+            a.tail.adam = ad;
+            a.tail.adam_on = 1;
+            a.tail.blocks = static_cast<int32_t>(std::max<int64_t>(1, blocks));
+            a.tail.done = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->d_status) + 16);
+            a.tail.status = h->d_status;
             if (adam_fused) *adam_fused = true;
         }
     }
@@ -996,7 +996,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
         GCP_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s));
         h->prof_used++;
     }
-    if (!deferred_fold && fold.nmodes > 0 && a.tail.nmodes == 0) {
+    if (!deferred_fold && fold.nmodes > 0 && a.tail.blocks == 0) {
         const int64_t total4 = fold.off4[fold.nmodes];
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((total4 + 255) / 256, int64_t(h->num_sms) * 8)));
         GCP_CUDA_TRY(launch_fold(fold, grid, s));

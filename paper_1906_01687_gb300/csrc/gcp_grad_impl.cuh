@@ -198,9 +198,9 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
     }
 }
 
-// The kernel's tail work, done by the last a.tail_blocks blocks to finish
+// The kernel's tail work, done by the last tail.blocks blocks to finish
 // their draws instead of a launch of its own: the fold of gcp_grad's replica
-// slabs into the caller's G_k, or (tail_adam, gcp_iteration with a small
+// slabs into the caller's G_k, or (adam_on, gcp_iteration with a small
 // factor set) the whole Adam step of Alg. 4 with the fold inside it.  After a
 // block barrier one thread fences (a release that covers the block's
 // reductions) and counts the block done; a
@@ -215,48 +215,24 @@ __device__ __forceinline__ void walk_batch(const GradArgs& a, Draw<D>& my, float
 // still to run always find room.  The last tail block to finish clears both
 // counters for the next launch (and, after an Adam step, advances the
 // iteration count).
-static __device__ __noinline__ void fold_tail(const GradArgs& a)
+static __device__ __noinline__ void tail_work(const TailArgs& t, int rank, bool tail_ok)
 {
-    __shared__ int tail_rank, tail_ok;
-    __syncthreads();
-    const unsigned grid = gridDim.x;
-    const unsigned K = static_cast<unsigned>(a.tail_blocks);
-    if (threadIdx.x == 0) {
-        __threadfence();  // after the barrier: releases the whole block's reductions (cumulative)
-        const unsigned ticket = atomicAdd(a.tail_done, 1u);
-        const int rank = static_cast<int>(ticket) - static_cast<int>(grid - K);
-        int ok = 1;
-        if (rank >= 0) {
-            int spins = 0;
-            while (*reinterpret_cast<volatile unsigned int*>(a.tail_done) < grid) {
-                if (++spins > kSpinLimit) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        tail_rank = rank;
-        tail_ok = ok;
-    }
-    __syncthreads();
-    const int rank = tail_rank;
-    if (rank < 0) return;
-    if (tail_ok && a.tail_adam) {
+    const unsigned K = static_cast<unsigned>(t.blocks);
+    if (tail_ok && t.adam_on) {
         __threadfence();
-        const AdamArgs& ad = a.adam;
+        const AdamArgs& ad = t.adam;
         const uint32_t total4 = static_cast<uint32_t>(ad.mt.off4[ad.mt.d]);
         const uint32_t gthread = static_cast<uint32_t>(rank) * blockDim.x + threadIdx.x;
         const volatile gcp_adam_state* st = ad.st;
-        const int64_t t = st->t;  // advanced by block 0 at the kernel's start
+        const int64_t step = st->t;  // advanced by block 0 at the kernel's start
         const float alpha = st->alpha;
         const int done = st->done;
         AdamElem e;
         adam_prepare(ad, gthread / kParts, total4, gthread % kParts, e);
-        adam_elements(ad, gthread, K * blockDim.x, e, t, alpha, done);
+        adam_elements(ad, gthread, K * blockDim.x, e, step, alpha, done);
     } else if (tail_ok) {
         __threadfence();
-        const FoldArgs& f = a.tail;
+        const FoldArgs& f = t.fold;
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         const int sub = threadIdx.x & 3;
         const unsigned quad = 0xFu << (threadIdx.x & 28);
@@ -295,15 +271,15 @@ static __device__ __noinline__ void fold_tail(const GradArgs& a)
             }
         }
     } else if (threadIdx.x == 0) {
-        set_status(a.tail_status, GCP_ERR_TIMEOUT);
+        set_status(t.status, GCP_ERR_TIMEOUT);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(a.tail_done + 1, 1u) == K - 1) {
-            if (a.tail_adam) a.adam.st->iter += 1;
-            a.tail_done[0] = 0u;
-            a.tail_done[1] = 0u;
+        if (atomicAdd(t.done + 1, 1u) == K - 1) {
+            if (t.adam_on) t.adam.st->iter += 1;
+            t.done[0] = 0u;
+            t.done[1] = 0u;
         }
     }
 }
@@ -482,7 +458,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     // has triggered, long before this one ends: block 0 publishes the next
     // launch's stream prediction before it triggers (fenced, so that the next
     // launch's early reads see it).  Otherwise it is written at the end.
-    if (a.tail_adam && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (a.tail.adam_on && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0) {
         *reinterpret_cast<volatile int64_t*>(a.stream_pred) =
             *reinterpret_cast<const volatile int64_t*>(a.dr.stream_dev) + 1;
         __threadfence();
@@ -649,7 +625,7 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
     }
 
     // the prediction for the next launch that reads its stream word from memory
-    if (!a.tail_adam && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
+    if (!a.tail.adam_on && a.dr.stream_dev && a.stream_pred && blockIdx.x == 0 && threadIdx.x == 0)
         *reinterpret_cast<volatile int64_t*>(a.stream_pred) = static_cast<int64_t>(actual + 1);
     if (a.smem_mask != 0) {
         __syncthreads();
@@ -666,7 +642,41 @@ __global__ void __launch_bounds__(256, grad_min_blocks<D, L, NC>(LAYOUT)) grad_k
             }
         }
     }
-    if (a.tail_blocks > 0) fold_tail(a);
+    if (a.tail.blocks > 0) {
+        // count this block done (after a block barrier one thread fences: a
+        // release that covers the block's reductions); the last tail.blocks to
+        // count wait, bounded, for every block, then do the tail work
+        __shared__ int tail_rank, tail_ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned grid = gridDim.x;
+            __threadfence();
+            const unsigned ticket = atomicAdd(a.tail.done, 1u);
+            const int rank = static_cast<int>(ticket) - static_cast<int>(grid - static_cast<unsigned>(a.tail.blocks));
+            int ok = 1;
+            if (rank >= 0) {
+                int spins = 0;
+                while (*reinterpret_cast<volatile unsigned int*>(a.tail.done) < grid) {
+                    if (++spins > kSpinLimit) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            tail_rank = rank;
+            tail_ok = ok;
+        }
+        __syncthreads();
+        if (tail_rank >= 0) {
+            // the tail's arguments in shared memory: a called function reaches
+            // the launch parameters only through generic loads, which are slow
+            __shared__ TailArgs s_tail;
+            if (threadIdx.x == 0) s_tail = a.tail;
+            __syncthreads();
+            tail_work(s_tail, tail_rank, tail_ok != 0);
+        }
+    }
 }
 
 #define GCP_GRAD_CONFIGS(X) \

@@ -110,6 +110,18 @@ struct AdamArgs {
     int32_t t_advanced;
 };
 
+// Work the last `blocks` blocks of a gradient launch to finish take on after
+// every block's reductions (the kernel tail): fold `fold`'s replica slabs
+// into G, or (adam_on) take the Adam step `adam`.
+struct TailArgs {
+    FoldArgs fold;
+    AdamArgs adam;
+    unsigned int* done;   // [0] blocks finished, [1] tail blocks finished (zero between launches)
+    int32_t* status;      // status word (a wait that ran out)
+    int32_t blocks;       // 0: no tail work; else 1..64
+    int32_t adam_on;
+};
+
 struct GradArgs {
     DrawArgs dr;
     int32_t ld, rank, loss, smem_floats;
@@ -125,12 +137,7 @@ struct GradArgs {
     int64_t* stream_pred;          // handle word: predicted stream of the next launch with dr.stream_dev
     gcp_adam_state* st_advance;    // gcp_iteration: the Adam state whose step count t this launch advances
     ZeroTileArgs zt;               // layout 3: the zeros made in this launch (dr.n_total then ends the nonzeros)
-    FoldArgs tail;                 // nmodes > 0: the last tail_blocks blocks fold these replica slabs into G
-    unsigned int* tail_done;       //   [0] blocks finished, [1] folding blocks finished (zero between launches)
-    int32_t tail_blocks;           //   1..64
-    int32_t* tail_status;          //   status word (a wait that ran out)
-    int32_t tail_adam;             // 1 (gcp_iteration): those blocks take the Adam step (adam) instead
-    AdamArgs adam;
+    TailArgs tail;                 // blocks > 0: work the last blocks to finish do instead of a launch
 };
 
 struct LossArgs {
