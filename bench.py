@@ -840,12 +840,12 @@ def form_count(torch, gcp, stream, peak):
     SOe = oracle.sample(XO, oracle.STRATIFIED, p, q, 7, gcp.STREAM_EST)
     F_ref = oracle.loss_estimate(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SOe)
     # the call's algorithmic bytes: nonzero draws read a 32-byte record; the
-    # zero pass probes the 8-byte hash slot of ~1.1 candidates per accepted
-    # zero (rho = 1.1, 1.5% of entries are nonzeros) and writes 4d bytes of
-    # indices that the gradient reads back
+    # zero draws probe the 8-byte hash slot of ~1.1 candidates per accepted
+    # zero (rho = 1.1, 1.5% of entries are nonzeros); no zero list is needed
+    # (the gradient kernel walks the accepted candidates it draws)
     omega = float(np.prod(dims))
     cand_per_zero = 1.1 * omega / (omega - len(vals))
-    zero_extra = 2 * 4 * len(dims) + 8 * cand_per_zero
+    zero_extra = 8 * cand_per_zero
     call_bytes = {b_f: grad_bytes(p, q, len(dims), rank, b_f, nz_extra=32, zero_extra=zero_extra) for b_f in (4, 2)}
     out = {"workload": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
            "metric": "entries/s of gcp_grad (zero pass + gradient)"}
