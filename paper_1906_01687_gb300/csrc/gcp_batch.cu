@@ -187,7 +187,7 @@ __device__ __forceinline__ void batch_grad_item(const BatchArgs& a, const int64_
     }
 }
 
-__global__ void __launch_bounds__(256) batch_grad_kernel(const BatchArgs a)
+__global__ void __launch_bounds__(256, 4) batch_grad_kernel(const BatchArgs a)
 {
     pdl_wait();
     pdl_trigger();
