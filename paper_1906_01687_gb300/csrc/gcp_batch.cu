@@ -276,7 +276,7 @@ __device__ __forceinline__ void batch_adam_element(const BatchDesc& P, int64_t p
 
 // Adam of every problem: per-problem bias corrections, learning rate and
 // done flag are read once per block into shared memory.
-__global__ void __launch_bounds__(256) batch_adam_kernel(const BatchArgs a)
+__global__ void __launch_bounds__(256, 3) batch_adam_kernel(const BatchArgs a)
 {
     pdl_wait();
     pdl_trigger();
