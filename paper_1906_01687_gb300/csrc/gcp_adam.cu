@@ -146,45 +146,61 @@ __global__ void __launch_bounds__(64) adam_split_kernel(const AdamArgs a)
 
 // The same step for large factor sets (bandwidth-bound): every thread takes
 // kStreamU float4 elements per round, a block's threads adjacent elements
-// (coalesced), with the loads of all of them -- G, its replica slabs, A, B, C
-// -- issued before any is used.  Replicated modes fold their slabs in the
-// thread that owns the element.  t was advanced by the gradient kernel;
-// block 0 advances iter, which no Adam block reads.
+// (coalesced), with the loads of all of them -- A, B, C, then G -- issued
+// before any is used; the first round's A, B, C before the dependency wait,
+// so that blocks made resident while the gradient kernel drains already
+// stream them.  Replicated modes fold their slabs in the thread that owns
+// the element.  t was advanced by the gradient kernel; block 0 advances
+// iter, which no Adam block reads.
 constexpr int kStreamU = 4;
 constexpr int kStreamBlock = 256;
 
 __global__ void __launch_bounds__(kStreamBlock, 2) adam_stream_kernel(const AdamArgs a)
 {
-    pdl_wait();
-    pdl_trigger();
     const ModeTable& mt = a.mt;
-    const float alpha = a.st->alpha;
-    const int done = a.st->done;
-    const float n = static_cast<float>(a.st->t);
-    const float ic1 = inv_bias_correction(a.beta1, n);
-    const float ic2 = inv_bias_correction(a.beta2, n);
-    const bool inside = a.eps_inside_sqrt != 0;
     const uint32_t total4 = static_cast<uint32_t>(mt.off4[mt.d]);
     const uint32_t ld4 = static_cast<uint32_t>(mt.ld) / 4;
     const uint32_t round = gridDim.x * kStreamBlock * kStreamU;
-    for (uint32_t base = blockIdx.x * kStreamBlock * kStreamU + threadIdx.x; base < total4; base += round) {
-        int k[kStreamU];
-        uint32_t loc[kStreamU];
-        float4 g[kStreamU], A4[kStreamU], B4[kStreamU], C4[kStreamU];
+    int k[kStreamU];
+    uint32_t loc[kStreamU];
+    float4 g[kStreamU], A4[kStreamU], B4[kStreamU], C4[kStreamU];
+    // an element's mode and position and its A, B, C: the first round's are
+    // loaded before the dependency wait -- A, B, C and the scalars alpha and
+    // done were last written two launches back or earlier (the previous
+    // iteration's Adam step, an epoch kernel), complete before the gradient
+    // kernel that precedes this one passed its own wait
+    auto prepare = [&](uint32_t base) {
 #pragma unroll
         for (int u = 0; u < kStreamU; ++u) {
             const uint32_t i4 = base + static_cast<uint32_t>(u) * kStreamBlock;
             k[u] = 0;
             loc[u] = 0;
-            g[u] = A4[u] = B4[u] = C4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            A4[u] = B4[u] = C4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (i4 < total4) {
                 k[u] = mode_of(mt, i4);
                 loc[u] = i4 - static_cast<uint32_t>(mt.off4[k[u]]);
-                g[u] = reinterpret_cast<const float4*>(mt.G[k[u]])[loc[u]];
                 A4[u] = reinterpret_cast<const float4*>(mt.A[k[u]])[loc[u]];
                 B4[u] = reinterpret_cast<const float4*>(mt.B[k[u]])[loc[u]];
                 C4[u] = reinterpret_cast<const float4*>(mt.C[k[u]])[loc[u]];
             }
+        }
+    };
+    const uint32_t base0 = blockIdx.x * kStreamBlock * kStreamU + threadIdx.x;
+    prepare(base0);
+    const float alpha = a.st->alpha;
+    const int done = a.st->done;
+    pdl_wait();
+    pdl_trigger();
+    const float n = static_cast<float>(a.st->t);  // advanced by the gradient kernel
+    const float ic1 = inv_bias_correction(a.beta1, n);
+    const float ic2 = inv_bias_correction(a.beta2, n);
+    const bool inside = a.eps_inside_sqrt != 0;
+    for (uint32_t base = base0; base < total4; base += round) {
+        if (base != base0) prepare(base);
+#pragma unroll
+        for (int u = 0; u < kStreamU; ++u) {
+            const uint32_t i4 = base + static_cast<uint32_t>(u) * kStreamBlock;
+            g[u] = i4 < total4 ? reinterpret_cast<const float4*>(mt.G[k[u]])[loc[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kStreamU; ++u) {
