@@ -795,9 +795,11 @@ def sweep_draws(torch, gcp, run, stream, peak, rank, sizes=(100_000, 1_000_000, 
     kernels."""
     out = []
     F = gcp.Factors([a[:, :rank] for a in run.F.A])
-    # the tuned shape without its grid (a grid fitted to 1e5 draws would starve larger launches)
+    # the tuned walk (lanes, chunks, block, layout) with the grid and the
+    # replica slabs automatic: both were fitted to 1e5 draws per iteration
     best = dict((run.tuned or {}).get("best") or {"early_draws": 1})
-    best.pop("grid_blocks", None)
+    for key in ("grid_blocks", "max_replicas", "replica_target"):
+        best.pop(key, None)
     gcp.gcp_set_tuning(run.h, **best)
     for s in sizes:
         spec = gcp.Sampling(gcp.SAMPLER_UNIFORM, 0, s, 99, 0)
