@@ -143,11 +143,20 @@ def autotune(h, F, loss, spec, configs: Optional[Iterable[dict]] = None, launche
     results = []
     stream = stream or torch.cuda.current_stream()
     cap = side_stream(stream) if graph else None
+    seen = set()
     for cfg in configs if configs is not None else candidates(F.rank):
         try:
             gcp.gcp_set_tuning(h, **cfg)
         except gcp.GcpError:
             continue
+        # candidates that come out as the same launch (e.g. a warp-level
+        # pre-reduction with no mode short enough for it) are timed once
+        launch = gcp.gcp_get_launch(h, F, spec.count())
+        key = (tuple(sorted((k, tuple(v) if isinstance(v, list) else v) for k, v in launch.items())),
+               cfg.get("tail_work", 0), cfg.get("zero_pass", 0))
+        if key in seen:
+            continue
+        seen.add(key)
         t = time_grad(h, F, loss, spec, launches, stream, call, graph, cap)
         results.append((t, cfg))
         if log:
