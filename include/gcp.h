@@ -296,14 +296,18 @@ gcp_status gcp_reserve(gcp_handle *h, const gcp_sampling *S, gcp_stream_t stream
    j < rank (the padding columns of G are not written).
    Exactly one of S and list is non-NULL:
      S    -- draws generated inside the kernel from the spec (fused
-             sampling, nothing materialised except stratified zeros, which
-             go through library scratch);
+             sampling, nothing materialised; stratified zeros are picked
+             inside the kernel too -- tiles of candidates, ordered by
+             decoupled look-back through library scratch -- or, with
+             gcp_tuning.zero_pass = 1 or 5 to 8 modes, listed first by a
+             separate pass);
      list -- a materialised list (gcp_sample output or the caller's own).
    stream_dev (device, nullable): if non-NULL the Philox stream word is read
    from *stream_dev on the device at run time instead of S->stream (used by
    graph-replayed epochs with &state->iter).
    Modes whose rows are hit often accumulate first in library-owned replica
-   slabs that a second kernel folds into G (and re-zeroes); the slabs are
+   slabs that a second kernel (or, with gcp_tuning.tail_work = 1, the
+   gradient kernel's last blocks) folds into G and re-zeroes; the slabs are
    allocated on the first call that needs them (cudaMalloc: make that call
    before any stream capture) and are shared by every call on this handle,
    so calls on one handle must not overlap on the GPU.
