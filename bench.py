@@ -70,13 +70,26 @@ def adam_bytes(dims, rank, bf16=False):
     return sum(dims) * rank * (32 + (2 if bf16 else 0))
 
 
-def kernel_source_hash():
+def code_hash(texts):
+    """Hash of C++/CUDA source texts with comments and blank space removed:
+    a change of code changes it, a change of comments does not."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1906_01687_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+    for text in texts:
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash():
+    """code_hash of the gradient kernel's sources: the key of the recorded traffic."""
+    texts = []
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1906_01687_gb300", "csrc", name)) as f:
+            texts.append(f.read())
+    return code_hash(texts)
 
 
 def recorded_traffic(launch, path=None):

@@ -73,3 +73,14 @@ def test_threaded_oracle_gradient_equals_one_call():
         f = bench.oracle_loss_threads(dims, A, oracle.GAUSSIAN, S, cores)
         assert abs(f - oracle.loss_estimate(dims, A, oracle.GAUSSIAN, S)) <= 1e-12 * abs(f)
     assert bench.host_cores() >= 1
+
+
+def test_code_hash_ignores_comments_not_code():
+    import bench
+    base = "int f(int x) {\n    return x + 1;  // one more\n}\n/* a note */\n"
+    h = bench.code_hash([base])
+    assert bench.code_hash([base.replace("// one more", "// the successor")]) == h
+    assert bench.code_hash([base.replace("/* a note */", "/* another\n   note */")]) == h
+    assert bench.code_hash([base.replace("    return", "\treturn")]) == h
+    assert bench.code_hash([base.replace("x + 1", "x + 2")]) != h
+    assert bench.code_hash([base, base]) != h
