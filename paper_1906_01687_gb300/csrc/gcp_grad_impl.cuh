@@ -11,13 +11,21 @@
 // L * NC * 4 >= rank).  With group_draws the warp instead takes 32 / L draws
 // at a time, one per group, each group's lanes computing the same
 // descriptor: L times more warps for the same draws, for small launches
-// that are bound by latency rather than by instructions.  m_i is reduced across the group with shuffles; the
-// row updates go either to shared-memory accumulators (modes whose whole G_k
-// fits and is hit often: flushed once per CTA) or straight to global memory
-// with 16-byte vector atomics (red.global.add.v4.f32).  A mode whose rows
-// are hit many times per launch adds into one of several replica slabs
+// that are bound by latency rather than by instructions.  m_i is reduced
+// across the group with shuffles; the row updates go either to shared-memory
+// accumulators (modes whose whole G_k fits and is hit often: flushed once
+// per CTA) or straight to global memory with 16-byte reductions
+// (red.global.add.v4.f32), optionally summed first across the groups of a
+// warp step that update the same 16 bytes (layouts 4 and 5).  A mode whose
+// rows are hit many times per launch adds into one of several replica slabs
 // (CTA b into replica b % reps), which keeps same-address contention at L2
-// low; a fold kernel then sums the replicas into G_k.
+// low; a fold kernel (or the kernel's own last blocks) then sums the
+// replicas into G_k.
+//
+// Stratified zeros (layouts 3 and 5).  The grid's first blocks draw the
+// zero candidates of Alg. 2 themselves, a tile of blockDim.x per block, and
+// keep the first q accepted in candidate order by decoupled look-back
+// (zero_tiles_block); the other blocks walk the nonzero draws.
 //
 // Early descriptors.  With a.early the first batch of each warp is drawn
 // before the dependency wait (griddepcontrol.wait), while the preceding
