@@ -64,6 +64,18 @@ def grad_bytes(p, q, d, rank, b_f, nz_extra=RECORD_BYTES, zero_extra=0):
     return p * (nz_extra + row_bytes(d, rank, b_f)) + q * (zero_extra + row_bytes(d, rank, b_f))
 
 
+def stratified_call_bytes(dims, nnz, p, q, rank, b_f, rho=1.1):
+    """Algorithmic bytes of a stratified gcp_grad call (Alg. 2): nonzero draws
+    read a 32-byte record (4 indices and the value, padded); each accepted
+    zero costs rho * omega / zeta candidates' 8-byte hash probes (zeta =
+    omega - nnz zeros); no zero list is read or written (the gradient kernel
+    walks the accepted candidates it draws); every draw gathers and updates
+    its d rows."""
+    omega = float(np.prod(dims))
+    cand_per_zero = rho * omega / (omega - nnz)
+    return grad_bytes(p, q, len(dims), rank, b_f, nz_extra=32, zero_extra=8 * cand_per_zero)
+
+
 def adam_bytes(dims, rank, bf16=False):
     """Algorithmic bytes of one Adam step: A, B, C, G read and written (32 B
     per factor entry), plus the BF16 copy written."""
@@ -854,14 +866,7 @@ def form_count(torch, gcp, stream, peak):
     est_spec = gcp.Sampling(gcp.SAMPLER_STRATIFIED, p, q, 7, gcp.STREAM_EST)
     SOe = oracle.sample(XO, oracle.STRATIFIED, p, q, 7, gcp.STREAM_EST)
     F_ref = oracle.loss_estimate(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SOe)
-    # the call's algorithmic bytes: nonzero draws read a 32-byte record; the
-    # zero draws probe the 8-byte hash slot of ~1.1 candidates per accepted
-    # zero (rho = 1.1, 1.5% of entries are nonzeros); no zero list is needed
-    # (the gradient kernel walks the accepted candidates it draws)
-    omega = float(np.prod(dims))
-    cand_per_zero = 1.1 * omega / (omega - len(vals))
-    zero_extra = 8 * cand_per_zero
-    call_bytes = {b_f: grad_bytes(p, q, len(dims), rank, b_f, nz_extra=32, zero_extra=zero_extra) for b_f in (4, 2)}
+    call_bytes = {b_f: stratified_call_bytes(dims, len(vals), p, q, rank, b_f) for b_f in (4, 2)}
     out = {"workload": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
            "metric": "entries/s of gcp_grad (zero pass + gradient)"}
     for name, bf16 in (("fp32", False), ("bf16", True)):

@@ -84,3 +84,18 @@ def test_code_hash_ignores_comments_not_code():
     assert bench.code_hash([base.replace("    return", "\treturn")]) == h
     assert bench.code_hash([base.replace("x + 1", "x + 2")]) != h
     assert bench.code_hash([base, base]) != h
+
+
+def test_stratified_call_bytes():
+    """The count tensor's call: 32-byte records, ~1.12 hash probes of 8 B per
+    zero, 160 B of rows gathered and 160 B updated per draw (rank 10, 4 modes,
+    FP32); BF16 rows gather half."""
+    import bench
+    dims, nnz = (6186, 24, 77, 32), 5_330_673
+    omega = 6186 * 24 * 77 * 32
+    probes = 1.1 * omega / (omega - nnz)
+    fp32 = bench.stratified_call_bytes(dims, nnz, 100_000, 100_000, 10, 4)
+    assert abs(fp32 - (100_000 * (32 + 320) + 100_000 * (8 * probes + 320))) < 1e-3
+    assert 68.0e6 < fp32 < 68.2e6
+    bf16 = bench.stratified_call_bytes(dims, nnz, 100_000, 100_000, 10, 2)
+    assert abs((fp32 - bf16) - 200_000 * 4 * 10 * 2) < 1e-3
