@@ -854,7 +854,7 @@ def count_problem(gcp):
 def form_count(torch, gcp, stream, peak):
     """FP32 vs BF16 factor storage on the count tensor (6186x24x77x32, 5.33M
     nonzeros, rank 10, Poisson-log, stratified 1e5 + 1e5 draws): the whole
-    gcp_grad call (ordered zero pass + gradient), its roofline fraction, and
+    gcp_grad call (ordered zero rejection + gradient + fold), its roofline fraction, and
     the gradient's and the loss estimate's errors against the FP64 oracle (at
     the FP32 factors) on the same draws."""
     import oracle
@@ -868,7 +868,7 @@ def form_count(torch, gcp, stream, peak):
     F_ref = oracle.loss_estimate(dims, [a.astype(np.float64) for a in A], oracle.POISSON_LOG, SOe)
     call_bytes = {b_f: stratified_call_bytes(dims, len(vals), p, q, rank, b_f) for b_f in (4, 2)}
     out = {"workload": "coo-6186x24x77x32-nnz5330673-r10-poissonlog-stratified-1e5+1e5",
-           "metric": "entries/s of gcp_grad (zero pass + gradient)"}
+           "metric": "entries/s of gcp_grad (zero rejection + gradient + fold)"}
     for name, bf16 in (("fp32", False), ("bf16", True)):
         F = gcp.Factors(A, bf16=bf16)
         tuned = autotune(h, F, gcp.LOSS_POISSON_LOG, spec, launches=10, stream=stream,
