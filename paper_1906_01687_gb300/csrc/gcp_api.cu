@@ -891,7 +891,7 @@ static gcp_status grad_impl(gcp_handle* h, const gcp_factors* F, gcp_loss loss, 
             const int64_t blocks_nz = (((nz + per_warp - 1) / per_warp) + sh.block / 32 - 1) / (sh.block / 32);
             grid = static_cast<int>(tiles + std::min<int64_t>(sh.grid, blocks_nz));
             layout = sh.comb ? 5 : 3;
-        } else {
+        } else if (z_end > z_begin) {  // (a range of nonzero draws only needs no zeros)
             st = ensure_zero_list(h, S->q);
             if (st != GCP_OK) return st;
             int32_t* zdst[GCP_MAX_MODES] = {};
