@@ -330,7 +330,8 @@ gcp_status gcp_grad(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
    across GPUs, each GPU taking one range and a sum of G across GPUs
    following -- the parallel use of sampling that Section 6 points to.  With
    a stratified spec each call examines every candidate tile (the zeros of
-   a range depend on every earlier candidate) and walks only its range.
+   a range depend on every earlier candidate) and walks only its range; a
+   range of nonzero draws only (first + count <= p) makes no zeros.
    stream_dev, replica slabs, allocation and overlap rules as for gcp_grad.
    Errors: GCP_ERR_INVALID_ARG (S NULL, first < 0, count < 0, or
    first + count beyond gcp_sample_count(S)) and as gcp_grad. */
