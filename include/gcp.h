@@ -234,11 +234,16 @@ gcp_status gcp_create(gcp_handle **out, const gcp_tensor *X, gcp_stream_t stream
    handle), GCP_ERR_CUDA. */
 gcp_status gcp_refresh(gcp_handle *h, gcp_stream_t stream);
 
-/* Frees the handle's device memory (synchronises the device first). */
+/* Frees the handle and all device memory it owns (waits for the whole
+   device first, so no launch of the handle is still running); h must not be
+   used afterwards.  Errors: GCP_ERR_INVALID_ARG (NULL handle). */
 gcp_status gcp_destroy(gcp_handle *h);
 
-/* Reads and clears the handle's sticky device status word (a gcp_status).
-   Synchronises the device.  host_out: host. */
+/* Reads and clears the handle's sticky device status word (a gcp_status:
+   the first error a kernel of the handle recorded since the last read, or
+   GCP_OK).  Synchronises the device.  host_out: host, one int32_t.
+   Errors: GCP_ERR_INVALID_ARG (NULL handle or host_out), GCP_ERR_CUDA (a
+   failed launch or copy; *host_out is then not written). */
 gcp_status gcp_get_device_status(gcp_handle *h, int32_t *host_out);
 
 /* Number of entries a sampling spec draws: q for uniform and observed,
@@ -268,7 +273,10 @@ int64_t gcp_sample_count(const gcp_sampling *S);
    (cudaMalloc), and the first observed call reads the count of entries of
    nonzero weight back to the host: make that first call (or gcp_reserve)
    before any stream capture.  A shortfall sets GCP_ERR_SAMPLE_SHORTFALL in
-   the device status; the unfilled slots then hold weight 0. */
+   the device status; the unfilled slots then hold weight 0.
+   Errors: GCP_ERR_INVALID_ARG (a NULL handle, a bad spec or list, out->n
+   other than gcp_sample_count(S)), GCP_ERR_UNSUPPORTED, GCP_ERR_NO_MEMORY,
+   GCP_ERR_CUDA. */
 gcp_status gcp_sample(gcp_handle *h, const gcp_sampling *S, const gcp_samples *out,
                       gcp_stream_t stream);
 
@@ -383,12 +391,13 @@ gcp_status gcp_loss_est(gcp_handle *h, const gcp_factors *F, gcp_loss loss,
    1024 blocks of 256), longer lists return GCP_ERR_INVALID_ARG.  out_dev:
    one device double.  The first call on a device does a one-time set-up:
    with that device current it looks up the array's device address
-   (cudaGetSymbolAddress); make that first call before any stream capture.
-   Every call clears the array's counter on the stream before its kernel.
+   (cudaGetSymbolAddress).  Every call clears the array's counter on the stream before its kernel.
    Every call shares the array: calls whose kernels overlap on the GPU
    (other streams, other threads) race and give wrong results.  Same
    arithmetic as gcp_loss_est (FP32 terms, FP64 sums); the block count may
-   differ, so the last bits may too. */
+   differ, so the last bits may too.  Errors: GCP_ERR_INVALID_ARG (d outside
+   2..8, a bad loss, factor set or list, a list that is too long, out_dev
+   NULL or not 8-byte aligned), GCP_ERR_CUDA (the set-up or the launch). */
 gcp_status gcp_loss_est_noalloc(int32_t d, const gcp_factors *F, gcp_loss loss, const gcp_samples *list,
                                 double *out_dev, gcp_stream_t stream);
 
@@ -396,8 +405,10 @@ gcp_status gcp_loss_est_noalloc(int32_t d, const gcp_factors *F, gcp_loss loss, 
 /* Adam with projection and the epoch logic of Alg. 4                       */
 /* ------------------------------------------------------------------------ */
 
-/* Sets *state (device) to the start of a run: F = F_old = 0, t = iter = 0,
-   alpha, bad = done = status = ticket = 0. */
+/* Sets *state (device, one gcp_adam_state, 8-byte aligned) to the start of
+   a run of Alg. 4: F = F_old = 0, t = iter = 0, the given step size alpha,
+   bad = done = status = ticket = 0.  Errors: GCP_ERR_INVALID_ARG (state NULL
+   or misaligned), GCP_ERR_CUDA. */
 gcp_status gcp_state_init(gcp_adam_state *state, float alpha, gcp_stream_t stream);
 
 /* One Adam step for every mode (Alg. 4, inner loop): with t = state->t,
@@ -408,7 +419,9 @@ gcp_status gcp_state_init(gcp_adam_state *state, float alpha, gcp_stream_t strea
    read from state.  B, C, G: device FP32 with A's layout.  Does nothing
    but zero G once state->done is set.  dims: host, d entries.  Factor sets
    of 2^31 or more float4 chunks (sum of n_k * ld / 4; 32 GB) are rejected
-   with GCP_ERR_INVALID_ARG. */
+   with GCP_ERR_INVALID_ARG.  Errors: GCP_ERR_INVALID_ARG (d outside 1..8, a
+   bad rank or ld, a NULL or misaligned factor, G, B, C or state, beta1 or
+   beta2 outside [0, 1), eps < 0, the size above), GCP_ERR_CUDA. */
 gcp_status gcp_adam_step(const gcp_factors *F, int32_t d, const int64_t *dims,
                          float *const G[GCP_MAX_MODES], float *const B[GCP_MAX_MODES],
                          float *const C[GCP_MAX_MODES], const gcp_adam_params *prm,
@@ -498,10 +511,15 @@ typedef struct gcp_batch gcp_batch; /* opaque: the device-side problem table */
    entry weights, a non-uniform spec, misaligned pointers) or count outside
    1..1024, GCP_ERR_NO_MEMORY. */
 gcp_status gcp_batch_create(gcp_batch **out, const gcp_batch_problem *problems, int32_t count, gcp_stream_t stream);
+
+/* Frees the batch and its device memory (waits for the whole device first;
+   the problems' caller-owned memory is not touched).  Errors:
+   GCP_ERR_INVALID_ARG (NULL batch). */
 gcp_status gcp_batch_destroy(gcp_batch *b);
 
 /* Launch shape of the batched gradient: threads per block (multiple of 32,
-   <= 256; 0 = 256) and blocks (0 = one resident wave). */
+   <= 256; 0 = 256) and blocks (0 = one resident wave).  Host-side only.
+   Errors: GCP_ERR_INVALID_ARG (NULL batch, values out of range). */
 gcp_status gcp_batch_set_tuning(gcp_batch *b, int32_t block, int32_t grid_blocks);
 
 /* Shape of the batched gradient for every problem: chunks_per_lane (1..8;
@@ -522,22 +540,26 @@ gcp_status gcp_batch_set_shape(gcp_batch *b, int32_t chunks_per_lane, int32_t re
 
 /* The shape problem `problem` runs with: lanes per draw, chunks per lane and
    the replica slabs of each mode (host outputs; replicas holds 4 entries,
-   0 beyond the problem's modes). */
+   0 beyond the problem's modes).  Errors: GCP_ERR_INVALID_ARG (NULL batch
+   or output, problem outside 0..count-1). */
 gcp_status gcp_batch_get_shape(gcp_batch *b, int32_t problem, int32_t *lanes, int32_t *chunks, int32_t *replicas);
 
 /* The sampled gradients of every problem (Eq. (4.3), Alg. 1) into G: warps
    take 32 consecutive draws of one problem at a time from a table of all
    problems' draws; a mode whose rows receive many updates adds them into
-   replica slabs, folded into G by a second launch. */
+   replica slabs, folded into G by a second launch.  Errors:
+   GCP_ERR_INVALID_ARG (NULL batch), GCP_ERR_CUDA. */
 gcp_status gcp_batch_grad(gcp_batch *b, gcp_stream_t stream);
 
 /* The Adam step of every problem (as gcp_adam_step), one launch.  It also
    folds (and clears) the replica slabs into which gcp_batch_iteration's
    gradient kernel spreads the updates of heavily hit rows; after a plain
-   gcp_batch_grad those slabs are already folded and zero. */
+   gcp_batch_grad those slabs are already folded and zero.  Errors:
+   GCP_ERR_INVALID_ARG (NULL batch), GCP_ERR_CUDA. */
 gcp_status gcp_batch_adam_step(gcp_batch *b, gcp_stream_t stream);
 
-/* gcp_batch_grad then gcp_batch_adam_step. */
+/* One GCP-Adam iteration of every problem (Alg. 4, inner loop body):
+   gcp_batch_grad then gcp_batch_adam_step.  Errors: as those two. */
 gcp_status gcp_batch_iteration(gcp_batch *b, gcp_stream_t stream);
 
 /* gcp_batch_iteration in one persistent launch: warps take every problem's
@@ -553,14 +575,21 @@ gcp_status gcp_batch_iteration(gcp_batch *b, gcp_stream_t stream);
    GPU.  Errors: GCP_ERR_INVALID_ARG (NULL batch), GCP_ERR_CUDA. */
 gcp_status gcp_batch_iteration_fused(gcp_batch *b, gcp_stream_t stream);
 
-/* Every problem's F-hat on its fixed list into its state->F (FP64), one launch. */
+/* Every problem's F-hat (Eq. (5.1)) on its fixed list into its state->F
+   (FP64), one launch.  Errors: GCP_ERR_INVALID_ARG (NULL batch),
+   GCP_ERR_CUDA. */
 gcp_status gcp_batch_loss_est(gcp_batch *b, gcp_stream_t stream);
 
-/* gcp_epoch_begin / gcp_epoch_end for every problem, one launch each. */
+/* gcp_epoch_begin / gcp_epoch_end (Alg. 4, outer loop) for every problem,
+   one launch each.  Errors: GCP_ERR_INVALID_ARG (NULL batch),
+   GCP_ERR_CUDA. */
 gcp_status gcp_batch_epoch_begin(gcp_batch *b, gcp_stream_t stream);
 gcp_status gcp_batch_epoch_end(gcp_batch *b, gcp_stream_t stream);
 
-/* Rounds A[k] into A_bf16[k] (round to nearest even) for every mode. */
+/* Rounds A[k] into A_bf16[k] (round to nearest even) for every mode:
+   A_bf16[k] is device BF16 with A[k]'s n_k x ld row-major layout.  dims:
+   host, d entries.  Errors: GCP_ERR_INVALID_ARG (the factor checks of
+   gcp_adam_step, or a NULL A_bf16[k]), GCP_ERR_CUDA. */
 gcp_status gcp_factors_to_bf16(const gcp_factors *F, int32_t d, const int64_t *dims,
                                gcp_stream_t stream);
 
@@ -659,7 +688,10 @@ typedef struct gcp_launch_info {
 gcp_status gcp_set_tuning(gcp_handle *h, const gcp_tuning *t);
 
 /* Reports the launch shape gcp_grad would use for these factors and draw
-   count (after automatic choices).  out: host. */
+   count (after automatic choices).  out: host.  Launches nothing.
+   Errors: GCP_ERR_INVALID_ARG (NULL handle or out, n_draws < 0, a bad
+   rank or ld, a NULL or misaligned factor, a tuned shape that is not
+   compiled for this tensor's modes). */
 gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, gcp_launch_info *out);
 
 /* Kernel timing for benchmarks.  With enable = 1 the handle creates
@@ -671,11 +703,15 @@ gcp_status gcp_get_launch(gcp_handle *h, const gcp_factors *F, int64_t n_draws, 
    gcp_tuning.tail_work), until the pairs are used up; enable = 0 destroys
    them.  gcp_profile_read synchronises the events of set `which` and returns
    the summed device time of its recorded launches in milliseconds and their
-   count, then starts a new count.  host outputs. */
+   count, then starts a new count.  host outputs.  gcp_profile synchronises
+   the device.  Errors: GCP_ERR_INVALID_ARG (NULL handle or output, capacity
+   outside 1..65536 with enable = 1, which not 0 or 1), GCP_ERR_NO_MEMORY
+   (the host arrays of events), GCP_ERR_CUDA. */
 gcp_status gcp_profile(gcp_handle *h, int32_t enable, int32_t capacity);
 gcp_status gcp_profile_read(gcp_handle *h, int32_t which, double *total_ms, int64_t *launches);
 
-/* A static string naming a status code. */
+/* A static string naming a status code ("unknown status" for a value that
+   is none); never NULL. */
 const char *gcp_status_string(gcp_status s);
 
 /* The CUDA runtime error behind the calling thread's most recent
@@ -686,7 +722,7 @@ const char *gcp_status_string(gcp_status s);
 int32_t gcp_last_cuda_error(void);
 const char *gcp_last_cuda_error_name(void);
 
-/* Library version string. */
+/* Library version string (static; never NULL). */
 const char *gcp_version(void);
 
 #ifdef __cplusplus
